@@ -1,0 +1,164 @@
+"""Ringo table->graph oracle.  TEST INFRASTRUCTURE ONLY.
+
+Plain CPU statement of the conversion defined in the paper's Section 3.4
+("Conversion of tables to graphs"): nodes are the unique values of the source
+and destination columns, every row is an edge, and each node keeps sorted out-
+and in-neighbour vectors (Section 3.2).  The arithmetic lives in
+``ringo_oracle.cpp`` (std::sort + std::unique per direction, std::map ID ->
+index); this module only compiles it with the host compiler and marshals numpy
+arrays through ctypes.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  The CUDA library neither imports nor links it,
+and the two share no code.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ringo_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LOCK = threading.Lock()
+_LIBS: dict[int, ctypes.CDLL] = {}
+
+
+class _OracleGraph(ctypes.Structure):
+    _fields_ = [
+        ("num_nodes", ctypes.c_int64),
+        ("num_edges", ctypes.c_int64),
+        ("node_ids", ctypes.POINTER(ctypes.c_int32)),
+        ("out_off", ctypes.POINTER(ctypes.c_int64)),
+        ("out_nbr", ctypes.POINTER(ctypes.c_int32)),
+        ("in_off", ctypes.POINTER(ctypes.c_int64)),
+        ("in_nbr", ctypes.POINTER(ctypes.c_int32)),
+    ]
+
+
+def lib_path(mutant: int = 0) -> str:
+    name = "libringo_oracle.so" if mutant == 0 else f"libringo_oracle_mutant{mutant}.so"
+    return os.path.join(_BUILD, name)
+
+
+def build(mutant: int = 0, force: bool = False) -> str:
+    """Compile the oracle (or one planted-mistake variant) with g++."""
+    path = lib_path(mutant)
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = f"{path}.{os.getpid()}.tmp"
+    cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", f"-DORACLE_MUTANT={mutant}",
+           _SRC, "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, path)
+    return path
+
+
+def _lib(mutant: int = 0) -> ctypes.CDLL:
+    with _LOCK:
+        if mutant not in _LIBS:
+            lib = ctypes.CDLL(build(mutant))
+            lib.oracle_table_to_graph.restype = ctypes.c_int
+            lib.oracle_table_to_graph.argtypes = [ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.c_int64, ctypes.POINTER(_OracleGraph)]
+            lib.oracle_free.argtypes = [ctypes.POINTER(_OracleGraph)]
+            lib.oracle_sample_lists.restype = ctypes.c_int
+            lib.oracle_sample_lists.argtypes = [
+                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)),
+                ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)), ctypes.c_void_p]
+            lib.oracle_free_lists.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+            lib.oracle_count_distinct.restype = ctypes.c_int
+            lib.oracle_count_distinct.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                  ctypes.c_void_p, ctypes.c_void_p]
+            _LIBS[mutant] = lib
+        return _LIBS[mutant]
+
+
+def _i32(a) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a), dtype=np.int32)
+    return a
+
+
+def _take(ptr, n: int, dtype) -> np.ndarray:
+    if n == 0:
+        return np.zeros(0, dtype=dtype)
+    return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dtype, copy=True)
+
+
+def table_to_graph(src, dst, mutant: int = 0) -> dict:
+    """Directed graph of an edge table, per the paper's Section 3.4.
+
+    Returns numpy arrays ``node_ids`` (int32, ascending), ``out_off`` /
+    ``in_off`` (int64, length V+1) and ``out_nbr`` / ``in_nbr`` (int32 node
+    indices, each list strictly increasing).
+    """
+    s, d = _i32(src), _i32(dst)
+    if s.shape != d.shape or s.ndim != 1:
+        raise ValueError("src and dst must be 1-D arrays of equal length")
+    lib = _lib(mutant)
+    g = _OracleGraph()
+    rc = lib.oracle_table_to_graph(s.ctypes.data, d.ctypes.data, s.size, ctypes.byref(g))
+    if rc != 0:
+        raise RuntimeError(f"oracle_table_to_graph failed ({rc})")
+    try:
+        V, E = int(g.num_nodes), int(g.num_edges)
+        return {
+            "num_nodes": V,
+            "num_edges": E,
+            "node_ids": _take(g.node_ids, V, np.int32),
+            "out_off": _take(g.out_off, V + 1, np.int64),
+            "out_nbr": _take(g.out_nbr, E, np.int32),
+            "in_off": _take(g.in_off, V + 1, np.int64),
+            "in_nbr": _take(g.in_nbr, E, np.int32),
+        }
+    finally:
+        lib.oracle_free(ctypes.byref(g))
+
+
+def sample_lists(src, dst, ids) -> tuple[list, list, np.ndarray]:
+    """Sorted unique out- and in-neighbour ID lists of the chosen node IDs.
+
+    One scan over all rows (Section 3.4's definition restricted to the chosen
+    nodes); usable on tables far too large for :func:`table_to_graph`.
+    Returns (out_lists, in_lists, present) with lists of int32 arrays.
+    """
+    s, d, q = _i32(src), _i32(dst), _i32(ids)
+    nq = q.size
+    oc = np.zeros(nq, np.int64)
+    ic = np.zeros(nq, np.int64)
+    pres = np.zeros(nq, np.int64)
+    po = ctypes.POINTER(ctypes.c_int32)()
+    pi = ctypes.POINTER(ctypes.c_int32)()
+    lib = _lib()
+    rc = lib.oracle_sample_lists(s.ctypes.data, d.ctypes.data, s.size, q.ctypes.data, nq,
+                                 oc.ctypes.data, ic.ctypes.data, ctypes.byref(po),
+                                 ctypes.byref(pi), pres.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("oracle_sample_lists failed")
+    try:
+        allo = _take(po, int(oc.sum()), np.int32)
+        alli = _take(pi, int(ic.sum()), np.int32)
+    finally:
+        lib.oracle_free_lists(po, pi)
+    oo = np.concatenate([[0], np.cumsum(oc)])
+    io = np.concatenate([[0], np.cumsum(ic)])
+    outs = [allo[oo[k]:oo[k + 1]] for k in range(nq)]
+    ins = [alli[io[k]:io[k + 1]] for k in range(nq)]
+    return outs, ins, pres.astype(bool)
+
+
+def count_distinct(src, dst) -> tuple[int, int]:
+    """(number of distinct rows, number of distinct node IDs) of a table."""
+    s, d = _i32(src), _i32(dst)
+    e = np.zeros(1, np.int64)
+    v = np.zeros(1, np.int64)
+    _lib().oracle_count_distinct(s.ctypes.data, d.ctypes.data, s.size, e.ctypes.data,
+                                 v.ctypes.data)
+    return int(e[0]), int(v[0])
