@@ -1,0 +1,394 @@
+"""Benchmark: table->graph conversion throughput on GB300.
+
+One step = one full conversion (every kernel of the path) of a synthetic edge
+table already resident in HBM, through the C ABI (ringo_table_to_graph).
+Default workload: the Twitter2010-shaped table (1.47B rows, 41.7M IDs), the
+configuration the paper's headline conversion number is quoted on (its
+Table 5).  edges/s = input rows / wall time, the paper's definition.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload twitter|lj|tiny]
+    python bench.py --impl reference ...   # the CPU oracle on bounded samples
+
+For N > 1 (torchrun) every rank converts its own table (replicas, weak
+scaling); the reported time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+WORKLOADS = {
+    "twitter": "Twitter2010-shaped edge table: 1.47B rows, 41.7M distinct 31-bit IDs, "
+               "Zipf in-degree (s=0.72) and out-degree (s=0.5), 0.5% duplicates, random order",
+    "lj": "LiveJournal-shaped edge table: 69M rows, 4.85M distinct 31-bit IDs, power-law "
+          "out/in weights (exponent 2.3, max 20K), 1% duplicates, random order",
+    "tiny": "1M-row edge table, 100K distinct 31-bit IDs, Zipf(1.1) src, uniform dst, "
+            "5% duplicates, 0.1% self-loops",
+}
+# the paper's own table->graph rates (Table 5, 4x Xeon E7-4870, real graphs)
+PAPER_RATE = {"twitter": 18.0e6, "lj": 13.0e6}
+CPU_SAMPLE_ROWS = {"twitter": 2_000_000, "lj": 2_000_000, "tiny": 1_000_000}
+REF_SAMPLE_ROWS = {"twitter": 1_000_000, "lj": 1_000_000, "tiny": 250_000}
+SORT_SOURCES = ["paper_1503_07881_gb300/csrc/sort_kernels.cu",
+                "paper_1503_07881_gb300/csrc/ringo_internal.cuh",
+                "paper_1503_07881_gb300/csrc/device_util.cuh"]
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------ dist --
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        if torch.cuda.is_available():
+            dist.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks --
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- roofline ---
+def measured_peak_hbm() -> tuple[float, str]:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def sort_source_digest() -> str:
+    h = hashlib.sha256()
+    for p in SORT_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_key_pass() -> float | None:
+    """DRAM bytes per key per radix pass from the committed ncu summary, if it
+    was taken on the current onesweep source."""
+    path = os.path.join(ROOT, "profiles", "onesweep_pass_ncu.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"dram_bytes_per_key_pass:\s*([0-9.]+)", text)
+    d = re.search(r"source_digest:\s*([0-9a-f]+)", text)
+    if not m or not d or d.group(1) != sort_source_digest():
+        return None
+    return float(m.group(1))
+
+
+# --------------------------------------------------------------- our arm --
+def run_ours(args, world, rank, local):
+    from paper_1503_07881_gb300 import ringo, tablegen
+    import oracle
+
+    ringo.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spec = tablegen.SPECS[args.workload]
+    t0 = time.time()
+    src, dst = tablegen.make_table(spec, seed=args.seed + rank, device=dev)
+    torch.cuda.synchronize()
+    log(f"[rank {rank}] generated {spec.rows} rows in {time.time() - t0:.1f}s")
+    N = spec.rows
+
+    def step():
+        g = ringo.ringo_table_to_graph(src, dst)
+        info = g.info()
+        g.free()
+        return info
+
+    info = None
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize()
+    E, V = info["num_edges"], info["num_nodes"]
+    P_out, P_in = info["out_sort_passes"], info["in_sort_passes"]
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler.start()
+    ringo.ringo_profile_start()
+    start.record(stream)
+    for _ in range(args.steps):
+        step()
+    end.record(stream)
+    torch.cuda.synchronize()
+    prof = ringo.ringo_profile_stop()
+    clocks = sampler.stop()
+    barrier(world)
+    ms = start.elapsed_time(end) / args.steps
+    ms = max_over_ranks(ms, world)
+    value = N * world / (ms / 1e3)
+
+    # roofline of the dominant kernel (the onesweep radix pass)
+    peak, peak_kind = measured_peak_hbm()
+    by = {p["name"]: p for p in prof}
+    sw = by.get("onesweep")
+    moved = 16.0 * (N * P_out + E * P_in) * args.steps  # read + write of 8-byte keys
+    sw_ms = sw["total_ms"] if sw else float("nan")
+    achieved = moved / (sw_ms / 1e3) / 1e9
+    per_key = ncu_traffic_per_key_pass()
+    traffic = None if per_key is None else per_key * N  # one out-sort launch over N keys
+    kernel_share = {p["name"]: round(p["total_ms"] / (ms * args.steps), 4) for p in prof}
+    # whole-path frozen model (8N + 20V + 16 + 8E compulsory, + 104N + 64E sort model)
+    model_bytes = 8 * N + 20 * V + 16 + 8 * E + 104 * N + 64 * E
+    model_frac = model_bytes / (ms / 1e3) / 1e9 / peak
+
+    # e2e: host columns -> graph -> host arrays, through the C ABI
+    e2e = None
+    if not args.no_e2e:
+        hs = torch.empty(N, dtype=torch.int32, pin_memory=True)
+        hd = torch.empty(N, dtype=torch.int32, pin_memory=True)
+        hs.copy_(src)
+        hd.copy_(dst)
+        outs = {"node_ids": torch.empty(V, dtype=torch.int32, pin_memory=True),
+                "out_off": torch.empty(V + 1, dtype=torch.int64, pin_memory=True),
+                "out_nbr": torch.empty(E, dtype=torch.int32, pin_memory=True),
+                "in_off": torch.empty(V + 1, dtype=torch.int64, pin_memory=True),
+                "in_nbr": torch.empty(E, dtype=torch.int32, pin_memory=True)}
+
+        def e2e_step():
+            g = ringo.ringo_table_to_graph_host(hs, hd)
+            g.copy_to_host(outs)
+            g.free()
+
+        e2e_step()
+        torch.cuda.synchronize()
+        k2 = max(1, min(args.steps, 5))
+        barrier(world)
+        s2 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        s2.record(stream)
+        for _ in range(k2):
+            e2e_step()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        ms2 = max_over_ranks(s2.elapsed_time(e2) / k2, world)
+        e2e = {"value": N * world / (ms2 / 1e3), "unit": "edges/s", "ms_per_step": round(ms2, 3),
+               "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 4 * V + 16 * (V + 1) + 8 * E}
+        del hs, hd, outs
+
+    # CPU baseline: the oracle on a bounded prefix sample of the same table
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        S = min(N, CPU_SAMPLE_ROWS[args.workload])
+        s_h, d_h = src[:S].cpu().numpy(), dst[:S].cpu().numpy()
+        t1 = time.perf_counter()
+        oracle.table_to_graph(s_h, d_h)
+        dt = time.perf_counter() - t1
+        cpu = {"value": S / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {S} rows of the same table, one oracle run "
+                         f"(std::sort + std::unique + std::map), {dt:.1f}s"}
+
+    launches = sum(p["launches"] for p in prof)
+    line = {
+        "metric": "table->graph edges/s",
+        "value": value,
+        "unit": "edges/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": (value / PAPER_RATE[args.workload]) if args.workload in PAPER_RATE else None,
+        "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "rows": N, "distinct_edges": E,
+                   "nodes": V, "radix_passes": {"out": P_out, "in": P_in},
+                   "l2": "inputs (8 B/row) larger than L2", "seed": args.seed,
+                   "parallelism": f"replicas x{world}",
+                   "model_roofline_frac": round(model_frac, 4),
+                   "model_bytes_per_step": model_bytes,
+                   "kernel_time_share": kernel_share,
+                   "vs_baseline_note": "paper Table 5 rate on real graphs, 4x Xeon E7-4870"},
+        "roofline": {"bound": "hbm", "kernel": "onesweep radix pass",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_kind,
+                     "algorithmic_bytes": "16 B per key per pass (8 B read + 8 B write)"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------- reference arm ----
+def run_reference(args, rank):
+    """The oracle, as it stands, on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1503_07881_gb300 import tablegen
+
+    spec = tablegen.SPECS[args.workload]
+    S = min(spec.rows, REF_SAMPLE_ROWS[args.workload])
+    n_slices = args.warmup + args.steps
+    slices = []
+    for k in range(n_slices):
+        lo = (k * S) % max(1, spec.rows - S + 1)
+        s, d = tablegen.make_table(spec, seed=args.seed, device="cpu", start=lo, count=S)
+        slices.append((s.numpy(), d.numpy()))
+    for k in range(args.warmup):
+        oracle.table_to_graph(*slices[k])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.table_to_graph(*slices[args.warmup + k])
+    dt = time.perf_counter() - t0
+    ms = dt * 1e3 / args.steps
+    value = S / (ms / 1e3)
+    line = {
+        "impl": "reference",
+        "metric": "table->graph edges/s",
+        "value": value,
+        "unit": "edges/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": (value / PAPER_RATE[args.workload]) if args.workload in PAPER_RATE else None,
+        "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "rows_per_step": S,
+                   "note": "each step converts a different bounded slice of the workload"},
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{S}-row slices of the workload, one per step"},
+        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="twitter")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("note: fewer than 3 warm-up steps requested; using 3")
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, int(os.environ.get("RANK", "0")))
+        return
+    world, rank, local = dist_setup(args)
+    try:
+        run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

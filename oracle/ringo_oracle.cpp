@@ -176,13 +176,23 @@ int oracle_sample_lists(const int32_t* src, const int32_t* dst, int64_t n,
                         int64_t* present) {
   std::map<int32_t, int64_t> slot;
   for (int64_t k = 0; k < nq; ++k) slot[ids[k]] = k;
+  // membership pre-filter (one bit per hash bucket) so that a scan over
+  // billions of rows only consults the map for likely matches
+  std::vector<uint64_t> filt(1 << 14, 0);
+  auto bucket = [](int32_t x) { return (uint32_t)(((uint32_t)x * 2654435761u) >> 12); };
+  for (int64_t k = 0; k < nq; ++k) filt[bucket(ids[k]) >> 6] |= 1ull << (bucket(ids[k]) & 63);
+  auto maybe = [&](int32_t x) { return (filt[bucket(x) >> 6] >> (bucket(x) & 63)) & 1; };
   std::vector<std::vector<int32_t>> outl(nq), inl(nq);
   std::vector<int64_t> seen(nq, 0);
   for (int64_t i = 0; i < n; ++i) {
-    auto a = slot.find(src[i]);
-    if (a != slot.end()) { outl[a->second].push_back(dst[i]); seen[a->second] = 1; }
-    auto b = slot.find(dst[i]);
-    if (b != slot.end()) { inl[b->second].push_back(src[i]); seen[b->second] = 1; }
+    if (maybe(src[i])) {
+      auto a = slot.find(src[i]);
+      if (a != slot.end()) { outl[a->second].push_back(dst[i]); seen[a->second] = 1; }
+    }
+    if (maybe(dst[i])) {
+      auto b = slot.find(dst[i]);
+      if (b != slot.end()) { inl[b->second].push_back(src[i]); seen[b->second] = 1; }
+    }
   }
   std::vector<int32_t> oc, ic;
   for (int64_t k = 0; k < nq; ++k) {

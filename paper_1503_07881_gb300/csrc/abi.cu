@@ -1,0 +1,472 @@
+// C ABI of libringo (declared in include/ringo.h) and the host orchestration
+// of the table->graph conversion (paper, Section 3.4).
+//
+// Launch sequence on the caller's stream, for N input rows:
+//   histogram                 digit counts of the 8 out-sort passes (1 read)
+//   plan(out)                 digit offsets; which passes move keys
+//   onesweep x 8              (src,dst) keys, 8-bit digits, LSD
+//   dedup                     distinct edges, source runs, in-sort histograms
+//   plan(in)
+//   onesweep x 4              (dst, source-run) keys on the dst half
+//   dst_runs                  destination runs, in_nbr as source-run indices
+//   -- stream sync: E, Vs, Vd sized on the host; node arrays allocated --
+//   merge                     node_ids, out_off, in_off, src_rank
+//   directory                 ID-range directory of node_ids
+//   remap                     out_nbr: ID -> index, in_nbr: run -> index
+//   -- stream sync: V and error flags --
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/ringo.h"
+#include "host_util.h"
+#include "ringo_internal.cuh"
+
+using namespace ringo;
+
+struct ringo_graph {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  ringo_graph_info info{};
+  int32_t* node_ids = nullptr;
+  int64_t* out_off = nullptr;
+  int32_t* out_nbr = nullptr;
+  int64_t* in_off = nullptr;
+  int32_t* in_nbr = nullptr;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+uint32_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x && p < (1ull << 31)) p <<= 1;
+  return (uint32_t)p;
+}
+
+void free_graph_arrays(ringo_graph* g) {
+  pool_free(g->node_ids, g->stream);
+  pool_free(g->out_off, g->stream);
+  pool_free(g->out_nbr, g->stream);
+  pool_free(g->in_off, g->stream);
+  pool_free(g->in_nbr, g->stream);
+  g->node_ids = nullptr;
+  g->out_off = g->in_off = nullptr;
+  g->out_nbr = g->in_nbr = nullptr;
+}
+
+// Graph of an empty table: no nodes, no edges, offsets {0}.
+int make_empty(ringo_graph* g) {
+  g->out_off = (int64_t*)pool_alloc(sizeof(int64_t), g->stream);
+  g->in_off = (int64_t*)pool_alloc(sizeof(int64_t), g->stream);
+  if (!g->out_off || !g->in_off) return RINGO_ENOMEM;
+  RINGO_CUDA_TRY(cudaMemsetAsync(g->out_off, 0, sizeof(int64_t), g->stream));
+  RINGO_CUDA_TRY(cudaMemsetAsync(g->in_off, 0, sizeof(int64_t), g->stream));
+  RINGO_CUDA_TRY(cudaStreamSynchronize(g->stream));
+  return RINGO_OK;
+}
+
+struct WsLayout {
+  size_t ctl, keysA, keysB, st0, st1, sc0, sc1, sc2, usrc, usrc_start, total;
+};
+
+WsLayout layout_for(uint32_t n) {
+  const size_t tiles = (n + kSortTile - 1) / kSortTile;
+  const size_t mtiles = ((size_t)2 * n + kMergeTile - 1) / kMergeTile + 1;
+  WsLayout L{};
+  size_t o = 0;
+  L.ctl = o; o = align_up(o + sizeof(Ctl));
+  L.keysA = o; o = align_up(o + sizeof(uint64_t) * ((size_t)n + 1));
+  L.keysB = o; o = align_up(o + sizeof(uint64_t) * ((size_t)n + 1));
+  L.st0 = o; o = align_up(o + sizeof(uint32_t) * tiles * kRadix);
+  L.st1 = o; o = align_up(o + sizeof(uint32_t) * tiles * kRadix);
+  L.sc0 = o; o = align_up(o + sizeof(uint64_t) * tiles);
+  L.sc1 = o; o = align_up(o + sizeof(uint64_t) * tiles);
+  L.sc2 = o; o = align_up(o + sizeof(uint64_t) * mtiles);
+  L.usrc = o; o = align_up(o + sizeof(int32_t) * ((size_t)n + 1));
+  L.usrc_start = o; o = align_up(o + sizeof(int32_t) * ((size_t)n + 1));
+  L.total = o;
+  return L;
+}
+
+// The conversion proper, for 1 <= n < 2^31 device rows.
+int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph* g) {
+  cudaStream_t s = g->stream;
+  const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
+  const WsLayout L = layout_for(n);
+  char* ws = (char*)pool_alloc(L.total, s);
+  if (!ws) return RINGO_ENOMEM;
+  g->out_nbr = (int32_t*)pool_alloc(sizeof(int32_t) * (size_t)n, s);
+  g->in_nbr = (int32_t*)pool_alloc(sizeof(int32_t) * (size_t)n, s);
+  Ctl* hctl = (Ctl*)pinned_get(sizeof(Ctl));
+  int32_t* rank_dir = nullptr;
+  int rc = RINGO_OK;
+  Ctl* dctl = (Ctl*)(ws + L.ctl);
+  if (!g->out_nbr || !g->in_nbr || !hctl) {
+    rc = RINGO_ENOMEM;
+    if (!hctl) set_error("pinned staging allocation failed");
+    goto done;
+  }
+  {
+    memset(hctl, 0, sizeof(Ctl));
+    hctl->n_rows = n;
+    hctl->src = d_src;
+    hctl->dst = d_dst;
+    hctl->keysA = (uint64_t*)(ws + L.keysA);
+    hctl->keysB = (uint64_t*)(ws + L.keysB);
+    hctl->status[0] = (uint32_t*)(ws + L.st0);
+    hctl->status[1] = (uint32_t*)(ws + L.st1);
+    hctl->status_rows = tiles;
+    hctl->scan_status[0] = (uint64_t*)(ws + L.sc0);
+    hctl->scan_status[1] = (uint64_t*)(ws + L.sc1);
+    hctl->scan_status[2] = (uint64_t*)(ws + L.sc2);
+    hctl->usrc = (int32_t*)(ws + L.usrc);
+    hctl->usrc_start = (int32_t*)(ws + L.usrc_start);
+    hctl->out_nbr = g->out_nbr;
+    hctl->in_nbr = g->in_nbr;
+#define TRY(x)                         \
+  do {                                 \
+    cudaError_t _e = (x);              \
+    if (_e != cudaSuccess) {           \
+      set_error(std::string(#x) + ": " + cudaGetErrorString(_e)); \
+      rc = RINGO_ECUDA;                \
+      goto done;                       \
+    }                                  \
+  } while (0)
+#define LAUNCH(name, call)                                           \
+  do {                                                               \
+    {                                                                \
+      ProfScope _ps(name, s);                                        \
+      call;                                                          \
+    }                                                                \
+    cudaError_t _e = cudaGetLastError();                             \
+    if (_e != cudaSuccess) {                                         \
+      set_error(std::string("launch ") + name + ": " + cudaGetErrorString(_e)); \
+      rc = RINGO_ECUDA;                                              \
+      goto done;                                                     \
+    }                                                                \
+  } while (0)
+    TRY(cudaMemcpyAsync(dctl, hctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    // status region 0 must start clear; each pass clears the other region
+    TRY(cudaMemsetAsync(ws + L.st0, 0, L.st1 - L.st0, s));
+    TRY(cudaMemsetAsync(ws + L.sc0, 0, L.usrc - L.sc0, s));
+
+    LAUNCH("histogram", launch_histogram(dctl, n, s));
+    LAUNCH("plan", launch_plan(dctl, 0, s));
+    for (int p = 0; p < kOutPasses; ++p)
+      LAUNCH("onesweep", launch_onesweep(dctl, 0, p, p, tiles, s));
+    LAUNCH("dedup", launch_dedup(dctl, tiles, s));
+    LAUNCH("plan", launch_plan(dctl, 1, s));
+    for (int p = 0; p < kInPasses; ++p)
+      LAUNCH("onesweep", launch_onesweep(dctl, 1, p, kOutPasses + p, tiles, s));
+    LAUNCH("dst_runs", launch_dst_runs(dctl, tiles, s));
+
+    TRY(cudaMemcpyAsync(hctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    if (hctl->err) {
+      set_error("a bounded device wait expired during the sort");
+      rc = RINGO_ETIMEOUT;
+      goto done;
+    }
+    const uint64_t cap = (uint64_t)hctl->Vs + hctl->Vd;
+    if (cap > 0x7FFFFFFFull) {
+      set_error("node count does not fit int32");
+      rc = RINGO_ERANGE;
+      goto done;
+    }
+    g->node_ids = (int32_t*)pool_alloc(sizeof(int32_t) * cap, s);
+    g->out_off = (int64_t*)pool_alloc(sizeof(int64_t) * (cap + 1), s);
+    g->in_off = (int64_t*)pool_alloc(sizeof(int64_t) * (cap + 1), s);
+    if (!g->node_ids || !g->out_off || !g->in_off) {
+      rc = RINGO_ENOMEM;
+      goto done;
+    }
+    // src_rank[Vs] and the directory[nb + 1]
+    const uint32_t nb = next_pow2(cap / 8 + 1);
+    rank_dir = (int32_t*)pool_alloc(sizeof(int32_t) * ((size_t)hctl->Vs + nb + 1), s);
+    if (!rank_dir) {
+      rc = RINGO_ENOMEM;
+      goto done;
+    }
+    hctl->node_ids = g->node_ids;
+    hctl->out_off = g->out_off;
+    hctl->in_off = g->in_off;
+    hctl->src_rank = rank_dir;
+    hctl->dir = rank_dir + hctl->Vs;
+    hctl->dir_buckets = nb;
+    TRY(cudaMemcpyAsync(dctl, hctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    const uint32_t mgrid = (uint32_t)((cap + kMergeTile - 1) / kMergeTile);
+    LAUNCH("merge", launch_merge(dctl, mgrid, s));
+    // V <= cap; the directory kernel reads the exact V on the device
+    LAUNCH("directory", launch_directory(dctl, (uint32_t)cap, s));
+    LAUNCH("remap", launch_remap(dctl, hctl->E, s));
+    TRY(cudaMemcpyAsync(hctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    if (hctl->err & (kErrLookback | kErrScan)) {
+      set_error("a bounded device wait expired");
+      rc = RINGO_ETIMEOUT;
+      goto done;
+    }
+    if (hctl->err & kErrRemap) {
+      set_error("internal error: neighbour ID missing from the node list");
+      rc = RINGO_ECUDA;
+      goto done;
+    }
+    g->info.nrows = n;
+    g->info.num_nodes = hctl->V;
+    g->info.num_edges = hctl->E;
+    g->info.num_src_nodes = hctl->Vs;
+    g->info.num_dst_nodes = hctl->Vd;
+    g->info.out_sort_passes = (int32_t)hctl->out_sort.active_passes;
+    g->info.in_sort_passes = (int32_t)hctl->in_sort.active_passes;
+#undef TRY
+#undef LAUNCH
+  }
+done:
+  pool_free(rank_dir, s);
+  pool_free(ws, s);
+  if (hctl) pinned_put(hctl);
+  return rc;
+}
+
+int check_dir(int dir) { return (dir == RINGO_OUT || dir == RINGO_IN) ? RINGO_OK : RINGO_EINVAL; }
+
+}  // namespace
+
+extern "C" {
+
+const char* ringo_status_string(int status) {
+  switch (status) {
+    case RINGO_OK: return "ok";
+    case RINGO_EINVAL: return "invalid argument";
+    case RINGO_ENOMEM: return "out of memory";
+    case RINGO_ECUDA: return "CUDA error";
+    case RINGO_ETIMEOUT: return "device wait timed out";
+    case RINGO_ENOTFOUND: return "not found";
+    case RINGO_EBUSY: return "busy";
+    case RINGO_ERANGE: return "size out of range";
+    default: return "unknown status";
+  }
+}
+
+const char* ringo_last_error(void) { return ringo::last_error(); }
+
+const char* ringo_version(void) { return "ringo-gb300 0.1 sm_103a"; }
+
+static int table_to_graph_impl(const int32_t* src, const int32_t* dst, int64_t nrows,
+                               void* stream, ringo_graph** out, bool host) {
+  if (!out) {
+    set_error("out is NULL");
+    return RINGO_EINVAL;
+  }
+  *out = nullptr;
+  if (nrows < 0 || (nrows > 0 && (!src || !dst))) {
+    set_error("nrows < 0 or NULL column");
+    return RINGO_EINVAL;
+  }
+  if (nrows > 0x7FFFFFFF) {
+    set_error("nrows exceeds 2^31 - 1");
+    return RINGO_ERANGE;
+  }
+  ringo_graph* g = new (std::nothrow) ringo_graph();
+  if (!g) return RINGO_ENOMEM;
+  g->stream = (cudaStream_t)stream;
+  cudaGetDevice(&g->device);
+  int rc;
+  if (nrows == 0) {
+    rc = make_empty(g);
+  } else if (host) {
+    const size_t bytes = sizeof(int32_t) * (size_t)nrows;
+    int32_t* d_src = (int32_t*)pool_alloc(bytes, g->stream);
+    int32_t* d_dst = (int32_t*)pool_alloc(bytes, g->stream);
+    if (!d_src || !d_dst) {
+      rc = RINGO_ENOMEM;
+    } else if (cudaMemcpyAsync(d_src, src, bytes, cudaMemcpyHostToDevice, g->stream) !=
+                   cudaSuccess ||
+               cudaMemcpyAsync(d_dst, dst, bytes, cudaMemcpyHostToDevice, g->stream) !=
+                   cudaSuccess) {
+      set_error(std::string("host->device copy failed: ") +
+                cudaGetErrorString(cudaGetLastError()));
+      rc = RINGO_ECUDA;
+    } else {
+      rc = convert(d_src, d_dst, (uint32_t)nrows, g);
+    }
+    pool_free(d_src, g->stream);
+    pool_free(d_dst, g->stream);
+  } else {
+    rc = convert(src, dst, (uint32_t)nrows, g);
+  }
+  if (rc != RINGO_OK) {
+    free_graph_arrays(g);
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return RINGO_OK;
+}
+
+int ringo_table_to_graph(const int32_t* src, const int32_t* dst, int64_t nrows, void* stream,
+                         ringo_graph** out) {
+  return table_to_graph_impl(src, dst, nrows, stream, out, false);
+}
+
+int ringo_table_to_graph_host(const int32_t* h_src, const int32_t* h_dst, int64_t nrows,
+                              void* stream, ringo_graph** out) {
+  return table_to_graph_impl(h_src, h_dst, nrows, stream, out, true);
+}
+
+int ringo_graph_num_nodes(const ringo_graph* g, int64_t* v) {
+  if (!g || !v) return RINGO_EINVAL;
+  *v = g->info.num_nodes;
+  return RINGO_OK;
+}
+
+int ringo_graph_num_edges(const ringo_graph* g, int64_t* e) {
+  if (!g || !e) return RINGO_EINVAL;
+  *e = g->info.num_edges;
+  return RINGO_OK;
+}
+
+int ringo_graph_get_info(const ringo_graph* g, ringo_graph_info* info) {
+  if (!g || !info) return RINGO_EINVAL;
+  *info = g->info;
+  return RINGO_OK;
+}
+
+int ringo_graph_node_ids(const ringo_graph* g, const int32_t** d_ids) {
+  if (!g || !d_ids) return RINGO_EINVAL;
+  *d_ids = g->info.num_nodes ? g->node_ids : nullptr;
+  return RINGO_OK;
+}
+
+int ringo_graph_csr(const ringo_graph* g, int dir, const int64_t** d_off, const int32_t** d_nbr) {
+  if (!g || !d_off || !d_nbr || check_dir(dir)) return RINGO_EINVAL;
+  *d_off = dir == RINGO_OUT ? g->out_off : g->in_off;
+  *d_nbr = g->info.num_edges ? (dir == RINGO_OUT ? g->out_nbr : g->in_nbr) : nullptr;
+  return RINGO_OK;
+}
+
+int ringo_graph_degrees(const ringo_graph* g, int dir, const int32_t* d_ids, int64_t n,
+                        int64_t* d_deg, void* stream) {
+  if (!g || check_dir(dir) || n < 0 || (n > 0 && (!d_ids || !d_deg))) return RINGO_EINVAL;
+  if (n > 0x7FFFFFFF) return RINGO_ERANGE;
+  if (n == 0) return RINGO_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (g->info.num_nodes == 0) {
+    RINGO_CUDA_TRY(cudaMemsetAsync(d_deg, 0xFF, sizeof(int64_t) * (size_t)n, s));
+    return RINGO_OK;
+  }
+  {
+    ProfScope ps("degrees", s);
+    launch_degrees(g->node_ids, dir == RINGO_OUT ? g->out_off : g->in_off,
+                   (uint32_t)g->info.num_nodes, d_ids, (uint32_t)n, d_deg, s);
+  }
+  RINGO_LAUNCH_CHECK("degrees");
+  return RINGO_OK;
+}
+
+int ringo_graph_degree(const ringo_graph* g, int dir, int32_t node_id, int64_t* deg) {
+  if (!g || !deg || check_dir(dir)) return RINGO_EINVAL;
+  cudaStream_t s = g->stream;
+  void* buf = pool_alloc(16, s);
+  if (!buf) return RINGO_ENOMEM;
+  int64_t* hbuf = (int64_t*)pinned_get(16);
+  int rc = RINGO_OK;
+  if (!hbuf) {
+    pool_free(buf, s);
+    return RINGO_ENOMEM;
+  }
+  hbuf[0] = node_id;
+  int32_t* d_id = (int32_t*)buf;
+  int64_t* d_deg = (int64_t*)((char*)buf + 8);
+  if (cudaMemcpyAsync(d_id, hbuf, sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    rc = RINGO_ECUDA;
+  } else if ((rc = ringo_graph_degrees(g, dir, d_id, 1, d_deg, s)) == RINGO_OK) {
+    if (cudaMemcpyAsync(hbuf + 1, d_deg, sizeof(int64_t), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = RINGO_ECUDA;
+    } else if (hbuf[1] < 0) {
+      rc = RINGO_ENOTFOUND;
+    } else {
+      *deg = hbuf[1];
+    }
+  }
+  pool_free(buf, s);
+  pinned_put(hbuf);
+  return rc;
+}
+
+int ringo_graph_degree_topk(const ringo_graph* g, int dir, int32_t k, int32_t* h_ids,
+                            int64_t* h_degs, int32_t* n_out) {
+  if (!g || !n_out || check_dir(dir) || k < 0) return RINGO_EINVAL;
+  if (k > 4096) {
+    set_error("k above 4096");
+    return RINGO_ERANGE;
+  }
+  const int64_t V = g->info.num_nodes;
+  const uint32_t kk = (uint32_t)(k < V ? k : V);
+  *n_out = (int32_t)kk;
+  if (kk == 0) return RINGO_OK;
+  if (!h_ids || !h_degs) return RINGO_EINVAL;
+  cudaStream_t s = g->stream;
+  const size_t sb = topk_scratch_bytes((uint32_t)V, kk);
+  const size_t out_bytes = align_up(sizeof(int32_t) * kk) + sizeof(int64_t) * kk;
+  char* buf = (char*)pool_alloc(align_up(sb) + out_bytes, s);
+  if (!buf) return RINGO_ENOMEM;
+  int32_t* d_ids = (int32_t*)(buf + align_up(sb));
+  int64_t* d_degs = (int64_t*)(buf + align_up(sb) + align_up(sizeof(int32_t) * kk));
+  int rc = RINGO_OK;
+  {
+    ProfScope ps("topk", s);
+    if (launch_topk(g->node_ids, dir == RINGO_OUT ? g->out_off : g->in_off, (uint32_t)V, kk,
+                    d_ids, d_degs, buf, sb, s) != 0)
+      rc = RINGO_EINVAL;
+  }
+  if (rc == RINGO_OK) {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h_ids, d_ids, sizeof(int32_t) * kk, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h_degs, d_degs, sizeof(int64_t) * kk, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error(std::string("topk: ") + cudaGetErrorString(e));
+      rc = RINGO_ECUDA;
+    }
+  }
+  pool_free(buf, s);
+  return rc;
+}
+
+int ringo_graph_copy_to_host(const ringo_graph* g, int32_t* h_node_ids, int64_t* h_out_off,
+                             int32_t* h_out_nbr, int64_t* h_in_off, int32_t* h_in_nbr) {
+  if (!g) return RINGO_EINVAL;
+  cudaStream_t s = g->stream;
+  const size_t V = (size_t)g->info.num_nodes, E = (size_t)g->info.num_edges;
+  if (h_node_ids && V)
+    RINGO_CUDA_TRY(cudaMemcpyAsync(h_node_ids, g->node_ids, 4 * V, cudaMemcpyDeviceToHost, s));
+  if (h_out_off)
+    RINGO_CUDA_TRY(cudaMemcpyAsync(h_out_off, g->out_off, 8 * (V + 1), cudaMemcpyDeviceToHost, s));
+  if (h_out_nbr && E)
+    RINGO_CUDA_TRY(cudaMemcpyAsync(h_out_nbr, g->out_nbr, 4 * E, cudaMemcpyDeviceToHost, s));
+  if (h_in_off)
+    RINGO_CUDA_TRY(cudaMemcpyAsync(h_in_off, g->in_off, 8 * (V + 1), cudaMemcpyDeviceToHost, s));
+  if (h_in_nbr && E)
+    RINGO_CUDA_TRY(cudaMemcpyAsync(h_in_nbr, g->in_nbr, 4 * E, cudaMemcpyDeviceToHost, s));
+  RINGO_CUDA_TRY(cudaStreamSynchronize(s));
+  return RINGO_OK;
+}
+
+void ringo_graph_free(ringo_graph* g) {
+  if (!g) return;
+  free_graph_arrays(g);
+  delete g;
+}
+
+}  // extern "C"

@@ -1,0 +1,583 @@
+// Kernels after the out-sort: adjacent-duplicate removal with source-run
+// extraction, destination-run extraction after the in-sort, the node-list
+// merge, the ID -> node-index remap, and degree queries.
+//
+// These are the "computing the number of neighbors for each node, and then
+// copying the neighbor vectors" steps of the paper's sort-first conversion
+// (Section 3.4), done with single-pass compactions (decoupled look-back) so
+// that every neighbour array is written once, in order, with no atomics on
+// the data.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "device_util.cuh"
+#include "ringo_internal.cuh"
+
+namespace ringo {
+
+namespace {
+constexpr int kWarps = kScanThreads / 32;
+
+__device__ __forceinline__ int32_t unbias(uint32_t b) { return (int32_t)(b ^ kBias); }
+}  // namespace
+
+// ------------------------------------------------------------------ K3 ----
+// Input: the out-sorted keys (bias(src) << 32 | bias(dst)), n_rows of them.
+// A key that differs from its predecessor is a distinct edge e; a key whose
+// src differs is the start of a source run s.  Outputs:
+//   in-sort keys  spare[e]   = bias(dst) << 32 | s_index(src)
+//   out_nbr[e]               = dst ID (replaced by its node index later)
+//   usrc[s], usrc_start[s]   = src ID and its first edge; usrc_start[Vs] = E
+//   in_sort.hist             = digit histograms of the in-sort passes
+__global__ void __launch_bounds__(kScanThreads) k_dedup(Ctl* __restrict__ ctl) {
+  __shared__ uint32_t s_hist[kInPasses][kRadix];
+  __shared__ uint32_t s_we[kWarps], s_ws[kWarps];
+  __shared__ uint64_t s_prefix;
+  __shared__ uint32_t s_tile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(&ctl->scan_counter[0], 1u);
+  for (int i = tid; i < kInPasses * kRadix; i += kScanThreads) (&s_hist[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint32_t n = ctl->n_rows;
+  const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
+  if (tile >= ntiles) return;
+  const uint64_t* __restrict__ keys = ctl->out_sort.result;
+  const uint32_t wbase = tile * (uint32_t)kScanTile + warp * (kScanItems * 32);
+
+  uint64_t key[kScanItems];
+  uint32_t valid = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const uint32_t pos = wbase + i * 32 + lane;
+    key[i] = pos < n ? __ldcs(keys + pos) : 0;
+    if (pos < n) valid |= 1u << i;
+  }
+  uint64_t before = 0;  // key just before this warp's first item
+  if (wbase > 0 && wbase <= n) before = keys[wbase - 1];
+
+  const uint32_t lt = lanemask_lt();
+  uint32_t he = 0, hs = 0, ce = 0, cs = 0;
+  uint16_t eloc[kScanItems], sloc[kScanItems];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, key[i], 1);
+    const uint64_t last_prev_item = __shfl_sync(0xFFFFFFFFu, i ? key[i - 1] : before, 31);
+    if (lane == 0) prev = i ? last_prev_item : before;
+    const uint32_t pos = wbase + i * 32 + lane;
+    const bool ok = (valid >> i) & 1u;
+    const bool first = pos == 0;
+    const bool h_e = ok && (first || key[i] != prev);
+    const bool h_s = ok && (first || (key[i] >> 32) != (prev >> 32));
+    const uint32_t be = __ballot_sync(0xFFFFFFFFu, h_e);
+    const uint32_t bs = __ballot_sync(0xFFFFFFFFu, h_s);
+    eloc[i] = (uint16_t)(ce + __popc(be & lt));
+    sloc[i] = (uint16_t)(cs + __popc(bs & lt));
+    ce += __popc(be);
+    cs += __popc(bs);
+    he |= (uint32_t)h_e << i;
+    hs |= (uint32_t)h_s << i;
+  }
+  if (lane == 0) {
+    s_we[warp] = ce;
+    s_ws[warp] = cs;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t e = lane < kWarps ? s_we[lane] : 0;
+    const uint32_t s = lane < kWarps ? s_ws[lane] : 0;
+    const uint32_t ei = warp_inclusive_sum(e), si = warp_inclusive_sum(s);
+    const uint32_t te = __shfl_sync(0xFFFFFFFFu, ei, 31), ts = __shfl_sync(0xFFFFFFFFu, si, 31);
+    const uint64_t excl = warp_lookback(ctl->scan_status[0], tile, pack2(te, ts), &ctl->err);
+    __syncwarp();
+    if (lane < kWarps) {
+      s_we[lane] = ei - e;
+      s_ws[lane] = si - s;
+    }
+    if (lane == 0) {
+      s_prefix = excl;
+      if (tile == ntiles - 1) {
+        const uint32_t E = unpackA(excl) + te, Vs = unpackB(excl) + ts;
+        ctl->E = E;
+        ctl->Vs = Vs;
+        ctl->usrc_start[Vs] = (int32_t)E;
+      }
+    }
+  }
+  __syncthreads();
+  const uint32_t e0 = unpackA(s_prefix) + s_we[warp];
+  const uint32_t s0 = unpackB(s_prefix) + s_ws[warp];
+  uint64_t* __restrict__ ekeys = ctl->out_sort.spare;
+  int32_t* __restrict__ out_nbr = ctl->out_nbr;
+  int32_t* __restrict__ usrc = ctl->usrc;
+  int32_t* __restrict__ usrc_start = ctl->usrc_start;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (!((he >> i) & 1u)) continue;
+    const uint32_t e = e0 + eloc[i];
+    const uint32_t s = s0 + sloc[i];
+    const bool head_s = (hs >> i) & 1u;
+    const uint32_t sidx = head_s ? s : s - 1;
+    const uint32_t db = (uint32_t)key[i];
+    ekeys[e] = ((uint64_t)db << 32) | sidx;
+    out_nbr[e] = unbias(db);
+    atomicAdd(&s_hist[0][db & 0xFF], 1u);
+    atomicAdd(&s_hist[1][(db >> 8) & 0xFF], 1u);
+    atomicAdd(&s_hist[2][(db >> 16) & 0xFF], 1u);
+    atomicAdd(&s_hist[3][db >> 24], 1u);
+    if (head_s) {
+      usrc[s] = unbias((uint32_t)(key[i] >> 32));
+      usrc_start[s] = (int32_t)e;
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < kInPasses * kRadix; i += kScanThreads) {
+    const uint32_t c = (&s_hist[0][0])[i];
+    if (c) atomicAdd(&ctl->in_sort.hist[0][0] + i, c);
+  }
+}
+
+void launch_dedup(Ctl* ctl, uint32_t grid, cudaStream_t s) {
+  if (grid) k_dedup<<<grid, kScanThreads, 0, s>>>(ctl);
+}
+
+// ------------------------------------------------------------------ K5 ----
+// Input: the in-sorted keys (bias(dst) << 32 | source-run index), E of them,
+// in (dst, src) order.  Writes in_nbr[k] = source-run index (turned into a
+// node index later) and the destination runs udst[d], udst_start[d]
+// (udst_start[Vd] = E), which live in the in-sort's spare buffer.
+__global__ void __launch_bounds__(kScanThreads) k_dst_runs(Ctl* __restrict__ ctl) {
+  __shared__ uint32_t s_w[kWarps];
+  __shared__ uint64_t s_prefix;
+  __shared__ uint32_t s_tile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(&ctl->scan_counter[1], 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint32_t n = ctl->E;
+  const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
+  int32_t* __restrict__ udst = reinterpret_cast<int32_t*>(ctl->in_sort.spare);
+  int32_t* __restrict__ udst_start = udst + (ctl->n_rows + 1);
+  if (tile == 0 && tid == 0) {
+    ctl->udst = udst;
+    ctl->udst_start = udst_start;
+  }
+  if (tile >= ntiles) return;
+  const uint64_t* __restrict__ keys = ctl->in_sort.result;
+  int32_t* __restrict__ in_nbr = ctl->in_nbr;
+  const uint32_t wbase = tile * (uint32_t)kScanTile + warp * (kScanItems * 32);
+  uint64_t key[kScanItems];
+  uint32_t valid = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const uint32_t pos = wbase + i * 32 + lane;
+    key[i] = pos < n ? __ldcs(keys + pos) : 0;
+    if (pos < n) {
+      valid |= 1u << i;
+      in_nbr[pos] = (int32_t)(uint32_t)key[i];
+    }
+  }
+  uint64_t before = 0;
+  if (wbase > 0 && wbase <= n) before = keys[wbase - 1];
+  const uint32_t lt = lanemask_lt();
+  uint32_t hd = 0, cd = 0;
+  uint16_t dloc[kScanItems];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, key[i], 1);
+    const uint64_t last_prev_item = __shfl_sync(0xFFFFFFFFu, i ? key[i - 1] : before, 31);
+    if (lane == 0) prev = i ? last_prev_item : before;
+    const uint32_t pos = wbase + i * 32 + lane;
+    const bool ok = (valid >> i) & 1u;
+    const bool h = ok && (pos == 0 || (key[i] >> 32) != (prev >> 32));
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, h);
+    dloc[i] = (uint16_t)(cd + __popc(b & lt));
+    cd += __popc(b);
+    hd |= (uint32_t)h << i;
+  }
+  if (lane == 0) s_w[warp] = cd;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t c = lane < kWarps ? s_w[lane] : 0;
+    const uint32_t ci = warp_inclusive_sum(c);
+    const uint32_t tc = __shfl_sync(0xFFFFFFFFu, ci, 31);
+    const uint64_t excl = warp_lookback(ctl->scan_status[1], tile, pack2(0, tc), &ctl->err);
+    __syncwarp();
+    if (lane < kWarps) s_w[lane] = ci - c;
+    if (lane == 0) {
+      s_prefix = excl;
+      if (tile == ntiles - 1) {
+        const uint32_t Vd = unpackB(excl) + tc;
+        ctl->Vd = Vd;
+        udst_start[Vd] = (int32_t)n;
+      }
+    }
+  }
+  __syncthreads();
+  const uint32_t d0 = unpackB(s_prefix) + s_w[warp];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (!((hd >> i) & 1u)) continue;
+    const uint32_t d = d0 + dloc[i];
+    udst[d] = unbias((uint32_t)(key[i] >> 32));
+    udst_start[d] = (int32_t)(wbase + i * 32 + lane);
+  }
+}
+
+void launch_dst_runs(Ctl* ctl, uint32_t grid, cudaStream_t s) {
+  if (grid) k_dst_runs<<<grid, kScanThreads, 0, s>>>(ctl);
+}
+
+// ----------------------------------------------------------- node merge ---
+// node_ids = usrc U udst (both ascending).  Merge path over the two lists,
+// with a src item placed before an equal dst item; a dst item equal to the
+// src item before it is the same node and is dropped.  For every node the
+// merge cursor (i, j) (src items and dst items consumed before it) gives
+//   out_off[r] = usrc_start[i]   and   in_off[r] = udst_start[j],
+// which holds for nodes in both lists and for nodes in only one of them.
+__device__ __forceinline__ uint32_t merge_path(const int32_t* __restrict__ a, uint32_t na,
+                                               const int32_t* __restrict__ b, uint32_t nb,
+                                               uint32_t diag) {
+  uint32_t lo = diag > nb ? diag - nb : 0;
+  uint32_t hi = diag < na ? diag : na;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] <= b[diag - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_merge(Ctl* __restrict__ ctl) {
+  __shared__ uint32_t s_sw[kWarps + 1];
+  __shared__ uint64_t s_prefix;
+  __shared__ uint32_t s_tile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(&ctl->scan_counter[2], 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint32_t Vs = ctl->Vs, Vd = ctl->Vd, M = Vs + Vd;
+  const uint32_t ntiles = (M + kMergeTile - 1) / kMergeTile;
+  if (tile >= ntiles) return;
+  const int32_t* __restrict__ usrc = ctl->usrc;
+  const int32_t* __restrict__ udst = ctl->udst;
+  const uint32_t k0 = tile * (uint32_t)kMergeTile + tid * kMergeItems;
+  int32_t x[kMergeItems];
+  uint32_t ci[kMergeItems], cj[kMergeItems];
+  uint32_t emit = 0, from_src = 0, cnt = 0;
+  if (k0 < M) {
+    uint32_t i = merge_path(usrc, Vs, udst, Vd, k0);
+    uint32_t j = k0 - i;
+#pragma unroll
+    for (int q = 0; q < kMergeItems; ++q) {
+      if (k0 + q >= M) break;
+      const bool take_s = i < Vs && (j >= Vd || usrc[i] <= udst[j]);
+      ci[q] = i;
+      cj[q] = j;
+      if (take_s) {
+        x[q] = usrc[i];
+        emit |= 1u << q;
+        from_src |= 1u << q;
+        ++i;
+      } else {
+        x[q] = udst[j];
+        if (i == 0 || usrc[i - 1] != x[q]) emit |= 1u << q;
+        ++j;
+      }
+    }
+    cnt = __popc(emit);
+  }
+  uint32_t total;
+  const uint32_t local = block_exclusive_sum<kScanThreads>(cnt, s_sw, total);
+  if (warp == 0) {
+    const uint64_t excl = warp_lookback(ctl->scan_status[2], tile, pack2(0, total), &ctl->err);
+    if (lane == 0) {
+      s_prefix = excl;
+      if (tile == ntiles - 1) {
+        const uint32_t V = unpackB(excl) + total;
+        ctl->V = V;
+        ctl->out_off[V] = (int64_t)ctl->E;
+        ctl->in_off[V] = (int64_t)ctl->E;
+      }
+    }
+  }
+  __syncthreads();
+  uint32_t r = unpackB(s_prefix) + local;
+  const int32_t* __restrict__ us = ctl->usrc_start;
+  const int32_t* __restrict__ ud = ctl->udst_start;
+#pragma unroll
+  for (int q = 0; q < kMergeItems; ++q) {
+    if (!((emit >> q) & 1u)) continue;
+    ctl->node_ids[r] = x[q];
+    ctl->out_off[r] = us[ci[q]];
+    ctl->in_off[r] = ud[cj[q]];
+    if ((from_src >> q) & 1u) ctl->src_rank[ci[q]] = (int32_t)r;
+    ++r;
+  }
+}
+
+void launch_merge(Ctl* ctl, uint32_t grid, cudaStream_t s) {
+  if (grid) k_merge<<<grid, kScanThreads, 0, s>>>(ctl);
+}
+
+// ------------------------------------------------------------ directory ---
+// ID-range directory over node_ids: bucket k covers biased IDs
+// [lo + k 2^shift, lo + (k+1) 2^shift) and dir[k] is the index of the first
+// node at or above that range, so a node's index is found by searching only
+// node_ids[dir[k] .. dir[k+1]).
+struct DirGeom {
+  uint32_t lo;
+  uint32_t shift;
+};
+__device__ __forceinline__ DirGeom dir_geom(const int32_t* ids, uint32_t V, uint32_t nb) {
+  DirGeom g;
+  g.lo = (uint32_t)ids[0] ^ kBias;
+  const uint32_t span = ((uint32_t)ids[V - 1] ^ kBias) - g.lo;
+  uint32_t sh = 0;
+  while (sh < 32 && (span >> sh) >= nb) ++sh;
+  g.shift = sh;
+  return g;
+}
+__device__ __forceinline__ uint32_t dir_bucket(DirGeom g, int32_t id) {
+  const uint32_t off = ((uint32_t)id ^ kBias) - g.lo;
+  return g.shift >= 32 ? 0u : (off >> g.shift);
+}
+
+__global__ void k_directory(Ctl* __restrict__ ctl) {
+  const uint32_t V = ctl->V, nb = ctl->dir_buckets;
+  if (V == 0) return;
+  const int32_t* __restrict__ ids = ctl->node_ids;
+  int32_t* __restrict__ dir = ctl->dir;
+  const DirGeom g = dir_geom(ids, V, nb);
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < V; r += gridDim.x * blockDim.x) {
+    const uint32_t br = dir_bucket(g, ids[r]);
+    const uint32_t from = r == 0 ? 0u : dir_bucket(g, ids[r - 1]) + 1;
+    for (uint32_t k = from; k <= br; ++k) dir[k] = (int32_t)r;
+    if (r == V - 1)
+      for (uint32_t k = br + 1; k <= nb; ++k) dir[k] = (int32_t)V;
+  }
+}
+
+void launch_directory(Ctl* ctl, uint32_t V, cudaStream_t s) {
+  if (V == 0) return;
+  uint32_t grid = (V + 255) / 256;
+  if (grid > 4096) grid = 4096;
+  k_directory<<<grid, 256, 0, s>>>(ctl);
+}
+
+// ---------------------------------------------------------------- remap ---
+// out_nbr: dst ID -> node index (directory + search of node_ids);
+// in_nbr : source-run index -> node index (src_rank).
+__device__ __forceinline__ int32_t find_index(const int32_t* __restrict__ ids,
+                                              const int32_t* __restrict__ dir, DirGeom g,
+                                              uint32_t nb, uint32_t V, int32_t x,
+                                              uint32_t* err) {
+  uint32_t b = dir_bucket(g, x);
+  if (b >= nb) b = nb - 1;  // only for an ID outside [ids[0], ids[V-1]] (a bug)
+  uint32_t lo = (uint32_t)dir[b], hi = (uint32_t)dir[b + 1];
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (ids[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  if (lo >= V || ids[lo] != x) {
+    atomicOr(err, kErrRemap);
+    return 0;
+  }
+  return (int32_t)lo;
+}
+
+__global__ void __launch_bounds__(256) k_remap(Ctl* __restrict__ ctl) {
+  const uint32_t E = ctl->E, V = ctl->V;
+  if (V == 0) return;
+  const int32_t* __restrict__ ids = ctl->node_ids;
+  const int32_t* __restrict__ dir = ctl->dir;
+  const int32_t* __restrict__ rank = ctl->src_rank;
+  int32_t* __restrict__ on = ctl->out_nbr;
+  int32_t* __restrict__ in = ctl->in_nbr;
+  const uint32_t nb = ctl->dir_buckets;
+  const DirGeom g = dir_geom(ids, V, nb);
+  const uint32_t E4 = E / 4;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < E4; q += stride) {
+    int4 a = reinterpret_cast<const int4*>(on)[q];
+    int4 b = reinterpret_cast<const int4*>(in)[q];
+    b.x = __ldg(rank + b.x);
+    b.y = __ldg(rank + b.y);
+    b.z = __ldg(rank + b.z);
+    b.w = __ldg(rank + b.w);
+    a.x = find_index(ids, dir, g, nb, V, a.x, &ctl->err);
+    a.y = find_index(ids, dir, g, nb, V, a.y, &ctl->err);
+    a.z = find_index(ids, dir, g, nb, V, a.z, &ctl->err);
+    a.w = find_index(ids, dir, g, nb, V, a.w, &ctl->err);
+    reinterpret_cast<int4*>(on)[q] = a;
+    reinterpret_cast<int4*>(in)[q] = b;
+  }
+  for (uint32_t e = E4 * 4 + blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride) {
+    on[e] = find_index(ids, dir, g, nb, V, on[e], &ctl->err);
+    in[e] = rank[in[e]];
+  }
+}
+
+void launch_remap(Ctl* ctl, uint32_t E, cudaStream_t s) {
+  if (E == 0) return;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  uint32_t want = (E / 4 + 255) / 256 + 1;
+  uint32_t cap = (uint32_t)sms * 8;
+  k_remap<<<want < cap ? want : cap, 256, 0, s>>>(ctl);
+}
+
+// -------------------------------------------------------------- degrees ---
+__global__ void k_degrees(const int32_t* __restrict__ node_ids, const int64_t* __restrict__ off,
+                          uint32_t V, const int32_t* __restrict__ q, uint32_t n,
+                          int64_t* __restrict__ deg) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int32_t x = q[t];
+    uint32_t lo = 0, hi = V;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (node_ids[mid] < x) lo = mid + 1;
+      else hi = mid;
+    }
+    deg[t] = (lo < V && node_ids[lo] == x) ? off[lo + 1] - off[lo] : -1;
+  }
+}
+
+void launch_degrees(const int32_t* node_ids, const int64_t* off, uint32_t V, const int32_t* ids,
+                    uint32_t n, int64_t* deg, cudaStream_t s) {
+  if (n == 0) return;
+  uint32_t grid = (n + 255) / 256;
+  if (grid > 8192) grid = 8192;
+  k_degrees<<<grid, 256, 0, s>>>(node_ids, off, V, ids, n, deg);
+}
+
+// ---------------------------------------------------------------- top-k ---
+// Nodes of largest degree, ties broken by smaller ID.  Each node gets the key
+// (degree << 32) | (0xFFFFFFFF - index): larger is better, and node index
+// order is ID order.  The k-th largest key is found by an MSD radix select
+// (8 digit rounds), the k keys at or above it are gathered, and one block
+// sorts them.
+struct TopkState {
+  uint64_t prefix;      // digits of the k-th key fixed so far
+  uint32_t remaining;   // rank of the k-th key among keys matching prefix
+  uint32_t count;       // gathered keys
+  uint32_t hist[kRadix];
+};
+
+__device__ __forceinline__ uint64_t topk_key(const int64_t* off, uint32_t r) {
+  const uint64_t d = (uint64_t)(off[r + 1] - off[r]);
+  return (d << 32) | (0xFFFFFFFFu - r);
+}
+
+__global__ void k_topk_hist(const int64_t* __restrict__ off, uint32_t V, TopkState* st,
+                            int round) {
+  __shared__ uint32_t h[kRadix];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int sh = 56 - 8 * round;
+  const uint64_t pre = st->prefix;
+  const uint64_t hi_mask = round == 0 ? 0ull : (~0ull << (64 - 8 * round));
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < V; r += gridDim.x * blockDim.x) {
+    const uint64_t k = topk_key(off, r);
+    if ((k & hi_mask) == pre) atomicAdd(&h[(k >> sh) & 0xFF], 1u);
+  }
+  __syncthreads();
+  if (h[threadIdx.x]) atomicAdd(&st->hist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_topk_pick(TopkState* st, int round) {
+  // one thread: walk digits from the top to find the bucket of the k-th key
+  if (threadIdx.x != 0) return;
+  const int sh = 56 - 8 * round;
+  uint32_t rem = st->remaining;
+  for (int d = kRadix - 1; d >= 0; --d) {
+    const uint32_t c = st->hist[d];
+    if (rem <= c) {
+      st->prefix |= (uint64_t)d << sh;
+      break;
+    }
+    rem -= c;
+  }
+  st->remaining = rem;
+  for (int d = 0; d < kRadix; ++d) st->hist[d] = 0;
+}
+
+__global__ void k_topk_gather(const int64_t* __restrict__ off, uint32_t V, TopkState* st,
+                              uint64_t* out, uint32_t k) {
+  const uint64_t thr = st->prefix;  // the k-th largest key; keys are distinct
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < V; r += gridDim.x * blockDim.x) {
+    const uint64_t key = topk_key(off, r);
+    if (key >= thr) {
+      const uint32_t slot = atomicAdd(&st->count, 1u);
+      if (slot < k) out[slot] = key;
+    }
+  }
+}
+
+constexpr int kTopkMax = 4096;
+__global__ void __launch_bounds__(1024) k_topk_sort(const int32_t* __restrict__ node_ids,
+                                                    const uint64_t* in, uint32_t k,
+                                                    int32_t* ids, int64_t* degs) {
+  __shared__ uint64_t s[kTopkMax];
+  uint32_t p2 = 1;
+  while (p2 < k) p2 <<= 1;
+  for (uint32_t i = threadIdx.x; i < p2; i += blockDim.x) s[i] = i < k ? in[i] : 0;
+  __syncthreads();
+  // bitonic sort, descending
+  for (uint32_t size = 2; size <= p2; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t i = threadIdx.x; i < p2; i += blockDim.x) {
+        const uint32_t j = i ^ stride;
+        if (j > i) {
+          const bool desc = (i & size) == 0;
+          const uint64_t a = s[i], b = s[j];
+          if (desc ? (a < b) : (a > b)) {
+            s[i] = b;
+            s[j] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
+    const uint64_t key = s[i];
+    const uint32_t r = 0xFFFFFFFFu - (uint32_t)key;
+    ids[i] = node_ids[r];
+    degs[i] = (int64_t)(key >> 32);
+  }
+}
+
+size_t topk_scratch_bytes(uint32_t V, uint32_t k) {
+  (void)V;
+  return sizeof(TopkState) + 16 + sizeof(uint64_t) * (size_t)(k ? k : 1);
+}
+
+int launch_topk(const int32_t* node_ids, const int64_t* off, uint32_t V, uint32_t k,
+                int32_t* d_ids, int64_t* d_degs, void* d_scratch, size_t scratch_bytes,
+                cudaStream_t s) {
+  if (k == 0 || V == 0) return 0;
+  if (k > (uint32_t)kTopkMax || k > V) return -1;
+  if (scratch_bytes < topk_scratch_bytes(V, k)) return -1;
+  TopkState* st = reinterpret_cast<TopkState*>(d_scratch);
+  uint64_t* keys = reinterpret_cast<uint64_t*>(
+      (reinterpret_cast<uintptr_t>(st + 1) + 15) & ~(uintptr_t)15);
+  TopkState init{};
+  init.prefix = 0;
+  init.remaining = k;
+  init.count = 0;
+  cudaMemcpyAsync(st, &init, sizeof(init), cudaMemcpyHostToDevice, s);
+  uint32_t grid = (V + 255) / 256;
+  if (grid > 2048) grid = 2048;
+  for (int round = 0; round < 8; ++round) {
+    k_topk_hist<<<grid, kRadix, 0, s>>>(off, V, st, round);
+    k_topk_pick<<<1, 32, 0, s>>>(st, round);
+  }
+  k_topk_gather<<<grid, 256, 0, s>>>(off, V, st, keys, k);
+  k_topk_sort<<<1, 1024, 0, s>>>(node_ids, keys, k, d_ids, d_degs);
+  return 0;
+}
+
+}  // namespace ringo

@@ -1,0 +1,288 @@
+"""Python binding of libringo (the C ABI in include/ringo.h).
+
+Argument marshalling only: every step of the conversion runs in the CUDA
+library.  PyTorch is used for device memory and streams: columns are passed
+as ``tensor.data_ptr()``, the stream as ``torch.cuda.current_stream()``.
+
+If the compiled library is missing this module raises: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+RINGO_OK, RINGO_EINVAL, RINGO_ENOMEM, RINGO_ECUDA = 0, 1, 2, 3
+RINGO_ETIMEOUT, RINGO_ENOTFOUND, RINGO_EBUSY, RINGO_ERANGE = 4, 5, 6, 7
+RINGO_OUT, RINGO_IN = 0, 1
+
+_lib = None
+
+
+class RingoError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({_status_name(status)}) {detail}".strip())
+
+
+def _status_name(s: int) -> str:
+    return {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOTFOUND",
+            6: "EBUSY", 7: "ERANGE"}.get(s, "unknown")
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("num_nodes", ctypes.c_int64),
+                ("num_edges", ctypes.c_int64), ("num_src_nodes", ctypes.c_int64),
+                ("num_dst_nodes", ctypes.c_int64), ("out_sort_passes", ctypes.c_int32),
+                ("in_sort_passes", ctypes.c_int32)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
+# every symbol include/ringo.h declares, with its ctypes signature
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_PP = ctypes.POINTER(ctypes.c_void_p)
+SIGNATURES = {
+    "ringo_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ringo_last_error": (ctypes.c_char_p, []),
+    "ringo_version": (ctypes.c_char_p, []),
+    "ringo_table_to_graph": (ctypes.c_int, [_P, _P, _I64, _P, _PP]),
+    "ringo_table_to_graph_host": (ctypes.c_int, [_P, _P, _I64, _P, _PP]),
+    "ringo_graph_num_nodes": (ctypes.c_int, [_P, _P]),
+    "ringo_graph_num_edges": (ctypes.c_int, [_P, _P]),
+    "ringo_graph_get_info": (ctypes.c_int, [_P, ctypes.POINTER(GraphInfo)]),
+    "ringo_graph_node_ids": (ctypes.c_int, [_P, _PP]),
+    "ringo_graph_csr": (ctypes.c_int, [_P, ctypes.c_int, _PP, _PP]),
+    "ringo_graph_degree": (ctypes.c_int, [_P, ctypes.c_int, _I32, _P]),
+    "ringo_graph_degrees": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _P, _P]),
+    "ringo_graph_degree_topk": (ctypes.c_int, [_P, ctypes.c_int, _I32, _P, _P, _P]),
+    "ringo_graph_copy_to_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "ringo_graph_free": (None, [_P]),
+    "ringo_profile_start": (ctypes.c_int, []),
+    "ringo_profile_stop": (ctypes.c_int, [ctypes.POINTER(KernelStat), _I32, _P]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libringo.so (building it in-tree with nvcc if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"libringo.so not built ({path}); run build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != RINGO_OK:
+        detail = load().ringo_last_error().decode(errors="replace")
+        raise RingoError(rc, where, detail)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class _DevArray:
+    """Borrowed device array exposed through __cuda_array_interface__; keeps
+    its graph alive while a tensor views it."""
+
+    def __init__(self, ptr: int, n: int, typestr: str, owner):
+        self._owner = owner
+        self.__cuda_array_interface__ = {
+            "shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3,
+            "strides": None, "stream": None,
+        }
+
+
+def _view(ptr, n: int, dtype: torch.dtype, owner) -> torch.Tensor:
+    if n == 0 or not ptr:
+        return torch.empty(0, dtype=dtype, device="cuda")
+    typestr = {torch.int32: "<i4", torch.int64: "<i8"}[dtype]
+    return torch.as_tensor(_DevArray(int(ptr), n, typestr, owner), device="cuda")
+
+
+class Graph:
+    """Owner of a ``ringo_graph*`` handle."""
+
+    def __init__(self, handle: int, stream_ptr: int):
+        self._h = ctypes.c_void_p(handle)
+        self._stream_ptr = stream_ptr
+
+    def __del__(self):
+        self.free()
+
+    def free(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            load().ringo_graph_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if not self._h.value:
+            raise RuntimeError("graph already freed")
+        return self._h
+
+    def info(self) -> dict:
+        gi = GraphInfo()
+        _check(load().ringo_graph_get_info(self.handle, ctypes.byref(gi)), "ringo_graph_get_info")
+        return {f: getattr(gi, f) for f, _ in GraphInfo._fields_}
+
+    @property
+    def num_nodes(self) -> int:
+        v = ctypes.c_int64()
+        _check(load().ringo_graph_num_nodes(self.handle, ctypes.byref(v)), "ringo_graph_num_nodes")
+        return v.value
+
+    @property
+    def num_edges(self) -> int:
+        e = ctypes.c_int64()
+        _check(load().ringo_graph_num_edges(self.handle, ctypes.byref(e)), "ringo_graph_num_edges")
+        return e.value
+
+    def node_ids(self) -> torch.Tensor:
+        p = ctypes.c_void_p()
+        _check(load().ringo_graph_node_ids(self.handle, ctypes.byref(p)), "ringo_graph_node_ids")
+        return _view(p.value, self.num_nodes, torch.int32, self)
+
+    def csr(self, direction: int = RINGO_OUT) -> tuple[torch.Tensor, torch.Tensor]:
+        po, pn = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(load().ringo_graph_csr(self.handle, direction, ctypes.byref(po), ctypes.byref(pn)),
+               "ringo_graph_csr")
+        return (_view(po.value, self.num_nodes + 1, torch.int64, self),
+                _view(pn.value, self.num_edges, torch.int32, self))
+
+    def degree(self, direction: int, node_id: int) -> int:
+        d = ctypes.c_int64()
+        _check(load().ringo_graph_degree(self.handle, direction, int(node_id), ctypes.byref(d)),
+               "ringo_graph_degree")
+        return d.value
+
+    def degrees(self, direction: int, ids: torch.Tensor, stream=None) -> torch.Tensor:
+        ids = ids.to(device="cuda", dtype=torch.int32).contiguous()
+        out = torch.empty(ids.numel(), dtype=torch.int64, device="cuda")
+        _check(load().ringo_graph_degrees(self.handle, direction, ids.data_ptr(), ids.numel(),
+                                          out.data_ptr(), _stream_ptr(stream)),
+               "ringo_graph_degrees")
+        return out
+
+    def degree_topk(self, direction: int, k: int) -> tuple[np.ndarray, np.ndarray]:
+        ids = np.zeros(max(k, 1), np.int32)
+        degs = np.zeros(max(k, 1), np.int64)
+        n = ctypes.c_int32()
+        _check(load().ringo_graph_degree_topk(self.handle, direction, int(k), ids.ctypes.data,
+                                              degs.ctypes.data, ctypes.byref(n)),
+               "ringo_graph_degree_topk")
+        return ids[:n.value].copy(), degs[:n.value].copy()
+
+    def copy_to_host(self, out: dict | None = None) -> dict:
+        """All five arrays into host memory (numpy, or caller-given buffers)."""
+        V, E = self.num_nodes, self.num_edges
+        if out is None:
+            out = {"node_ids": np.empty(V, np.int32), "out_off": np.empty(V + 1, np.int64),
+                   "out_nbr": np.empty(E, np.int32), "in_off": np.empty(V + 1, np.int64),
+                   "in_nbr": np.empty(E, np.int32)}
+
+        def ptr(a):
+            if isinstance(a, torch.Tensor):
+                return a.data_ptr()
+            return a.ctypes.data
+
+        _check(load().ringo_graph_copy_to_host(
+            self.handle, ptr(out["node_ids"]), ptr(out["out_off"]), ptr(out["out_nbr"]),
+            ptr(out["in_off"]), ptr(out["in_nbr"])), "ringo_graph_copy_to_host")
+        res = dict(out)
+        res["num_nodes"], res["num_edges"] = V, E
+        return res
+
+
+def _col_ptr(t: torch.Tensor, name: str) -> int:
+    if t.dtype != torch.int32 or t.dim() != 1:
+        raise ValueError(f"{name} must be a 1-D int32 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def ringo_table_to_graph(src: torch.Tensor, dst: torch.Tensor, stream=None) -> Graph:
+    """Section 3.4 conversion of device columns (int32 CUDA tensors)."""
+    if src.numel() != dst.numel():
+        raise ValueError("src and dst differ in length")
+    if src.numel() and (not src.is_cuda or not dst.is_cuda):
+        raise ValueError("columns must be CUDA tensors; use ringo_table_to_graph_host")
+    lib = load()
+    sp = _stream_ptr(stream)
+    h = ctypes.c_void_p()
+    _check(lib.ringo_table_to_graph(_col_ptr(src, "src") if src.numel() else None,
+                                    _col_ptr(dst, "dst") if dst.numel() else None,
+                                    src.numel(), sp, ctypes.byref(h)), "ringo_table_to_graph")
+    return Graph(h.value, sp)
+
+
+def ringo_table_to_graph_host(src, dst, stream=None) -> Graph:
+    """The same conversion from host columns (numpy arrays or CPU tensors;
+    pinned CPU tensors copy fastest)."""
+    def hptr(a):
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != torch.int32 or not a.is_contiguous():
+                raise ValueError("host column must be a contiguous CPU int32 tensor")
+            return a.data_ptr(), a.numel(), a
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        return a.ctypes.data, a.size, a
+
+    ps, ns, keep_s = hptr(src)
+    pd, nd, keep_d = hptr(dst)
+    if ns != nd:
+        raise ValueError("src and dst differ in length")
+    lib = load()
+    sp = _stream_ptr(stream)
+    h = ctypes.c_void_p()
+    _check(lib.ringo_table_to_graph_host(ps if ns else None, pd if nd else None, ns, sp,
+                                         ctypes.byref(h)), "ringo_table_to_graph_host")
+    del keep_s, keep_d
+    return Graph(h.value, sp)
+
+
+def ringo_profile_start() -> None:
+    _check(load().ringo_profile_start(), "ringo_profile_start")
+
+
+def ringo_profile_stop() -> list[dict]:
+    cap = 64
+    arr = (KernelStat * cap)()
+    n = ctypes.c_int32()
+    _check(load().ringo_profile_stop(arr, cap, ctypes.byref(n)), "ringo_profile_stop")
+    return [{"name": arr[i].name.decode(), "launches": arr[i].launches,
+             "total_ms": arr[i].total_ms} for i in range(min(n.value, cap))]
+
+
+def ringo_version() -> str:
+    return load().ringo_version().decode()

@@ -208,22 +208,30 @@ def _draw(u: torch.Tensor, nodes: int, tables) -> torch.Tensor:
     return slot if rank_map is None else rank_map[slot]
 
 
-def make_table(spec: TableSpec | str, seed: int = 1, device="cpu",
-               chunk: int = 1 << 25) -> tuple[torch.Tensor, torch.Tensor]:
-    """Generate (src, dst) int32 columns of ``spec`` on ``device``."""
+def make_table(spec: TableSpec | str, seed: int = 1, device="cpu", chunk: int = 1 << 25,
+               start: int = 0, count: int | None = None) -> tuple[torch.Tensor, torch.Tensor]:
+    """Generate (src, dst) int32 columns of ``spec`` on ``device``.
+
+    ``start``/``count`` select rows [start, start+count) of the full table
+    (every row is a function of its index, so a slice equals the same rows
+    of the whole table)."""
     if isinstance(spec, str):
         spec = SPECS[spec]
     device = torch.device(device)
     n = spec.rows
+    if count is None:
+        count = n - start
+    if start < 0 or count < 0 or start + count > n:
+        raise ValueError("row range outside the table")
     ids = distinct_ids(spec.nodes, seed, device)
     out_tab = _law_tables(spec, spec.out_law, seed, 11, device)
     in_tab = _law_tables(spec, spec.in_law, seed, 12, device)
-    src = torch.empty(n, dtype=torch.int32, device=device)
-    dst = torch.empty(n, dtype=torch.int32, device=device)
+    src = torch.empty(count, dtype=torch.int32, device=device)
+    dst = torch.empty(count, dtype=torch.int32, device=device)
     dup_cut = int(spec.dup * TWO32)
     loop_cut = int(spec.loop * TWO32)
-    for lo in range(0, n, chunk):
-        hi = min(n, lo + chunk)
+    for lo in range(start, start + count, chunk):
+        hi = min(start + count, lo + chunk)
         i = torch.arange(lo, hi, dtype=torch.int64, device=device)
         # a duplicate row copies the base draw of another random row index
         is_dup = uniform32(i, seed, 1) < dup_cut
@@ -232,8 +240,8 @@ def make_table(spec: TableSpec | str, seed: int = 1, device="cpu",
         d = ids[_draw(uniform32(j, seed, 4), spec.nodes, in_tab)]
         if loop_cut:
             d = torch.where(uniform32(j, seed, 5) < loop_cut, s, d)
-        src[lo:hi] = s.to(torch.int32)
-        dst[lo:hi] = d.to(torch.int32)
+        src[lo - start:hi - start] = s.to(torch.int32)
+        dst[lo - start:hi - start] = d.to(torch.int32)
     return src, dst
 
 

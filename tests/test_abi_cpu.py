@@ -1,0 +1,55 @@
+"""The C-ABI library builds, loads and exports every declared symbol, and
+argument checks that happen before any CUDA call behave (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1503_07881_gb300 import build, ringo
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols() -> set:
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"RINGO_API\s+[\w\s\*]*?\b(ringo_\w+)\s*\(", text))
+    return names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = declared_symbols()
+    assert len(names) >= 17
+    for n in sorted(names):
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_binding_covers_every_declared_symbol():
+    assert declared_symbols() == set(ringo.SIGNATURES)
+
+
+def test_status_strings_and_version():
+    lib = ringo.load()
+    assert lib.ringo_status_string(0) == b"ok"
+    assert lib.ringo_status_string(4) == b"device wait timed out"
+    assert lib.ringo_version().startswith(b"ringo-gb300")
+
+
+def test_argument_validation_before_any_device_work():
+    lib = ringo.load()
+    h = ctypes.c_void_p()
+    assert lib.ringo_table_to_graph(None, None, 0, None, None) == ringo.RINGO_EINVAL
+    assert lib.ringo_table_to_graph(None, None, -1, None, ctypes.byref(h)) == ringo.RINGO_EINVAL
+    assert lib.ringo_table_to_graph(None, None, 5, None, ctypes.byref(h)) == ringo.RINGO_EINVAL
+    fake = ctypes.c_void_p(256)  # never dereferenced: the size check comes first
+    assert lib.ringo_table_to_graph(fake, fake, 1 << 31, None, ctypes.byref(h)) == ringo.RINGO_ERANGE
+    assert h.value is None
+    assert b"nrows" in lib.ringo_last_error()
+    v = ctypes.c_int64()
+    assert lib.ringo_graph_num_nodes(None, ctypes.byref(v)) == ringo.RINGO_EINVAL
+    lib.ringo_graph_free(None)  # no-op

@@ -1,0 +1,164 @@
+"""CUDA path vs the oracle, element by element, through the C ABI.
+
+Integer work: the bar is bit-exact equality of all five arrays plus V and E.
+Sizes span one partial tile up to many 4096-key tiles with ragged tails; the
+full-size workloads (69M and 1.47B rows) are checked on sampled nodes against
+the oracle's scan and on whole-table properties.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gpu_checks
+import oracle
+import pins
+from paper_1503_07881_gb300 import ringo, tablegen as tg
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_convert(src, dst) -> dict:
+    s = torch.as_tensor(np.asarray(src, np.int32)).cuda()
+    d = torch.as_tensor(np.asarray(dst, np.int32)).cuda()
+    g = ringo.ringo_table_to_graph(s, d)
+    try:
+        return g.copy_to_host()
+    finally:
+        g.free()
+
+
+def compare_with_oracle(src, dst, what=""):
+    src = np.asarray(src, np.int32)
+    dst = np.asarray(dst, np.int32)
+    pins.assert_same_graph(gpu_convert(src, dst), oracle.table_to_graph(src, dst), what)
+
+
+def test_golden_tables():
+    pins.check_golden(gpu_convert)
+
+
+def test_brute_force_exhaustive():
+    pins.check_brute_force_exhaustive(gpu_convert, alphabet=(-1, 0, 1, 2), max_rows=3)
+
+
+def test_brute_force_random_extreme_ids():
+    pins.check_brute_force_random(gpu_convert, trials=300)
+
+
+def test_special_cases():
+    pins.check_special_cases(gpu_convert)
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 511, 4095, 4096, 4097, 8191, 12289, 65537,
+                               100_003])
+def test_ragged_sizes(n):
+    s, d = tg.signed_table(n, max(2, n // 7), seed=n)
+    compare_with_oracle(s.numpy(), d.numpy(), f"signed n={n}")
+
+
+@pytest.mark.parametrize("spec", ["tiny", "lj", "twitter"])
+def test_shapes_scaled(spec):
+    sp = tg.SPECS[spec].scaled(1_500_017)
+    s, d = tg.make_table(sp, seed=2)
+    compare_with_oracle(s.numpy(), d.numpy(), sp.name)
+
+
+def test_tiny_config_full():
+    s, d = tg.make_table("tiny", seed=1)
+    compare_with_oracle(s.numpy(), d.numpy(), "tiny 1M")
+
+
+def test_generator_same_on_cpu_and_gpu():
+    sp = tg.SPECS["twitter"].scaled(300_000)
+    sc, dc = tg.make_table(sp, seed=4, device="cpu")
+    sg, dg = tg.make_table(sp, seed=4, device="cuda")
+    assert torch.equal(sc, sg.cpu()) and torch.equal(dc, dg.cpu())
+
+
+def test_small_id_range_skips_passes():
+    # IDs in [0, 200): the top digits never vary, so radix passes are skipped
+    rng = np.random.default_rng(5)
+    s = rng.integers(0, 200, 50_000).astype(np.int32)
+    d = rng.integers(0, 200, 50_000).astype(np.int32)
+    compare_with_oracle(s, d, "small range")
+    g = ringo.ringo_table_to_graph(torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
+    info = g.info()
+    assert info["out_sort_passes"] == 2 and info["in_sort_passes"] == 1
+
+
+def test_all_rows_identical_and_single_row():
+    compare_with_oracle(np.full(10_000, 7, np.int32), np.full(10_000, -3, np.int32), "identical")
+    compare_with_oracle(np.array([5], np.int32), np.array([5], np.int32), "one loop")
+
+
+def test_empty_table():
+    g = ringo.ringo_table_to_graph(torch.empty(0, dtype=torch.int32, device="cuda"),
+                                   torch.empty(0, dtype=torch.int32, device="cuda"))
+    a = g.copy_to_host()
+    assert a["num_nodes"] == 0 and a["num_edges"] == 0
+    assert a["out_off"].tolist() == [0] and a["in_off"].tolist() == [0]
+
+
+def test_row_order_and_duplicates():
+    s, d = tg.signed_table(30_000, 4_000, seed=12)
+    pins.check_row_order_and_duplicates(gpu_convert, s.numpy(), d.numpy())
+
+
+def test_unaligned_columns_and_host_entry():
+    s, d = tg.signed_table(20_001, 3_000, seed=13)
+    want = oracle.table_to_graph(s.numpy()[1:], d.numpy()[1:])
+    sg, dg = s.cuda(), d.cuda()
+    g = ringo.ringo_table_to_graph(sg[1:], dg[1:])  # 4-byte offset: not 16-byte aligned
+    pins.assert_same_graph(g.copy_to_host(), want, "unaligned")
+    h = ringo.ringo_table_to_graph_host(s.numpy()[1:], d.numpy()[1:])
+    pins.assert_same_graph(h.copy_to_host(), want, "host entry")
+    hp = ringo.ringo_table_to_graph_host(s[1:].clone().pin_memory(), d[1:].clone().pin_memory())
+    pins.assert_same_graph(hp.copy_to_host(), want, "pinned host entry")
+
+
+def test_degrees_and_topk():
+    s, d = tg.make_table(tg.SPECS["twitter"].scaled(400_000), seed=6)
+    want = oracle.table_to_graph(s.numpy(), d.numpy())
+    g = ringo.ringo_table_to_graph(s.cuda(), d.cuda())
+    ids = want["node_ids"]
+    q = np.r_[ids[::97], np.int32(-5), np.int32(2**31 - 1)]
+    for di, name in ((0, "out"), (1, "in")):
+        deg = np.diff(want[f"{name}_off"])
+        r = np.searchsorted(ids, q)
+        hit = (r < ids.size) & (ids[np.minimum(r, ids.size - 1)] == q)
+        exp = np.where(hit, deg[np.minimum(r, ids.size - 1)], -1)
+        got = g.degrees(di, torch.from_numpy(q)).cpu().numpy()
+        assert np.array_equal(got, exp)
+        assert g.degree(di, int(ids[5])) == int(deg[5])
+        with pytest.raises(ringo.RingoError) as e:
+            g.degree(di, -5 if -5 not in ids else 2**31 - 2)
+        assert e.value.status == ringo.RINGO_ENOTFOUND
+        for k in (1, 100, 4096):
+            tid, tdeg = g.degree_topk(di, k)
+            order = np.lexsort((ids, -deg))[:k]
+            assert np.array_equal(tid, ids[order]) and np.array_equal(tdeg, deg[order])
+
+
+def _full_size(spec: str, seed: int, n_random: int):
+    src, dst = tg.make_table(spec, seed=seed, device="cuda")
+    g = ringo.ringo_table_to_graph(src, dst)
+    a = gpu_checks.graph_arrays(g)
+    gpu_checks.check_properties(a, src, dst)
+    src_h, dst_h = src.cpu().numpy(), dst.cpu().numpy()
+    ids = a["node_ids"].cpu().numpy()
+    sample = gpu_checks.pick_samples(src_h, dst_h, ids, a, n_random=n_random)
+    gpu_checks.check_samples(a, src_h, dst_h, sample)
+    e, v = g.num_edges, g.num_nodes
+    g.free()
+    return e, v
+
+
+def test_lj_full_size_sampled():
+    e, v = _full_size("lj", 1, 300)
+    assert 6.5e7 < e < 6.9e7 and 4.5e6 < v <= 4.85e6
+
+
+@pytest.mark.slow
+def test_twitter_full_size_sampled():
+    e, v = _full_size("twitter", 1, 100)
+    assert 1.4e9 < e < 1.47e9 and 3.5e7 < v <= 4.17e7
