@@ -129,6 +129,8 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
     hctl->usrc_start = (int32_t*)(ws + L.usrc_start);
     hctl->out_nbr = g->out_nbr;
     hctl->in_nbr = g->in_nbr;
+    hctl->id_lo = 0xFFFFFFFFu;
+    hctl->id_hi = 0;
 #define TRY(x)                         \
   do {                                 \
     cudaError_t _e = (x);              \
@@ -186,9 +188,15 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
       rc = RINGO_ENOMEM;
       goto done;
     }
-    // src_rank[Vs] and the directory[nb + 1]
-    const uint32_t nb = next_pow2(cap / 8 + 1);
-    rank_dir = (int32_t*)pool_alloc(sizeof(int32_t) * ((size_t)hctl->Vs + nb + 1), s);
+    // ID -> index structure: a rank bitmap when the ID range is dense enough
+    // (at most 16 bytes of bitmap per merge item), else a directory with
+    // about 32 nodes per bucket (small enough to stay in L2).
+    const uint64_t sectors = (uint64_t)(hctl->id_hi - hctl->id_lo) / kSectorIds + 1;
+    const bool dense = sectors * 32 <= 16 * cap;
+    const uint32_t nb = dense ? 1u : next_pow2(cap / 32 + 1);
+    const size_t rank_words = ((size_t)hctl->Vs + nb + 1 + 63) & ~(size_t)63;
+    const size_t bm_words = dense ? (size_t)sectors * 8 : 0;
+    rank_dir = (int32_t*)pool_alloc(sizeof(int32_t) * (rank_words + bm_words), s);
     if (!rank_dir) {
       rc = RINGO_ENOMEM;
       goto done;
@@ -199,12 +207,17 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
     hctl->src_rank = rank_dir;
     hctl->dir = rank_dir + hctl->Vs;
     hctl->dir_buckets = nb;
+    hctl->rank_mode = dense ? kRankBitmap : kRankDirectory;
+    hctl->bitmap = dense ? (uint32_t*)(rank_dir + rank_words) : nullptr;
+    hctl->bitmap_sectors = dense ? (uint32_t)sectors : 0;
+    if (dense) TRY(cudaMemsetAsync(hctl->bitmap, 0, sizeof(uint32_t) * bm_words, s));
     TRY(cudaMemcpyAsync(dctl, hctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     const uint32_t mgrid = (uint32_t)((cap + kMergeTile - 1) / kMergeTile);
     LAUNCH("merge", launch_merge(dctl, mgrid, s));
     // V <= cap; the directory kernel reads the exact V on the device
-    LAUNCH("directory", launch_directory(dctl, (uint32_t)cap, s));
-    LAUNCH("remap", launch_remap(dctl, hctl->E, s));
+    if (dense) LAUNCH("rank_bitmap", launch_rank_bitmap(dctl, (uint32_t)cap, s));
+    else LAUNCH("directory", launch_directory(dctl, (uint32_t)cap, s));
+    LAUNCH("remap", launch_remap(dctl, hctl->E, hctl->rank_mode, s));
     TRY(cudaMemcpyAsync(hctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
     if (hctl->err & (kErrLookback | kErrScan)) {

@@ -38,6 +38,59 @@ __device__ __forceinline__ bool spin_backoff(uint32_t& spins) {
   return spins > kSpinLimit;
 }
 
+// ---- mbarrier + bulk asynchronous copy (global -> shared) ----
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later asynchronous-proxy (bulk copy) accesses to the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Bulk copy of `bytes` (multiple of 16; both addresses 16-byte aligned) from
+// global memory into this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_addr(sdst)), "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// Bounded wait for a bulk copy phase.  Gives up (returns false) after about a
+// second, or at once when another block has already recorded an error.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  const volatile uint32_t* err) {
+  uint32_t spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    ++spins;
+    if (err && (spins & 1023) == 0 && *err) return false;
+    if (spins > kSpinLimit) return false;
+  }
+  return true;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_inclusive_sum(T x) {
   const int lane = threadIdx.x & 31;
@@ -97,7 +150,7 @@ __device__ __forceinline__ uint64_t warp_lookback(uint64_t* status, uint32_t til
     const int64_t idx = j - lane;
     uint64_t s = idx >= 0 ? ld_relaxed_u64(status + idx) : kScanInc;
     while (__any_sync(0xFFFFFFFFu, (s >> 62) == 0)) {
-      if (spin_backoff(spins)) {
+      if (spin_backoff(spins) || ((spins & 255) == 0 && *(volatile uint32_t*)err)) {
         gave_up = true;
         break;
       }

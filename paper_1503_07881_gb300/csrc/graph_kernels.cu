@@ -365,19 +365,68 @@ void launch_directory(Ctl* ctl, uint32_t V, cudaStream_t s) {
   k_directory<<<grid, 256, 0, s>>>(ctl);
 }
 
+// ------------------------------------------------------------ rank bitmap -
+// Dense ID ranges: sector k covers biased IDs [id_lo + 224 k, id_lo + 224 (k+1));
+// word 0 holds the number of nodes below the sector and words 1..7 hold one
+// bit per ID.  node index(x) = word0 + set bits below x in its sector.
+__global__ void k_rank_bitmap(Ctl* __restrict__ ctl) {
+  const uint32_t V = ctl->V, ns = ctl->bitmap_sectors, lo = ctl->id_lo;
+  if (V == 0) return;
+  const int32_t* __restrict__ ids = ctl->node_ids;
+  uint32_t* __restrict__ bm = ctl->bitmap;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < V; r += gridDim.x * blockDim.x) {
+    const uint32_t off = ((uint32_t)ids[r] ^ kBias) - lo;
+    const uint32_t sec = off / kSectorIds, o = off - sec * kSectorIds;
+    atomicOr(&bm[(size_t)sec * 8 + 1 + (o >> 5)], 1u << (o & 31));
+    const uint32_t from =
+        r == 0 ? 0u : (((uint32_t)ids[r - 1] ^ kBias) - lo) / kSectorIds + 1;
+    for (uint32_t k = from; k <= sec; ++k) bm[(size_t)k * 8] = r;
+    if (r == V - 1)
+      for (uint32_t k = sec + 1; k < ns; ++k) bm[(size_t)k * 8] = V;
+  }
+}
+
+void launch_rank_bitmap(Ctl* ctl, uint32_t V, cudaStream_t s) {
+  if (V == 0) return;
+  uint32_t grid = (V + 255) / 256;
+  if (grid > 4096) grid = 4096;
+  k_rank_bitmap<<<grid, 256, 0, s>>>(ctl);
+}
+
 // ---------------------------------------------------------------- remap ---
-// out_nbr: dst ID -> node index (directory + search of node_ids);
-// in_nbr : source-run index -> node index (src_rank).
+// out_nbr: dst ID -> node index; in_nbr: source-run index -> node index
+// (src_rank).  Eight edges per thread so that eight independent random reads
+// are in flight at once.
+__device__ __forceinline__ int32_t bitmap_index(const uint32_t* __restrict__ bm, uint32_t lo,
+                                                int32_t x, uint32_t* err) {
+  const uint32_t off = ((uint32_t)x ^ kBias) - lo;
+  const uint32_t sec = off / kSectorIds, o = off - sec * kSectorIds;
+  const uint4* p = reinterpret_cast<const uint4*>(bm + (size_t)sec * 8);
+  const uint4 h0 = __ldg(p), h1 = __ldg(p + 1);
+  const uint32_t w[7] = {h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+  const uint32_t wi = o >> 5, bi = o & 31;
+  uint32_t r = h0.x;
+  uint32_t cur = 0;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    if ((uint32_t)k < wi) r += __popc(w[k]);
+    if ((uint32_t)k == wi) cur = w[k];
+  }
+  r += __popc(cur & ((1u << bi) - 1u));
+  if (!((cur >> bi) & 1u)) atomicOr(err, kErrRemap);
+  return (int32_t)r;
+}
+
 __device__ __forceinline__ int32_t find_index(const int32_t* __restrict__ ids,
                                               const int32_t* __restrict__ dir, DirGeom g,
                                               uint32_t nb, uint32_t V, int32_t x,
                                               uint32_t* err) {
   uint32_t b = dir_bucket(g, x);
   if (b >= nb) b = nb - 1;  // only for an ID outside [ids[0], ids[V-1]] (a bug)
-  uint32_t lo = (uint32_t)dir[b], hi = (uint32_t)dir[b + 1];
+  uint32_t lo = (uint32_t)__ldg(dir + b), hi = (uint32_t)__ldg(dir + b + 1);
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (ids[mid] < x) lo = mid + 1;
+    if (__ldg(ids + mid) < x) lo = mid + 1;
     else hi = mid;
   }
   if (lo >= V || ids[lo] != x) {
@@ -387,46 +436,70 @@ __device__ __forceinline__ int32_t find_index(const int32_t* __restrict__ ids,
   return (int32_t)lo;
 }
 
+template <bool kBitmap>
 __global__ void __launch_bounds__(256) k_remap(Ctl* __restrict__ ctl) {
   const uint32_t E = ctl->E, V = ctl->V;
   if (V == 0) return;
   const int32_t* __restrict__ ids = ctl->node_ids;
   const int32_t* __restrict__ dir = ctl->dir;
+  const uint32_t* __restrict__ bm = ctl->bitmap;
+  const uint32_t lo = ctl->id_lo;
   const int32_t* __restrict__ rank = ctl->src_rank;
   int32_t* __restrict__ on = ctl->out_nbr;
   int32_t* __restrict__ in = ctl->in_nbr;
+  uint32_t* err = &ctl->err;
   const uint32_t nb = ctl->dir_buckets;
-  const DirGeom g = dir_geom(ids, V, nb);
-  const uint32_t E4 = E / 4;
+  DirGeom g{0, 0};
+  if (!kBitmap) g = dir_geom(ids, V, nb);
+  auto lookup = [&](int32_t x) -> int32_t {
+    return kBitmap ? bitmap_index(bm, lo, x, err) : find_index(ids, dir, g, nb, V, x, err);
+  };
+  const uint32_t E8 = E / 8;
   const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < E4; q += stride) {
-    int4 a = reinterpret_cast<const int4*>(on)[q];
-    int4 b = reinterpret_cast<const int4*>(in)[q];
-    b.x = __ldg(rank + b.x);
-    b.y = __ldg(rank + b.y);
-    b.z = __ldg(rank + b.z);
-    b.w = __ldg(rank + b.w);
-    a.x = find_index(ids, dir, g, nb, V, a.x, &ctl->err);
-    a.y = find_index(ids, dir, g, nb, V, a.y, &ctl->err);
-    a.z = find_index(ids, dir, g, nb, V, a.z, &ctl->err);
-    a.w = find_index(ids, dir, g, nb, V, a.w, &ctl->err);
-    reinterpret_cast<int4*>(on)[q] = a;
-    reinterpret_cast<int4*>(in)[q] = b;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < E8; q += stride) {
+    const int4* on4 = reinterpret_cast<const int4*>(on) + 2 * (size_t)q;
+    const int4* in4 = reinterpret_cast<const int4*>(in) + 2 * (size_t)q;
+    int4 a0 = __ldcs(on4), a1 = __ldcs(on4 + 1);
+    int4 b0 = __ldcs(in4), b1 = __ldcs(in4 + 1);
+    b0.x = __ldg(rank + b0.x);
+    b0.y = __ldg(rank + b0.y);
+    b0.z = __ldg(rank + b0.z);
+    b0.w = __ldg(rank + b0.w);
+    b1.x = __ldg(rank + b1.x);
+    b1.y = __ldg(rank + b1.y);
+    b1.z = __ldg(rank + b1.z);
+    b1.w = __ldg(rank + b1.w);
+    a0.x = lookup(a0.x);
+    a0.y = lookup(a0.y);
+    a0.z = lookup(a0.z);
+    a0.w = lookup(a0.w);
+    a1.x = lookup(a1.x);
+    a1.y = lookup(a1.y);
+    a1.z = lookup(a1.z);
+    a1.w = lookup(a1.w);
+    int4* on4w = reinterpret_cast<int4*>(on) + 2 * (size_t)q;
+    int4* in4w = reinterpret_cast<int4*>(in) + 2 * (size_t)q;
+    __stcs(on4w, a0);
+    __stcs(on4w + 1, a1);
+    __stcs(in4w, b0);
+    __stcs(in4w + 1, b1);
   }
-  for (uint32_t e = E4 * 4 + blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride) {
-    on[e] = find_index(ids, dir, g, nb, V, on[e], &ctl->err);
+  for (uint32_t e = E8 * 8 + blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride) {
+    on[e] = lookup(on[e]);
     in[e] = rank[in[e]];
   }
 }
 
-void launch_remap(Ctl* ctl, uint32_t E, cudaStream_t s) {
+void launch_remap(Ctl* ctl, uint32_t E, uint32_t mode, cudaStream_t s) {
   if (E == 0) return;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  uint32_t want = (E / 4 + 255) / 256 + 1;
+  uint32_t want = (E / 8 + 255) / 256 + 1;
   uint32_t cap = (uint32_t)sms * 8;
-  k_remap<<<want < cap ? want : cap, 256, 0, s>>>(ctl);
+  const uint32_t grid = want < cap ? want : cap;
+  if (mode == kRankBitmap) k_remap<true><<<grid, 256, 0, s>>>(ctl);
+  else k_remap<false><<<grid, 256, 0, s>>>(ctl);
 }
 
 // -------------------------------------------------------------- degrees ---

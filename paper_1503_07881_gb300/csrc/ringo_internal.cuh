@@ -40,6 +40,10 @@ constexpr uint32_t kErrLookback = 1u;   // a radix look-back wait gave up
 constexpr uint32_t kErrScan = 2u;       // a scan look-back wait gave up
 constexpr uint32_t kErrRemap = 4u;      // an ID missing from node_ids (bug)
 
+constexpr uint32_t kRankDirectory = 0;
+constexpr uint32_t kRankBitmap = 1;
+constexpr uint32_t kSectorIds = 224;  // ID bits per 32-byte rank sector
+
 // A bounded wait: about a second at most before the kernel records an error.
 constexpr uint32_t kSpinLimit = 1u << 21;
 
@@ -105,8 +109,16 @@ struct Ctl {
   int32_t* udst;              // distinct dst IDs (placed in the spare buffer)
   int32_t* udst_start;        // first in-edge of each dst run
   int32_t* src_rank;          // [Vs] node index of usrc[i]
-  int32_t* dir;               // [dir_buckets + 1] ID-range directory
+  uint32_t id_lo, id_hi;      // smallest / largest biased ID in either column
+  // ID -> node index, one of two structures (rank_mode):
+  //  kRankDirectory: dir[k] = first node at or above bucket k of the ID range
+  //  kRankBitmap:    32-byte sectors of {node count below the sector, 224 ID
+  //                  bits}; one sector read answers a lookup
+  uint32_t rank_mode;
+  int32_t* dir;               // [dir_buckets + 1]
   uint32_t dir_buckets;       // power of two
+  uint32_t* bitmap;           // [bitmap_sectors * 8]
+  uint32_t bitmap_sectors;
   // outputs
   int32_t* out_nbr;           // [n_rows] capacity
   int32_t* in_nbr;            // [n_rows] capacity
@@ -126,7 +138,8 @@ void launch_dedup(Ctl* ctl, uint32_t grid, cudaStream_t s);
 void launch_dst_runs(Ctl* ctl, uint32_t grid, cudaStream_t s);
 void launch_merge(Ctl* ctl, uint32_t grid, cudaStream_t s);
 void launch_directory(Ctl* ctl, uint32_t V, cudaStream_t s);
-void launch_remap(Ctl* ctl, uint32_t E, cudaStream_t s);
+void launch_rank_bitmap(Ctl* ctl, uint32_t V, cudaStream_t s);
+void launch_remap(Ctl* ctl, uint32_t E, uint32_t mode, cudaStream_t s);
 void launch_degrees(const int32_t* node_ids, const int64_t* off, uint32_t V,
                     const int32_t* ids, uint32_t n, int64_t* deg, cudaStream_t s);
 int launch_topk(const int32_t* node_ids, const int64_t* off, uint32_t V, uint32_t k,

@@ -18,8 +18,8 @@ pytestmark = pytest.mark.gpu
 
 
 def gpu_convert(src, dst) -> dict:
-    s = torch.as_tensor(np.asarray(src, np.int32)).cuda()
-    d = torch.as_tensor(np.asarray(dst, np.int32)).cuda()
+    s = torch.as_tensor(np.ascontiguousarray(src, np.int32)).cuda()
+    d = torch.as_tensor(np.ascontiguousarray(dst, np.int32)).cuda()
     g = ringo.ringo_table_to_graph(s, d)
     try:
         return g.copy_to_host()
