@@ -149,6 +149,36 @@ RINGO_API int ringo_graph_copy_to_host(const ringo_graph* g, int32_t* h_node_ids
 RINGO_API void ringo_graph_free(ringo_graph* g);
 
 /*
+ * ringo_table_to_graph_noalloc -- the same conversion for callers that cannot
+ * allocate device memory at the time of the call (a fixed memory budget
+ * reserved up front, a serving loop that must not enter the allocator).
+ * The paper has no counterpart: this is a property of this library only.
+ *   No device or pinned host memory is allocated.  Scratch space is one
+ *   fixed __device__ array inside the library (about 30 MB on every GPU that
+ *   loads it, held until the process exits), so:
+ *   - nrows <= RINGO_NOALLOC_MAX_ROWS, else RINGO_ERANGE;
+ *   - calls whose GPU work overlaps (other streams or threads) race on that
+ *     array and give wrong results: callers serialise them;
+ *   - the first call on each device looks up the array's device address;
+ *     make that first call before any stream capture.
+ *   src, dst          device columns of nrows int32 IDs (borrowed)
+ *   node_ids          device, node_capacity entries       } caller-owned
+ *   out_off, in_off   device, node_capacity + 1 entries   } outputs, same
+ *   out_nbr, in_nbr   device, edge_capacity entries       } layout as above
+ *   edge_capacity     must be >= nrows
+ *   node_capacity     must be >= distinct sources + distinct destinations of
+ *                     the table (2 * nrows always suffices), else RINGO_ERANGE
+ *   num_nodes, num_edges  host outputs: V and E
+ * Blocks until the result is complete (two stream synchronisations).
+ */
+#define RINGO_NOALLOC_MAX_ROWS (1 << 20)
+RINGO_API int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* dst, int64_t nrows,
+                                           void* stream, int32_t* node_ids, int64_t* out_off,
+                                           int32_t* out_nbr, int64_t* in_off, int32_t* in_nbr,
+                                           int64_t node_capacity, int64_t edge_capacity,
+                                           int64_t* num_nodes, int64_t* num_edges);
+
+/*
  * Kernel timing.  While profiling is on, every kernel the library launches is
  * bracketed by CUDA events on its own stream.  ringo_profile_stop()
  * synchronises those events and returns, per kernel name, the number of

@@ -1,0 +1,230 @@
+// ringo_table_to_graph_noalloc: the table->graph conversion for callers that
+// cannot allocate device memory.
+//
+// Some callers are not allowed to call cudaMalloc (or any allocator) at the
+// point where they convert a table: code running under a fixed device-memory
+// budget that was reserved up front, a serving loop that must never block in
+// the allocator or fragment the pool, or a host thread that already holds
+// all the device memory it is allowed.  This entry point runs the same
+// kernels as ringo_table_to_graph, but every scratch buffer lives in one
+// file-scope __device__ array of fixed size, and the caller passes the output
+// buffers.  It allocates no device or pinned host memory.
+//
+// The scratch array (g_noalloc_scratch, about 30 MB) exists once on every GPU
+// that loads this library and stays there until the process exits.  Its
+// address is looked up once per device (cudaGetSymbolAddress) with that
+// device current; that lookup happens on the first call on a device, which
+// should therefore come before any stream capture.  All calls share the
+// array: two calls whose work overlaps on the GPU (different streams or
+// threads) race and corrupt each other's results; callers must serialise
+// them.  The array keeps whatever the last call left in it, so each call
+// clears the parts that must start at zero.
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "../../include/ringo.h"
+#include "host_util.h"
+#include "ringo_internal.cuh"
+
+using namespace ringo;
+
+namespace {
+
+constexpr uint32_t kMaxRows = RINGO_NOALLOC_MAX_ROWS;
+constexpr size_t kA = 256;
+constexpr size_t up(size_t x) { return (x + kA - 1) & ~(kA - 1); }
+constexpr size_t kTiles = (kMaxRows + kSortTile - 1) / kSortTile;
+constexpr size_t kMergeTiles = (2 * (size_t)kMaxRows + kMergeTile - 1) / kMergeTile + 1;
+// directory buckets for at most 2 * kMaxRows merge items, about 32 per bucket
+constexpr size_t kMaxBuckets = 1u << 17;
+static_assert(kMaxBuckets >= (2 * (size_t)kMaxRows) / 32 + 1, "directory too small");
+
+constexpr size_t kOffCtl = 0;
+constexpr size_t kOffKeysA = up(kOffCtl + sizeof(Ctl));
+constexpr size_t kOffKeysB = up(kOffKeysA + 8 * ((size_t)kMaxRows + 1));
+constexpr size_t kOffSt0 = up(kOffKeysB + 8 * ((size_t)kMaxRows + 1));
+constexpr size_t kOffSt1 = up(kOffSt0 + 4 * kTiles * kRadix);
+constexpr size_t kOffSc0 = up(kOffSt1 + 4 * kTiles * kRadix);
+constexpr size_t kOffSc1 = up(kOffSc0 + 8 * kTiles);
+constexpr size_t kOffSc2 = up(kOffSc1 + 8 * kTiles);
+constexpr size_t kOffUsrc = up(kOffSc2 + 8 * kMergeTiles);
+constexpr size_t kOffUsrcStart = up(kOffUsrc + 4 * ((size_t)kMaxRows + 1));
+constexpr size_t kOffRankDir = up(kOffUsrcStart + 4 * ((size_t)kMaxRows + 1));
+constexpr size_t kScratchBytes = up(kOffRankDir + 4 * ((size_t)kMaxRows + kMaxBuckets + 1));
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_mu;
+constexpr int kMaxDevices = 64;
+unsigned char* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once
+// per device; the host-side symbol itself is not a device address).
+int scratch_address(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    set_error("ringo_table_to_graph_noalloc: no usable current device");
+    return RINGO_ECUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error(std::string("cudaGetSymbolAddress of the scratch array failed: ") +
+                cudaGetErrorString(e));
+      return RINGO_ECUDA;
+    }
+    g_scratch_addr[dev] = (unsigned char*)p;
+  }
+  *out = g_scratch_addr[dev];
+  return RINGO_OK;
+}
+
+uint32_t pow2_at_least(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return (uint32_t)p;
+}
+
+}  // namespace
+
+extern "C" int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* dst,
+                                            int64_t nrows, void* stream, int32_t* node_ids,
+                                            int64_t* out_off, int32_t* out_nbr,
+                                            int64_t* in_off, int32_t* in_nbr,
+                                            int64_t node_capacity, int64_t edge_capacity,
+                                            int64_t* num_nodes, int64_t* num_edges) {
+  if (nrows < 0 || !num_nodes || !num_edges || !out_off || !in_off ||
+      (nrows > 0 && (!src || !dst || !node_ids || !out_nbr || !in_nbr))) {
+    set_error("ringo_table_to_graph_noalloc: bad argument (negative size or NULL pointer)");
+    return RINGO_EINVAL;
+  }
+  if (nrows > (int64_t)kMaxRows) {
+    set_error("ringo_table_to_graph_noalloc: nrows exceeds RINGO_NOALLOC_MAX_ROWS "
+              "(the fixed scratch array holds tables of at most 1048576 rows)");
+    return RINGO_ERANGE;
+  }
+  if (edge_capacity < nrows) {
+    set_error("ringo_table_to_graph_noalloc: edge_capacity must be at least nrows");
+    return RINGO_ERANGE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* ws = nullptr;
+  int rc = scratch_address(&ws);
+  if (rc != RINGO_OK) return rc;
+  *num_nodes = 0;
+  *num_edges = 0;
+#define NA_TRY(x)                                                              \
+  do {                                                                         \
+    cudaError_t _e = (x);                                                      \
+    if (_e != cudaSuccess) {                                                   \
+      set_error(std::string(#x) + ": " + cudaGetErrorString(_e));              \
+      return RINGO_ECUDA;                                                      \
+    }                                                                          \
+  } while (0)
+  if (nrows == 0) {
+    NA_TRY(cudaMemsetAsync(out_off, 0, sizeof(int64_t), s));
+    NA_TRY(cudaMemsetAsync(in_off, 0, sizeof(int64_t), s));
+    NA_TRY(cudaStreamSynchronize(s));
+    return RINGO_OK;
+  }
+  const uint32_t n = (uint32_t)nrows;
+  const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
+  Ctl* dctl = (Ctl*)(ws + kOffCtl);
+  Ctl h;  // host staging copy of the control block (pageable, on the stack)
+  memset(&h, 0, sizeof(h));
+  h.n_rows = n;
+  h.src = src;
+  h.dst = dst;
+  h.keysA = (uint64_t*)(ws + kOffKeysA);
+  h.keysB = (uint64_t*)(ws + kOffKeysB);
+  h.status[0] = (uint32_t*)(ws + kOffSt0);
+  h.status[1] = (uint32_t*)(ws + kOffSt1);
+  h.status_rows = tiles;
+  h.scan_status[0] = (uint64_t*)(ws + kOffSc0);
+  h.scan_status[1] = (uint64_t*)(ws + kOffSc1);
+  h.scan_status[2] = (uint64_t*)(ws + kOffSc2);
+  h.usrc = (int32_t*)(ws + kOffUsrc);
+  h.usrc_start = (int32_t*)(ws + kOffUsrcStart);
+  h.out_nbr = out_nbr;
+  h.in_nbr = in_nbr;
+  h.id_lo = 0xFFFFFFFFu;
+  h.id_hi = 0;
+  // state left by the previous call: the control block is rewritten whole,
+  // status region 0 and the scan statuses are cleared
+  NA_TRY(cudaMemcpyAsync(dctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+  NA_TRY(cudaMemsetAsync(ws + kOffSt0, 0, 4 * (size_t)tiles * kRadix, s));
+  NA_TRY(cudaMemsetAsync(ws + kOffSc0, 0, kOffUsrc - kOffSc0, s));
+#define NA_LAUNCH(name, call)                                                  \
+  do {                                                                         \
+    {                                                                          \
+      ProfScope _ps(name, s);                                                  \
+      call;                                                                    \
+    }                                                                          \
+    cudaError_t _e = cudaGetLastError();                                       \
+    if (_e != cudaSuccess) {                                                   \
+      set_error(std::string("launch ") + name + ": " + cudaGetErrorString(_e)); \
+      return RINGO_ECUDA;                                                      \
+    }                                                                          \
+  } while (0)
+  NA_LAUNCH("histogram", launch_histogram(dctl, n, s));
+  NA_LAUNCH("plan", launch_plan(dctl, 0, s));
+  for (int p = 0; p < kOutPasses; ++p)
+    NA_LAUNCH("onesweep", launch_onesweep(dctl, 0, p, p, tiles, s));
+  NA_LAUNCH("dedup", launch_dedup(dctl, tiles, s));
+  NA_LAUNCH("plan", launch_plan(dctl, 1, s));
+  for (int p = 0; p < kInPasses; ++p)
+    NA_LAUNCH("onesweep", launch_onesweep(dctl, 1, p, kOutPasses + p, tiles, s));
+  NA_LAUNCH("dst_runs", launch_dst_runs(dctl, tiles, s));
+  NA_TRY(cudaMemcpyAsync(&h, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  NA_TRY(cudaStreamSynchronize(s));
+  if (h.err) {
+    set_error("ringo_table_to_graph_noalloc: a bounded device wait expired");
+    return RINGO_ETIMEOUT;
+  }
+  const uint64_t cap = (uint64_t)h.Vs + h.Vd;
+  if ((int64_t)cap > node_capacity) {
+    set_error("ringo_table_to_graph_noalloc: node_capacity is below (distinct sources + "
+              "distinct destinations) of this table; 2 * nrows always suffices");
+    return RINGO_ERANGE;
+  }
+  // ID -> index through the directory only (the rank bitmap's size depends
+  // on the ID range and need not fit the fixed scratch array)
+  const uint32_t nb = pow2_at_least(cap / 32 + 1);
+  int32_t* rank_dir = (int32_t*)(ws + kOffRankDir);
+  h.node_ids = node_ids;
+  h.out_off = out_off;
+  h.in_off = in_off;
+  h.src_rank = rank_dir;
+  h.dir = rank_dir + h.Vs;
+  h.dir_buckets = nb;
+  h.rank_mode = kRankDirectory;
+  h.bitmap = nullptr;
+  h.bitmap_sectors = 0;
+  NA_TRY(cudaMemcpyAsync(dctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+  const uint32_t mgrid = (uint32_t)((cap + kMergeTile - 1) / kMergeTile);
+  NA_LAUNCH("merge", launch_merge(dctl, mgrid, s));
+  NA_LAUNCH("directory", launch_directory(dctl, (uint32_t)cap, s));
+  NA_LAUNCH("remap", launch_remap(dctl, h.E, kRankDirectory, s));
+  NA_TRY(cudaMemcpyAsync(&h, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  NA_TRY(cudaStreamSynchronize(s));
+#undef NA_LAUNCH
+#undef NA_TRY
+  if (h.err & (kErrLookback | kErrScan)) {
+    set_error("ringo_table_to_graph_noalloc: a bounded device wait expired");
+    return RINGO_ETIMEOUT;
+  }
+  if (h.err & kErrRemap) {
+    set_error("ringo_table_to_graph_noalloc: internal error in the ID -> index remap");
+    return RINGO_ECUDA;
+  }
+  *num_nodes = h.V;
+  *num_edges = h.E;
+  return RINGO_OK;
+}

@@ -69,6 +69,8 @@ SIGNATURES = {
     "ringo_graph_degree_topk": (ctypes.c_int, [_P, ctypes.c_int, _I32, _P, _P, _P]),
     "ringo_graph_copy_to_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "ringo_graph_free": (None, [_P]),
+    "ringo_table_to_graph_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P, _P, _P, _I64,
+                                                    _I64, _P, _P]),
     "ringo_profile_start": (ctypes.c_int, []),
     "ringo_profile_stop": (ctypes.c_int, [ctypes.POINTER(KernelStat), _I32, _P]),
 }
@@ -286,3 +288,27 @@ def ringo_profile_stop() -> list[dict]:
 
 def ringo_version() -> str:
     return load().ringo_version().decode()
+
+
+NOALLOC_MAX_ROWS = 1 << 20
+
+
+def ringo_table_to_graph_noalloc(src: torch.Tensor, dst: torch.Tensor, out: dict,
+                                 stream=None) -> tuple[int, int]:
+    """The conversion into caller-owned device buffers, with no device
+    allocation inside the library (fixed internal scratch; at most
+    NOALLOC_MAX_ROWS rows; overlapping calls race).  ``out`` holds int32
+    ``node_ids`` / ``out_nbr`` / ``in_nbr`` and int64 ``out_off`` / ``in_off``
+    CUDA tensors.  Returns (num_nodes, num_edges)."""
+    if src.numel() != dst.numel():
+        raise ValueError("src and dst differ in length")
+    n = src.numel()
+    v = ctypes.c_int64()
+    e = ctypes.c_int64()
+    _check(load().ringo_table_to_graph_noalloc(
+        _col_ptr(src, "src") if n else None, _col_ptr(dst, "dst") if n else None, n,
+        _stream_ptr(stream), out["node_ids"].data_ptr(), out["out_off"].data_ptr(),
+        out["out_nbr"].data_ptr(), out["in_off"].data_ptr(), out["in_nbr"].data_ptr(),
+        out["node_ids"].numel(), min(out["out_nbr"].numel(), out["in_nbr"].numel()),
+        ctypes.byref(v), ctypes.byref(e)), "ringo_table_to_graph_noalloc")
+    return v.value, e.value
