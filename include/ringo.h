@@ -154,7 +154,7 @@ RINGO_API void ringo_graph_free(ringo_graph* g);
  * reserved up front, a serving loop that must not enter the allocator).
  * The paper has no counterpart: this is a property of this library only.
  *   No device or pinned host memory is allocated.  Scratch space is one
- *   fixed __device__ array inside the library (about 30 MB on every GPU that
+ *   fixed __device__ array inside the library (about 41 MB on every GPU that
  *   loads it, held until the process exits), so:
  *   - nrows <= RINGO_NOALLOC_MAX_ROWS, else RINGO_ERANGE;
  *   - calls whose GPU work overlaps (other streams or threads) race on that

@@ -1,19 +1,11 @@
-// C ABI of libringo (declared in include/ringo.h) and the host orchestration
-// of the table->graph conversion (paper, Section 3.4).
-//
-// Launch sequence on the caller's stream, for N input rows:
-//   histogram                 digit counts of the 8 out-sort passes (1 read)
-//   plan(out)                 digit offsets; which passes move keys
-//   onesweep x 8              (src,dst) keys, 8-bit digits, LSD
-//   dedup                     distinct edges, source runs, in-sort histograms
-//   plan(in)
-//   onesweep x 4              (dst, source-run) keys on the dst half
-//   dst_runs                  destination runs, in_nbr as source-run indices
-//   -- stream sync: E, Vs, Vd sized on the host; node arrays allocated --
-//   merge                     node_ids, out_off, in_off, src_rank
-//   directory                 ID-range directory of node_ids
-//   remap                     out_nbr: ID -> index, in_nbr: run -> index
-//   -- stream sync: V and error flags --
+// C ABI of libringo (declared in include/ringo.h) and the host side of the
+// table->graph conversion (paper, Section 3.4).  The kernel sequence itself
+// is in pipeline.cu:
+//   phase 1  histogram, 4 dst passes, dst ranks, 4 src passes, dedup,
+//            plan + 4 in-sort passes, destination-run starts
+//   -- stream sync: E, Vs, Vd; node arrays and rank maps allocated --
+//   phase 2  merge, block tables, remap
+//   -- stream sync: V and the error word --
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -72,7 +64,7 @@ int make_empty(ringo_graph* g) {
 }
 
 struct WsLayout {
-  size_t ctl, keysA, keysB, st0, st1, sc0, sc1, sc2, usrc, usrc_start, total;
+  size_t ctl, keysA, keysB, st0, st1, sc0, sc1, sc2, usrc, usrc_start, udst, udst_start, total;
 };
 
 WsLayout layout_for(uint32_t n) {
@@ -90,8 +82,23 @@ WsLayout layout_for(uint32_t n) {
   L.sc2 = o; o = align_up(o + sizeof(uint64_t) * mtiles);
   L.usrc = o; o = align_up(o + sizeof(int32_t) * ((size_t)n + 1));
   L.usrc_start = o; o = align_up(o + sizeof(int32_t) * ((size_t)n + 1));
+  L.udst = o; o = align_up(o + sizeof(int32_t) * ((size_t)n + 1));
+  L.udst_start = o; o = align_up(o + sizeof(int32_t) * ((size_t)n + 1));
   L.total = o;
   return L;
+}
+
+// Words of the rank-map region: src_rank[Vs], dst_rank[Vd], and the two
+// block tables, each part 16-byte aligned.
+inline size_t up4(size_t x) { return (x + 3) & ~(size_t)3; }
+inline size_t rank_region_words(uint32_t Vs, uint32_t Vd) {
+  return up4(Vs) + up4(Vd) + up4((Vs + 31) / 32) + up4((Vd + 31) / 32);
+}
+void place_rank_region(Ctl* h, int32_t* base, uint32_t Vs, uint32_t Vd) {
+  h->src_rank = base;
+  h->dst_rank = base + up4(Vs);
+  h->src_blk = (uint32_t*)(h->dst_rank + up4(Vd));
+  h->dst_blk = h->src_blk + up4((Vs + 31) / 32);
 }
 
 // The conversion proper, for 1 <= n < 2^31 device rows.
@@ -104,7 +111,7 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
   g->out_nbr = (int32_t*)pool_alloc(sizeof(int32_t) * (size_t)n, s);
   g->in_nbr = (int32_t*)pool_alloc(sizeof(int32_t) * (size_t)n, s);
   Ctl* hctl = (Ctl*)pinned_get(sizeof(Ctl));
-  int32_t* rank_dir = nullptr;
+  int32_t* ranks = nullptr;
   int rc = RINGO_OK;
   Ctl* dctl = (Ctl*)(ws + L.ctl);
   if (!g->out_nbr || !g->in_nbr || !hctl) {
@@ -127,10 +134,10 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
     hctl->scan_status[2] = (uint64_t*)(ws + L.sc2);
     hctl->usrc = (int32_t*)(ws + L.usrc);
     hctl->usrc_start = (int32_t*)(ws + L.usrc_start);
+    hctl->udst = (int32_t*)(ws + L.udst);
+    hctl->udst_start = (int32_t*)(ws + L.udst_start);
     hctl->out_nbr = g->out_nbr;
     hctl->in_nbr = g->in_nbr;
-    hctl->id_lo = 0xFFFFFFFFu;
-    hctl->id_hi = 0;
 #define TRY(x)                         \
   do {                                 \
     cudaError_t _e = (x);              \
@@ -140,34 +147,11 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
       goto done;                       \
     }                                  \
   } while (0)
-#define LAUNCH(name, call)                                           \
-  do {                                                               \
-    {                                                                \
-      ProfScope _ps(name, s);                                        \
-      call;                                                          \
-    }                                                                \
-    cudaError_t _e = cudaGetLastError();                             \
-    if (_e != cudaSuccess) {                                         \
-      set_error(std::string("launch ") + name + ": " + cudaGetErrorString(_e)); \
-      rc = RINGO_ECUDA;                                              \
-      goto done;                                                     \
-    }                                                                \
-  } while (0)
     TRY(cudaMemcpyAsync(dctl, hctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     // status region 0 must start clear; each pass clears the other region
     TRY(cudaMemsetAsync(ws + L.st0, 0, L.st1 - L.st0, s));
     TRY(cudaMemsetAsync(ws + L.sc0, 0, L.usrc - L.sc0, s));
-
-    LAUNCH("histogram", launch_histogram(dctl, n, s));
-    LAUNCH("plan", launch_plan(dctl, 0, s));
-    for (int p = 0; p < kOutPasses; ++p)
-      LAUNCH("onesweep", launch_onesweep(dctl, 0, p, p, tiles, s));
-    LAUNCH("dedup", launch_dedup(dctl, tiles, s));
-    LAUNCH("plan", launch_plan(dctl, 1, s));
-    for (int p = 0; p < kInPasses; ++p)
-      LAUNCH("onesweep", launch_onesweep(dctl, 1, p, kOutPasses + p, tiles, s));
-    LAUNCH("dst_runs", launch_dst_runs(dctl, tiles, s));
-
+    if ((rc = enqueue_phase1(dctl, n, s)) != RINGO_OK) goto done;
     TRY(cudaMemcpyAsync(hctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
     if (hctl->err) {
@@ -184,40 +168,17 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
     g->node_ids = (int32_t*)pool_alloc(sizeof(int32_t) * cap, s);
     g->out_off = (int64_t*)pool_alloc(sizeof(int64_t) * (cap + 1), s);
     g->in_off = (int64_t*)pool_alloc(sizeof(int64_t) * (cap + 1), s);
-    if (!g->node_ids || !g->out_off || !g->in_off) {
-      rc = RINGO_ENOMEM;
-      goto done;
-    }
-    // ID -> index structure: a rank bitmap when the ID range is dense enough
-    // (at most 16 bytes of bitmap per merge item), else a directory with
-    // about 32 nodes per bucket (small enough to stay in L2).
-    const uint64_t sectors = (uint64_t)(hctl->id_hi - hctl->id_lo) / kSectorIds + 1;
-    const bool dense = sectors * 32 <= 16 * cap;
-    const uint32_t nb = dense ? 1u : next_pow2(cap / 32 + 1);
-    const size_t rank_words = ((size_t)hctl->Vs + nb + 1 + 63) & ~(size_t)63;
-    const size_t bm_words = dense ? (size_t)sectors * 8 : 0;
-    rank_dir = (int32_t*)pool_alloc(sizeof(int32_t) * (rank_words + bm_words), s);
-    if (!rank_dir) {
+    ranks = (int32_t*)pool_alloc(sizeof(int32_t) * rank_region_words(hctl->Vs, hctl->Vd), s);
+    if (!g->node_ids || !g->out_off || !g->in_off || !ranks) {
       rc = RINGO_ENOMEM;
       goto done;
     }
     hctl->node_ids = g->node_ids;
     hctl->out_off = g->out_off;
     hctl->in_off = g->in_off;
-    hctl->src_rank = rank_dir;
-    hctl->dir = rank_dir + hctl->Vs;
-    hctl->dir_buckets = nb;
-    hctl->rank_mode = dense ? kRankBitmap : kRankDirectory;
-    hctl->bitmap = dense ? (uint32_t*)(rank_dir + rank_words) : nullptr;
-    hctl->bitmap_sectors = dense ? (uint32_t)sectors : 0;
-    if (dense) TRY(cudaMemsetAsync(hctl->bitmap, 0, sizeof(uint32_t) * bm_words, s));
+    place_rank_region(hctl, ranks, hctl->Vs, hctl->Vd);
     TRY(cudaMemcpyAsync(dctl, hctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-    const uint32_t mgrid = (uint32_t)((cap + kMergeTile - 1) / kMergeTile);
-    LAUNCH("merge", launch_merge(dctl, mgrid, s));
-    // V <= cap; the directory kernel reads the exact V on the device
-    if (dense) LAUNCH("rank_bitmap", launch_rank_bitmap(dctl, (uint32_t)cap, s));
-    else LAUNCH("directory", launch_directory(dctl, (uint32_t)cap, s));
-    LAUNCH("remap", launch_remap(dctl, hctl->E, hctl->rank_mode, s));
+    if ((rc = enqueue_phase2(dctl, hctl->Vs, hctl->Vd, hctl->E, s)) != RINGO_OK) goto done;
     TRY(cudaMemcpyAsync(hctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
     if (hctl->err & (kErrLookback | kErrScan)) {
@@ -226,7 +187,7 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
       goto done;
     }
     if (hctl->err & kErrRemap) {
-      set_error("internal error: neighbour ID missing from the node list");
+      set_error("internal error in the run index -> node index remap");
       rc = RINGO_ECUDA;
       goto done;
     }
@@ -238,10 +199,9 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
     g->info.out_sort_passes = (int32_t)hctl->out_sort.active_passes;
     g->info.in_sort_passes = (int32_t)hctl->in_sort.active_passes;
 #undef TRY
-#undef LAUNCH
   }
 done:
-  pool_free(rank_dir, s);
+  pool_free(ranks, s);
   pool_free(ws, s);
   if (hctl) pinned_put(hctl);
   return rc;

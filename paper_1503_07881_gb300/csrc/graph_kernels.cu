@@ -1,6 +1,7 @@
-// Kernels after the out-sort: adjacent-duplicate removal with source-run
-// extraction, destination-run extraction after the in-sort, the node-list
-// merge, the ID -> node-index remap, and degree queries.
+// Kernels around the sorts: destination ranks between the dst and src
+// passes, adjacent-duplicate removal with source-run extraction,
+// destination-run starts after the in-sort, the node-list merge, the run
+// index -> node index remap, and degree queries.
 //
 // These are the "computing the number of neighbors for each node, and then
 // copying the neighbor vectors" steps of the paper's sort-first conversion
@@ -22,11 +23,11 @@ __device__ __forceinline__ int32_t unbias(uint32_t b) { return (int32_t)(b ^ kBi
 }  // namespace
 
 // ------------------------------------------------------------------ K3 ----
-// Input: the out-sorted keys (bias(src) << 32 | bias(dst)), n_rows of them.
-// A key that differs from its predecessor is a distinct edge e; a key whose
-// src differs is the start of a source run s.  Outputs:
-//   in-sort keys  spare[e]   = bias(dst) << 32 | s_index(src)
-//   out_nbr[e]               = dst ID (replaced by its node index later)
+// Input: the out-sorted keys (bias(src) << 32 | dst-run index), n_rows of
+// them.  A key that differs from its predecessor is a distinct edge e; a key
+// whose src differs is the start of a source run s.  Outputs:
+//   in-sort keys  spare[e]   = dst-run index << 32 | s_index(src)
+//   out_nbr[e]               = dst-run index (turned into a node index later)
 //   usrc[s], usrc_start[s]   = src ID and its first edge; usrc_start[Vs] = E
 //   in_sort.hist             = digit histograms of the in-sort passes
 __global__ void __launch_bounds__(kScanThreads) k_dedup(Ctl* __restrict__ ctl) {
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(kScanThreads) k_dedup(Ctl* __restrict__ ctl) {
     const uint32_t sidx = head_s ? s : s - 1;
     const uint32_t db = (uint32_t)key[i];
     ekeys[e] = ((uint64_t)db << 32) | sidx;
-    out_nbr[e] = unbias(db);
+    out_nbr[e] = (int32_t)db;
     atomicAdd(&s_hist[0][db & 0xFF], 1u);
     atomicAdd(&s_hist[1][(db >> 8) & 0xFF], 1u);
     atomicAdd(&s_hist[2][(db >> 16) & 0xFF], 1u);
@@ -141,12 +142,15 @@ void launch_dedup(Ctl* ctl, uint32_t grid, cudaStream_t s) {
   if (grid) k_dedup<<<grid, kScanThreads, 0, s>>>(ctl);
 }
 
-// ------------------------------------------------------------------ K5 ----
-// Input: the in-sorted keys (bias(dst) << 32 | source-run index), E of them,
-// in (dst, src) order.  Writes in_nbr[k] = source-run index (turned into a
-// node index later) and the destination runs udst[d], udst_start[d]
-// (udst_start[Vd] = E), which live in the in-sort's spare buffer.
-__global__ void __launch_bounds__(kScanThreads) k_dst_runs(Ctl* __restrict__ ctl) {
+// ------------------------------------------------------------- dst rank ---
+// Runs between out-sort passes 3 and 4, when the keys are in dst order.
+// Each key's dst is replaced by its destination-run index (the rank of the
+// dst among the distinct dst values), which keeps the key order; the run
+// heads give udst[], the distinct destination IDs in ascending order.
+// Reads rank_step.in (or packs from the columns when every dst pass was
+// trivial) and writes rank_step.out.  Single-pass compaction count with
+// decoupled look-back.
+__global__ void __launch_bounds__(kScanThreads) k_dst_rank(Ctl* __restrict__ ctl) {
   __shared__ uint32_t s_w[kWarps];
   __shared__ uint64_t s_prefix;
   __shared__ uint32_t s_tile;
@@ -154,31 +158,32 @@ __global__ void __launch_bounds__(kScanThreads) k_dst_runs(Ctl* __restrict__ ctl
   if (tid == 0) s_tile = atomicAdd(&ctl->scan_counter[1], 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
-  const uint32_t n = ctl->E;
+  const uint32_t n = ctl->n_rows;
   const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
-  int32_t* __restrict__ udst = reinterpret_cast<int32_t*>(ctl->in_sort.spare);
-  int32_t* __restrict__ udst_start = udst + (ctl->n_rows + 1);
-  if (tile == 0 && tid == 0) {
-    ctl->udst = udst;
-    ctl->udst_start = udst_start;
-  }
   if (tile >= ntiles) return;
-  const uint64_t* __restrict__ keys = ctl->in_sort.result;
-  int32_t* __restrict__ in_nbr = ctl->in_nbr;
+  const uint64_t* __restrict__ in = ctl->rank_step.in;
+  uint64_t* __restrict__ out = ctl->rank_step.out;
+  const int32_t* __restrict__ src = ctl->src;
+  const int32_t* __restrict__ dst = ctl->dst;
+  auto key_at = [&](uint32_t pos) -> uint64_t {
+    if (in) return in[pos];
+    return ((uint64_t)((uint32_t)src[pos] ^ kBias) << 32) | ((uint32_t)dst[pos] ^ kBias);
+  };
   const uint32_t wbase = tile * (uint32_t)kScanTile + warp * (kScanItems * 32);
   uint64_t key[kScanItems];
   uint32_t valid = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const uint32_t pos = wbase + i * 32 + lane;
-    key[i] = pos < n ? __ldcs(keys + pos) : 0;
     if (pos < n) {
+      key[i] = in ? __ldcs(in + pos) : key_at(pos);
       valid |= 1u << i;
-      in_nbr[pos] = (int32_t)(uint32_t)key[i];
+    } else {
+      key[i] = 0;
     }
   }
   uint64_t before = 0;
-  if (wbase > 0 && wbase <= n) before = keys[wbase - 1];
+  if (wbase > 0 && wbase <= n) before = key_at(wbase - 1);
   const uint32_t lt = lanemask_lt();
   uint32_t hd = 0, cd = 0;
   uint16_t dloc[kScanItems];
@@ -189,7 +194,7 @@ __global__ void __launch_bounds__(kScanThreads) k_dst_runs(Ctl* __restrict__ ctl
     if (lane == 0) prev = i ? last_prev_item : before;
     const uint32_t pos = wbase + i * 32 + lane;
     const bool ok = (valid >> i) & 1u;
-    const bool h = ok && (pos == 0 || (key[i] >> 32) != (prev >> 32));
+    const bool h = ok && (pos == 0 || (uint32_t)key[i] != (uint32_t)prev);
     const uint32_t b = __ballot_sync(0xFFFFFFFFu, h);
     dloc[i] = (uint16_t)(cd + __popc(b & lt));
     cd += __popc(b);
@@ -206,26 +211,65 @@ __global__ void __launch_bounds__(kScanThreads) k_dst_runs(Ctl* __restrict__ ctl
     if (lane < kWarps) s_w[lane] = ci - c;
     if (lane == 0) {
       s_prefix = excl;
-      if (tile == ntiles - 1) {
-        const uint32_t Vd = unpackB(excl) + tc;
-        ctl->Vd = Vd;
-        udst_start[Vd] = (int32_t)n;
-      }
+      if (tile == ntiles - 1) ctl->Vd = unpackB(excl) + tc;
     }
   }
   __syncthreads();
   const uint32_t d0 = unpackB(s_prefix) + s_w[warp];
+  int32_t* __restrict__ udst = ctl->udst;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    if (!((hd >> i) & 1u)) continue;
-    const uint32_t d = d0 + dloc[i];
-    udst[d] = unbias((uint32_t)(key[i] >> 32));
-    udst_start[d] = (int32_t)(wbase + i * 32 + lane);
+    if (!((valid >> i) & 1u)) continue;
+    const bool h = (hd >> i) & 1u;
+    const uint32_t r = d0 + dloc[i] + (h ? 0u : 0xFFFFFFFFu);  // inclusive count - 1
+    __stcs(out + wbase + i * 32 + lane, (key[i] & 0xFFFFFFFF00000000ull) | r);
+    if (h) udst[r] = unbias((uint32_t)key[i]);
   }
 }
 
-void launch_dst_runs(Ctl* ctl, uint32_t grid, cudaStream_t s) {
-  if (grid) k_dst_runs<<<grid, kScanThreads, 0, s>>>(ctl);
+void launch_dst_rank(Ctl* ctl, uint32_t grid, cudaStream_t s) {
+  if (grid) k_dst_rank<<<grid, kScanThreads, 0, s>>>(ctl);
+}
+
+// ------------------------------------------------------------------ K5 ----
+// Input: the in-sorted keys (dst-run index << 32 | source-run index), E of
+// them, in (dst, src) order.  Writes in_nbr[k] = source-run index (turned
+// into a node index later) and, at each change of dst-run index d, the run's
+// first in-edge udst_start[d] = k (udst_start[Vd] = E).  Every dst-run index
+// occurs, so no compaction is needed.
+__global__ void __launch_bounds__(256) k_dst_runs(Ctl* __restrict__ ctl) {
+  const uint32_t E = ctl->E;
+  const uint64_t* __restrict__ keys = ctl->in_sort.result;
+  int32_t* __restrict__ in_nbr = ctl->in_nbr;
+  int32_t* __restrict__ ustart = ctl->udst_start;
+  const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t0 == 0) ustart[ctl->Vd] = (int32_t)E;
+  const uint32_t E2 = E / 2;
+  for (uint32_t q = t0; q < E2; q += gridDim.x * blockDim.x) {
+    const ulonglong2 kk = __ldcs(reinterpret_cast<const ulonglong2*>(keys) + q);
+    const uint32_t k = 2 * q;
+    const uint32_t d0 = (uint32_t)(kk.x >> 32), d1 = (uint32_t)(kk.y >> 32);
+    const uint32_t dp = k ? (uint32_t)(keys[k - 1] >> 32) : 0xFFFFFFFFu;
+    if (k == 0 || d0 != dp) ustart[d0] = (int32_t)k;
+    if (d1 != d0) ustart[d1] = (int32_t)(k + 1);
+    reinterpret_cast<int2*>(in_nbr)[q] = make_int2((int32_t)(uint32_t)kk.x, (int32_t)(uint32_t)kk.y);
+  }
+  if ((E & 1) && t0 == 0) {
+    const uint32_t k = E - 1;
+    const uint64_t key = keys[k];
+    const uint32_t d = (uint32_t)(key >> 32);
+    if (k == 0 || d != (uint32_t)(keys[k - 1] >> 32)) ustart[d] = (int32_t)k;
+    in_nbr[k] = (int32_t)(uint32_t)key;
+  }
+}
+
+void launch_dst_runs(Ctl* ctl, uint32_t n_rows, cudaStream_t s) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  uint32_t want = (n_rows / 2 + 255) / 256 + 1;
+  uint32_t cap = (uint32_t)sms * 8;
+  k_dst_runs<<<want < cap ? want : cap, 256, 0, s>>>(ctl);
 }
 
 // ----------------------------------------------------------- node merge ---
@@ -235,6 +279,7 @@ void launch_dst_runs(Ctl* ctl, uint32_t grid, cudaStream_t s) {
 // merge cursor (i, j) (src items and dst items consumed before it) gives
 //   out_off[r] = usrc_start[i]   and   in_off[r] = udst_start[j],
 // which holds for nodes in both lists and for nodes in only one of them.
+// Also src_rank[i] and dst_rank[j]: the node index of each list entry.
 __device__ __forceinline__ uint32_t merge_path(const int32_t* __restrict__ a, uint32_t na,
                                                const int32_t* __restrict__ b, uint32_t nb,
                                                uint32_t diag) {
@@ -264,13 +309,14 @@ __global__ void __launch_bounds__(kScanThreads) k_merge(Ctl* __restrict__ ctl) {
   const uint32_t k0 = tile * (uint32_t)kMergeTile + tid * kMergeItems;
   int32_t x[kMergeItems];
   uint32_t ci[kMergeItems], cj[kMergeItems];
-  uint32_t emit = 0, from_src = 0, cnt = 0;
+  uint32_t emit = 0, from_src = 0, cnt = 0, used = 0;
   if (k0 < M) {
     uint32_t i = merge_path(usrc, Vs, udst, Vd, k0);
     uint32_t j = k0 - i;
 #pragma unroll
     for (int q = 0; q < kMergeItems; ++q) {
       if (k0 + q >= M) break;
+      used |= 1u << q;
       const bool take_s = i < Vs && (j >= Vd || usrc[i] <= udst[j]);
       ci[q] = i;
       cj[q] = j;
@@ -302,17 +348,25 @@ __global__ void __launch_bounds__(kScanThreads) k_merge(Ctl* __restrict__ ctl) {
     }
   }
   __syncthreads();
-  uint32_t r = unpackB(s_prefix) + local;
+  uint32_t r = unpackB(s_prefix) + local;  // nodes emitted before this item
   const int32_t* __restrict__ us = ctl->usrc_start;
   const int32_t* __restrict__ ud = ctl->udst_start;
 #pragma unroll
   for (int q = 0; q < kMergeItems; ++q) {
-    if (!((emit >> q) & 1u)) continue;
-    ctl->node_ids[r] = x[q];
-    ctl->out_off[r] = us[ci[q]];
-    ctl->in_off[r] = ud[cj[q]];
-    if ((from_src >> q) & 1u) ctl->src_rank[ci[q]] = (int32_t)r;
-    ++r;
+    if (!((used >> q) & 1u)) continue;
+    const bool e = (emit >> q) & 1u;
+    if ((from_src >> q) & 1u) {
+      ctl->src_rank[ci[q]] = (int32_t)r;
+    } else {
+      // a dropped dst item is the node emitted just before it
+      ctl->dst_rank[cj[q]] = (int32_t)(e ? r : r - 1);
+    }
+    if (e) {
+      ctl->node_ids[r] = x[q];
+      ctl->out_off[r] = us[ci[q]];
+      ctl->in_off[r] = ud[cj[q]];
+      ++r;
+    }
   }
 }
 
@@ -320,140 +374,55 @@ void launch_merge(Ctl* ctl, uint32_t grid, cudaStream_t s) {
   if (grid) k_merge<<<grid, kScanThreads, 0, s>>>(ctl);
 }
 
-// ------------------------------------------------------------ directory ---
-// ID-range directory over node_ids: bucket k covers biased IDs
-// [lo + k 2^shift, lo + (k+1) 2^shift) and dir[k] is the index of the first
-// node at or above that range, so a node's index is found by searching only
-// node_ids[dir[k] .. dir[k+1]).
-struct DirGeom {
-  uint32_t lo;
-  uint32_t shift;
-};
-__device__ __forceinline__ DirGeom dir_geom(const int32_t* ids, uint32_t V, uint32_t nb) {
-  DirGeom g;
-  g.lo = (uint32_t)ids[0] ^ kBias;
-  const uint32_t span = ((uint32_t)ids[V - 1] ^ kBias) - g.lo;
-  uint32_t sh = 0;
-  while (sh < 32 && (span >> sh) >= nb) ++sh;
-  g.shift = sh;
-  return g;
-}
-__device__ __forceinline__ uint32_t dir_bucket(DirGeom g, int32_t id) {
-  const uint32_t off = ((uint32_t)id ^ kBias) - g.lo;
-  return g.shift >= 32 ? 0u : (off >> g.shift);
-}
-
-__global__ void k_directory(Ctl* __restrict__ ctl) {
-  const uint32_t V = ctl->V, nb = ctl->dir_buckets;
-  if (V == 0) return;
-  const int32_t* __restrict__ ids = ctl->node_ids;
-  int32_t* __restrict__ dir = ctl->dir;
-  const DirGeom g = dir_geom(ids, V, nb);
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < V; r += gridDim.x * blockDim.x) {
-    const uint32_t br = dir_bucket(g, ids[r]);
-    const uint32_t from = r == 0 ? 0u : dir_bucket(g, ids[r - 1]) + 1;
-    for (uint32_t k = from; k <= br; ++k) dir[k] = (int32_t)r;
-    if (r == V - 1)
-      for (uint32_t k = br + 1; k <= nb; ++k) dir[k] = (int32_t)V;
+// ---------------------------------------------------------- block tables --
+// blk[k] = map[32k], with kBlkDense set when the 32 entries from 32k are
+// consecutive node indices (no node of the other kind lies between them);
+// then map[j] = (blk[j >> 5] & ~kBlkDense) + (j & 31) without reading map.
+__global__ void k_rank_blocks(Ctl* __restrict__ ctl) {
+  const uint32_t Vs = ctl->Vs, Vd = ctl->Vd;
+  const uint32_t ns = (Vs + 31) >> kBlkShift, nd = (Vd + 31) >> kBlkShift;
+  const uint32_t nmax = ns > nd ? ns : nd;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nmax; k += gridDim.x * blockDim.x) {
+    if (k < ns) {
+      const uint32_t a = k << kBlkShift, e = min(a + 32, Vs) - 1;
+      const int32_t r0 = ctl->src_rank[a], r1 = ctl->src_rank[e];
+      ctl->src_blk[k] = (uint32_t)r0 | ((uint32_t)(r1 - r0) == e - a ? kBlkDense : 0u);
+    }
+    if (k < nd) {
+      const uint32_t a = k << kBlkShift, e = min(a + 32, Vd) - 1;
+      const int32_t r0 = ctl->dst_rank[a], r1 = ctl->dst_rank[e];
+      ctl->dst_blk[k] = (uint32_t)r0 | ((uint32_t)(r1 - r0) == e - a ? kBlkDense : 0u);
+    }
   }
 }
 
-void launch_directory(Ctl* ctl, uint32_t V, cudaStream_t s) {
-  if (V == 0) return;
-  uint32_t grid = (V + 255) / 256;
+void launch_rank_blocks(Ctl* ctl, uint32_t Vs, uint32_t Vd, cudaStream_t s) {
+  const uint32_t n = ((Vs > Vd ? Vs : Vd) + 31) >> kBlkShift;
+  if (n == 0) return;
+  uint32_t grid = (n + 255) / 256;
   if (grid > 4096) grid = 4096;
-  k_directory<<<grid, 256, 0, s>>>(ctl);
-}
-
-// ------------------------------------------------------------ rank bitmap -
-// Dense ID ranges: sector k covers biased IDs [id_lo + 224 k, id_lo + 224 (k+1));
-// word 0 holds the number of nodes below the sector and words 1..7 hold one
-// bit per ID.  node index(x) = word0 + set bits below x in its sector.
-__global__ void k_rank_bitmap(Ctl* __restrict__ ctl) {
-  const uint32_t V = ctl->V, ns = ctl->bitmap_sectors, lo = ctl->id_lo;
-  if (V == 0) return;
-  const int32_t* __restrict__ ids = ctl->node_ids;
-  uint32_t* __restrict__ bm = ctl->bitmap;
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < V; r += gridDim.x * blockDim.x) {
-    const uint32_t off = ((uint32_t)ids[r] ^ kBias) - lo;
-    const uint32_t sec = off / kSectorIds, o = off - sec * kSectorIds;
-    atomicOr(&bm[(size_t)sec * 8 + 1 + (o >> 5)], 1u << (o & 31));
-    const uint32_t from =
-        r == 0 ? 0u : (((uint32_t)ids[r - 1] ^ kBias) - lo) / kSectorIds + 1;
-    for (uint32_t k = from; k <= sec; ++k) bm[(size_t)k * 8] = r;
-    if (r == V - 1)
-      for (uint32_t k = sec + 1; k < ns; ++k) bm[(size_t)k * 8] = V;
-  }
-}
-
-void launch_rank_bitmap(Ctl* ctl, uint32_t V, cudaStream_t s) {
-  if (V == 0) return;
-  uint32_t grid = (V + 255) / 256;
-  if (grid > 4096) grid = 4096;
-  k_rank_bitmap<<<grid, 256, 0, s>>>(ctl);
+  k_rank_blocks<<<grid, 256, 0, s>>>(ctl);
 }
 
 // ---------------------------------------------------------------- remap ---
-// out_nbr: dst ID -> node index; in_nbr: source-run index -> node index
-// (src_rank).  Eight edges per thread so that eight independent random reads
-// are in flight at once.
-__device__ __forceinline__ int32_t bitmap_index(const uint32_t* __restrict__ bm, uint32_t lo,
-                                                int32_t x, uint32_t* err) {
-  const uint32_t off = ((uint32_t)x ^ kBias) - lo;
-  const uint32_t sec = off / kSectorIds, o = off - sec * kSectorIds;
-  const uint4* p = reinterpret_cast<const uint4*>(bm + (size_t)sec * 8);
-  const uint4 h0 = __ldg(p), h1 = __ldg(p + 1);
-  const uint32_t w[7] = {h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-  const uint32_t wi = o >> 5, bi = o & 31;
-  uint32_t r = h0.x;
-  uint32_t cur = 0;
-#pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    if ((uint32_t)k < wi) r += __popc(w[k]);
-    if ((uint32_t)k == wi) cur = w[k];
-  }
-  r += __popc(cur & ((1u << bi) - 1u));
-  if (!((cur >> bi) & 1u)) atomicOr(err, kErrRemap);
-  return (int32_t)r;
+// out_nbr: dst-run index -> node index; in_nbr: source-run index -> node
+// index.  Eight edges per thread; the block tables are small enough to stay
+// in L2, and the full maps are read only inside blocks with a gap.
+__device__ __forceinline__ int32_t map_index(const uint32_t* __restrict__ blk,
+                                             const int32_t* __restrict__ map, uint32_t j) {
+  const uint32_t p = __ldg(blk + (j >> kBlkShift));
+  if (p & kBlkDense) return (int32_t)((p & ~kBlkDense) + (j & 31));
+  return __ldg(map + j);
 }
 
-__device__ __forceinline__ int32_t find_index(const int32_t* __restrict__ ids,
-                                              const int32_t* __restrict__ dir, DirGeom g,
-                                              uint32_t nb, uint32_t V, int32_t x,
-                                              uint32_t* err) {
-  uint32_t b = dir_bucket(g, x);
-  if (b >= nb) b = nb - 1;  // only for an ID outside [ids[0], ids[V-1]] (a bug)
-  uint32_t lo = (uint32_t)__ldg(dir + b), hi = (uint32_t)__ldg(dir + b + 1);
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (__ldg(ids + mid) < x) lo = mid + 1;
-    else hi = mid;
-  }
-  if (lo >= V || ids[lo] != x) {
-    atomicOr(err, kErrRemap);
-    return 0;
-  }
-  return (int32_t)lo;
-}
-
-template <bool kBitmap>
 __global__ void __launch_bounds__(256) k_remap(Ctl* __restrict__ ctl) {
-  const uint32_t E = ctl->E, V = ctl->V;
-  if (V == 0) return;
-  const int32_t* __restrict__ ids = ctl->node_ids;
-  const int32_t* __restrict__ dir = ctl->dir;
-  const uint32_t* __restrict__ bm = ctl->bitmap;
-  const uint32_t lo = ctl->id_lo;
-  const int32_t* __restrict__ rank = ctl->src_rank;
+  const uint32_t E = ctl->E;
+  const uint32_t* __restrict__ sb = ctl->src_blk;
+  const uint32_t* __restrict__ db = ctl->dst_blk;
+  const int32_t* __restrict__ sr = ctl->src_rank;
+  const int32_t* __restrict__ dr = ctl->dst_rank;
   int32_t* __restrict__ on = ctl->out_nbr;
   int32_t* __restrict__ in = ctl->in_nbr;
-  uint32_t* err = &ctl->err;
-  const uint32_t nb = ctl->dir_buckets;
-  DirGeom g{0, 0};
-  if (!kBitmap) g = dir_geom(ids, V, nb);
-  auto lookup = [&](int32_t x) -> int32_t {
-    return kBitmap ? bitmap_index(bm, lo, x, err) : find_index(ids, dir, g, nb, V, x, err);
-  };
   const uint32_t E8 = E / 8;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < E8; q += stride) {
@@ -461,22 +430,22 @@ __global__ void __launch_bounds__(256) k_remap(Ctl* __restrict__ ctl) {
     const int4* in4 = reinterpret_cast<const int4*>(in) + 2 * (size_t)q;
     int4 a0 = __ldcs(on4), a1 = __ldcs(on4 + 1);
     int4 b0 = __ldcs(in4), b1 = __ldcs(in4 + 1);
-    b0.x = __ldg(rank + b0.x);
-    b0.y = __ldg(rank + b0.y);
-    b0.z = __ldg(rank + b0.z);
-    b0.w = __ldg(rank + b0.w);
-    b1.x = __ldg(rank + b1.x);
-    b1.y = __ldg(rank + b1.y);
-    b1.z = __ldg(rank + b1.z);
-    b1.w = __ldg(rank + b1.w);
-    a0.x = lookup(a0.x);
-    a0.y = lookup(a0.y);
-    a0.z = lookup(a0.z);
-    a0.w = lookup(a0.w);
-    a1.x = lookup(a1.x);
-    a1.y = lookup(a1.y);
-    a1.z = lookup(a1.z);
-    a1.w = lookup(a1.w);
+    a0.x = map_index(db, dr, a0.x);
+    a0.y = map_index(db, dr, a0.y);
+    a0.z = map_index(db, dr, a0.z);
+    a0.w = map_index(db, dr, a0.w);
+    a1.x = map_index(db, dr, a1.x);
+    a1.y = map_index(db, dr, a1.y);
+    a1.z = map_index(db, dr, a1.z);
+    a1.w = map_index(db, dr, a1.w);
+    b0.x = map_index(sb, sr, b0.x);
+    b0.y = map_index(sb, sr, b0.y);
+    b0.z = map_index(sb, sr, b0.z);
+    b0.w = map_index(sb, sr, b0.w);
+    b1.x = map_index(sb, sr, b1.x);
+    b1.y = map_index(sb, sr, b1.y);
+    b1.z = map_index(sb, sr, b1.z);
+    b1.w = map_index(sb, sr, b1.w);
     int4* on4w = reinterpret_cast<int4*>(on) + 2 * (size_t)q;
     int4* in4w = reinterpret_cast<int4*>(in) + 2 * (size_t)q;
     __stcs(on4w, a0);
@@ -485,21 +454,19 @@ __global__ void __launch_bounds__(256) k_remap(Ctl* __restrict__ ctl) {
     __stcs(in4w + 1, b1);
   }
   for (uint32_t e = E8 * 8 + blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride) {
-    on[e] = lookup(on[e]);
-    in[e] = rank[in[e]];
+    on[e] = map_index(db, dr, (uint32_t)on[e]);
+    in[e] = map_index(sb, sr, (uint32_t)in[e]);
   }
 }
 
-void launch_remap(Ctl* ctl, uint32_t E, uint32_t mode, cudaStream_t s) {
+void launch_remap(Ctl* ctl, uint32_t E, cudaStream_t s) {
   if (E == 0) return;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   uint32_t want = (E / 8 + 255) / 256 + 1;
   uint32_t cap = (uint32_t)sms * 8;
-  const uint32_t grid = want < cap ? want : cap;
-  if (mode == kRankBitmap) k_remap<true><<<grid, 256, 0, s>>>(ctl);
-  else k_remap<false><<<grid, 256, 0, s>>>(ctl);
+  k_remap<<<want < cap ? want : cap, 256, 0, s>>>(ctl);
 }
 
 // -------------------------------------------------------------- degrees ---

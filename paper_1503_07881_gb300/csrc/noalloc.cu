@@ -10,7 +10,7 @@
 // file-scope __device__ array of fixed size, and the caller passes the output
 // buffers.  It allocates no device or pinned host memory.
 //
-// The scratch array (g_noalloc_scratch, about 30 MB) exists once on every GPU
+// The scratch array (g_noalloc_scratch, about 41 MB) exists once on every GPU
 // that loads this library and stays there until the process exits.  Its
 // address is looked up once per device (cudaGetSymbolAddress) with that
 // device current; that lookup happens on the first call on a device, which
@@ -37,11 +37,11 @@ namespace {
 constexpr uint32_t kMaxRows = RINGO_NOALLOC_MAX_ROWS;
 constexpr size_t kA = 256;
 constexpr size_t up(size_t x) { return (x + kA - 1) & ~(kA - 1); }
+constexpr size_t up4(size_t x) { return (x + 3) & ~(size_t)3; }
 constexpr size_t kTiles = (kMaxRows + kSortTile - 1) / kSortTile;
 constexpr size_t kMergeTiles = (2 * (size_t)kMaxRows + kMergeTile - 1) / kMergeTile + 1;
-// directory buckets for at most 2 * kMaxRows merge items, about 32 per bucket
-constexpr size_t kMaxBuckets = 1u << 17;
-static_assert(kMaxBuckets >= (2 * (size_t)kMaxRows) / 32 + 1, "directory too small");
+// rank maps of at most kMaxRows sources and destinations, and their tables
+constexpr size_t kRankWords = 2 * up4(kMaxRows) + 2 * up4((kMaxRows + 31) / 32);
 
 constexpr size_t kOffCtl = 0;
 constexpr size_t kOffKeysA = up(kOffCtl + sizeof(Ctl));
@@ -53,8 +53,10 @@ constexpr size_t kOffSc1 = up(kOffSc0 + 8 * kTiles);
 constexpr size_t kOffSc2 = up(kOffSc1 + 8 * kTiles);
 constexpr size_t kOffUsrc = up(kOffSc2 + 8 * kMergeTiles);
 constexpr size_t kOffUsrcStart = up(kOffUsrc + 4 * ((size_t)kMaxRows + 1));
-constexpr size_t kOffRankDir = up(kOffUsrcStart + 4 * ((size_t)kMaxRows + 1));
-constexpr size_t kScratchBytes = up(kOffRankDir + 4 * ((size_t)kMaxRows + kMaxBuckets + 1));
+constexpr size_t kOffUdst = up(kOffUsrcStart + 4 * ((size_t)kMaxRows + 1));
+constexpr size_t kOffUdstStart = up(kOffUdst + 4 * ((size_t)kMaxRows + 1));
+constexpr size_t kOffRanks = up(kOffUdstStart + 4 * ((size_t)kMaxRows + 1));
+constexpr size_t kScratchBytes = up(kOffRanks + 4 * kRankWords);
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -84,12 +86,6 @@ int scratch_address(unsigned char** out) {
   }
   *out = g_scratch_addr[dev];
   return RINGO_OK;
-}
-
-uint32_t pow2_at_least(uint64_t x) {
-  uint64_t p = 1;
-  while (p < x) p <<= 1;
-  return (uint32_t)p;
 }
 
 }  // namespace
@@ -152,36 +148,16 @@ extern "C" int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* d
   h.scan_status[2] = (uint64_t*)(ws + kOffSc2);
   h.usrc = (int32_t*)(ws + kOffUsrc);
   h.usrc_start = (int32_t*)(ws + kOffUsrcStart);
+  h.udst = (int32_t*)(ws + kOffUdst);
+  h.udst_start = (int32_t*)(ws + kOffUdstStart);
   h.out_nbr = out_nbr;
   h.in_nbr = in_nbr;
-  h.id_lo = 0xFFFFFFFFu;
-  h.id_hi = 0;
   // state left by the previous call: the control block is rewritten whole,
   // status region 0 and the scan statuses are cleared
   NA_TRY(cudaMemcpyAsync(dctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
   NA_TRY(cudaMemsetAsync(ws + kOffSt0, 0, 4 * (size_t)tiles * kRadix, s));
   NA_TRY(cudaMemsetAsync(ws + kOffSc0, 0, kOffUsrc - kOffSc0, s));
-#define NA_LAUNCH(name, call)                                                  \
-  do {                                                                         \
-    {                                                                          \
-      ProfScope _ps(name, s);                                                  \
-      call;                                                                    \
-    }                                                                          \
-    cudaError_t _e = cudaGetLastError();                                       \
-    if (_e != cudaSuccess) {                                                   \
-      set_error(std::string("launch ") + name + ": " + cudaGetErrorString(_e)); \
-      return RINGO_ECUDA;                                                      \
-    }                                                                          \
-  } while (0)
-  NA_LAUNCH("histogram", launch_histogram(dctl, n, s));
-  NA_LAUNCH("plan", launch_plan(dctl, 0, s));
-  for (int p = 0; p < kOutPasses; ++p)
-    NA_LAUNCH("onesweep", launch_onesweep(dctl, 0, p, p, tiles, s));
-  NA_LAUNCH("dedup", launch_dedup(dctl, tiles, s));
-  NA_LAUNCH("plan", launch_plan(dctl, 1, s));
-  for (int p = 0; p < kInPasses; ++p)
-    NA_LAUNCH("onesweep", launch_onesweep(dctl, 1, p, kOutPasses + p, tiles, s));
-  NA_LAUNCH("dst_runs", launch_dst_runs(dctl, tiles, s));
+  if ((rc = enqueue_phase1(dctl, n, s)) != RINGO_OK) return rc;
   NA_TRY(cudaMemcpyAsync(&h, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
   NA_TRY(cudaStreamSynchronize(s));
   if (h.err) {
@@ -194,34 +170,25 @@ extern "C" int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* d
               "distinct destinations) of this table; 2 * nrows always suffices");
     return RINGO_ERANGE;
   }
-  // ID -> index through the directory only (the rank bitmap's size depends
-  // on the ID range and need not fit the fixed scratch array)
-  const uint32_t nb = pow2_at_least(cap / 32 + 1);
-  int32_t* rank_dir = (int32_t*)(ws + kOffRankDir);
+  int32_t* ranks = (int32_t*)(ws + kOffRanks);
   h.node_ids = node_ids;
   h.out_off = out_off;
   h.in_off = in_off;
-  h.src_rank = rank_dir;
-  h.dir = rank_dir + h.Vs;
-  h.dir_buckets = nb;
-  h.rank_mode = kRankDirectory;
-  h.bitmap = nullptr;
-  h.bitmap_sectors = 0;
+  h.src_rank = ranks;
+  h.dst_rank = ranks + up4(h.Vs);
+  h.src_blk = (uint32_t*)(h.dst_rank + up4(h.Vd));
+  h.dst_blk = h.src_blk + up4((h.Vs + 31) / 32);
   NA_TRY(cudaMemcpyAsync(dctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-  const uint32_t mgrid = (uint32_t)((cap + kMergeTile - 1) / kMergeTile);
-  NA_LAUNCH("merge", launch_merge(dctl, mgrid, s));
-  NA_LAUNCH("directory", launch_directory(dctl, (uint32_t)cap, s));
-  NA_LAUNCH("remap", launch_remap(dctl, h.E, kRankDirectory, s));
+  if ((rc = enqueue_phase2(dctl, h.Vs, h.Vd, h.E, s)) != RINGO_OK) return rc;
   NA_TRY(cudaMemcpyAsync(&h, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
   NA_TRY(cudaStreamSynchronize(s));
-#undef NA_LAUNCH
 #undef NA_TRY
   if (h.err & (kErrLookback | kErrScan)) {
     set_error("ringo_table_to_graph_noalloc: a bounded device wait expired");
     return RINGO_ETIMEOUT;
   }
   if (h.err & kErrRemap) {
-    set_error("ringo_table_to_graph_noalloc: internal error in the ID -> index remap");
+    set_error("ringo_table_to_graph_noalloc: internal error in the remap");
     return RINGO_ECUDA;
   }
   *num_nodes = h.V;

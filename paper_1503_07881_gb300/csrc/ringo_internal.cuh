@@ -2,14 +2,19 @@
 //
 // Pipeline (the paper's sort-first conversion, Section 3.4, re-designed for
 // one GB300): the two ID columns are packed into 64-bit keys (biased src in
-// the high word, biased dst in the low word) and LSD radix sorted; adjacent
-// duplicates are dropped while source runs are counted; the surviving edges,
-// re-keyed as (dst, source-run index), are stably sorted on the dst bits; the
-// destination runs are counted; the sorted source and destination ID lists are
-// merged into the node list; finally neighbour IDs are turned into node
-// indices.  Every step is a kernel below; sizes that only the device knows
-// (E, V, which radix passes are trivial) live in the device control block
-// `Ctl`, so the launch sequence needs no host decisions between kernels.
+// the high word, biased dst in the low word) and LSD radix sorted.  After the
+// four passes over the dst digits the keys are in dst order; one streaming
+// kernel then replaces each dst by its destination-run index (monotone, so
+// the order is kept) and emits the distinct destination IDs.  The four src
+// passes follow.  Adjacent duplicates are dropped while source runs are
+// counted; the surviving edges, re-keyed as (dst-run, source-run), are stably
+// sorted on the dst-run half; destination-run starts are recorded; the two
+// sorted ID lists are merged into the node list; finally both neighbour
+// arrays go from run indices to node indices through monotone maps, almost
+// always answered by a small block table that stays in L2.  Sizes that only
+// the device knows (E, V, which radix passes are trivial) live in the device
+// control block `Ctl`, so the launch sequence needs no host decisions
+// between kernels except the one sync that sizes the node arrays.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,11 +43,7 @@ constexpr uint32_t kBias = 0x80000000u;  // int32 -> uint32 preserving order
 // Ctl::err bits
 constexpr uint32_t kErrLookback = 1u;   // a radix look-back wait gave up
 constexpr uint32_t kErrScan = 2u;       // a scan look-back wait gave up
-constexpr uint32_t kErrRemap = 4u;      // an ID missing from node_ids (bug)
-
-constexpr uint32_t kRankDirectory = 0;
-constexpr uint32_t kRankBitmap = 1;
-constexpr uint32_t kSectorIds = 224;  // ID bits per 32-byte rank sector
+constexpr uint32_t kErrRemap = 4u;      // a run index outside its map (bug)
 
 // A bounded wait: about a second at most before the kernel records an error.
 constexpr uint32_t kSpinLimit = 1u << 21;
@@ -94,7 +95,7 @@ struct Ctl {
   uint32_t n_rows;
   uint32_t E, Vs, Vd, V;
   uint32_t err;
-  uint32_t scan_counter[4];   // dynamic tile counters: dedup, dst runs, merge
+  uint32_t scan_counter[4];   // dynamic tile counters: dedup, dst_rank, merge
   // inputs
   const int32_t* src;
   const int32_t* dst;
@@ -103,22 +104,18 @@ struct Ctl {
   uint64_t* keysB;            // [n_rows + 1]
   uint32_t* status[2];        // [status_rows][kRadix] each, alternating passes
   uint32_t status_rows;
-  uint64_t* scan_status[3];   // [tiles] each: dedup, dst runs, merge
+  uint64_t* scan_status[3];   // [tiles] each: dedup, dst_rank, merge
   int32_t* usrc;              // [n_rows + 1] distinct src IDs, ascending
-  int32_t* usrc_start;        // [n_rows + 1] first edge of each src run
-  int32_t* udst;              // distinct dst IDs (placed in the spare buffer)
-  int32_t* udst_start;        // first in-edge of each dst run
-  int32_t* src_rank;          // [Vs] node index of usrc[i]
-  uint32_t id_lo, id_hi;      // smallest / largest biased ID in either column
-  // ID -> node index, one of two structures (rank_mode):
-  //  kRankDirectory: dir[k] = first node at or above bucket k of the ID range
-  //  kRankBitmap:    32-byte sectors of {node count below the sector, 224 ID
-  //                  bits}; one sector read answers a lookup
-  uint32_t rank_mode;
-  int32_t* dir;               // [dir_buckets + 1]
-  uint32_t dir_buckets;       // power of two
-  uint32_t* bitmap;           // [bitmap_sectors * 8]
-  uint32_t bitmap_sectors;
+  int32_t* usrc_start;        // [n_rows + 1] first out-edge of each source run
+  int32_t* udst;              // [n_rows + 1] distinct dst IDs, ascending
+  int32_t* udst_start;        // [n_rows + 1] first in-edge of each destination run
+  PassDesc rank_step;         // dst -> dst-run index, between out-sort passes 3 and 4
+  // run index -> node index (both monotone), with block tables:
+  //   blk[k] = map[32k] | 0x80000000 when map[32k .. 32k+31] has no gap
+  int32_t* src_rank;          // [Vs]
+  int32_t* dst_rank;          // [Vd]
+  uint32_t* src_blk;          // [ceil(Vs / 32)]
+  uint32_t* dst_blk;          // [ceil(Vd / 32)]
   // outputs
   int32_t* out_nbr;           // [n_rows] capacity
   int32_t* in_nbr;            // [n_rows] capacity
@@ -129,22 +126,32 @@ struct Ctl {
   SortCtl in_sort;
 };
 
+constexpr uint32_t kBlkDense = 0x80000000u;
+constexpr int kBlkShift = 5;  // 32 map entries per block-table word
+
 // --------------------------------------------------------- host launchers --
 // Each enqueues one kernel on `s`; `ctl` is the device copy of the block.
 void launch_histogram(Ctl* ctl, uint32_t n_rows, cudaStream_t s);
 void launch_plan(Ctl* ctl, int which, cudaStream_t s);
 void launch_onesweep(Ctl* ctl, int which, int pass, int gpass, uint32_t grid, cudaStream_t s);
+void launch_dst_rank(Ctl* ctl, uint32_t grid, cudaStream_t s);
 void launch_dedup(Ctl* ctl, uint32_t grid, cudaStream_t s);
-void launch_dst_runs(Ctl* ctl, uint32_t grid, cudaStream_t s);
+void launch_dst_runs(Ctl* ctl, uint32_t n_rows, cudaStream_t s);
 void launch_merge(Ctl* ctl, uint32_t grid, cudaStream_t s);
-void launch_directory(Ctl* ctl, uint32_t V, cudaStream_t s);
-void launch_rank_bitmap(Ctl* ctl, uint32_t V, cudaStream_t s);
-void launch_remap(Ctl* ctl, uint32_t E, uint32_t mode, cudaStream_t s);
+void launch_rank_blocks(Ctl* ctl, uint32_t Vs, uint32_t Vd, cudaStream_t s);
+void launch_remap(Ctl* ctl, uint32_t E, cudaStream_t s);
 void launch_degrees(const int32_t* node_ids, const int64_t* off, uint32_t V,
                     const int32_t* ids, uint32_t n, int64_t* deg, cudaStream_t s);
 int launch_topk(const int32_t* node_ids, const int64_t* off, uint32_t V, uint32_t k,
                 int32_t* d_ids, int64_t* d_degs, void* d_scratch, size_t scratch_bytes,
                 cudaStream_t s);
 size_t topk_scratch_bytes(uint32_t V, uint32_t k);
+
+// The launch sequence, shared by every entry point (pipeline.cu).
+//   phase 1: histogram .. destination runs; afterwards E, Vs, Vd are final
+//   phase 2: merge, block tables, remap; needs node arrays and rank maps set
+//            in the control block (by the caller, after reading Vs and Vd)
+int enqueue_phase1(Ctl* dctl, uint32_t n_rows, cudaStream_t s);
+int enqueue_phase2(Ctl* dctl, uint32_t Vs, uint32_t Vd, uint32_t E, cudaStream_t s);
 
 }  // namespace ringo

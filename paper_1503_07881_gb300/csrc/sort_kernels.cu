@@ -22,11 +22,8 @@ namespace ringo {
 // Pass p looks at bits [8p, 8p+8) of key = bias(src) << 32 | bias(dst).
 constexpr int kHistThreads = 512;
 
-__device__ __forceinline__ void hist_row(uint32_t (*h)[kRadix], int32_t s, int32_t d,
-                                         uint32_t& lo, uint32_t& hi) {
+__device__ __forceinline__ void hist_row(uint32_t (*h)[kRadix], int32_t s, int32_t d) {
   const uint32_t sb = (uint32_t)s ^ kBias, db = (uint32_t)d ^ kBias;
-  lo = min(lo, min(sb, db));
-  hi = max(hi, max(sb, db));
   atomicAdd(&h[0][db & 0xFF], 1u);
   atomicAdd(&h[1][(db >> 8) & 0xFF], 1u);
   atomicAdd(&h[2][(db >> 16) & 0xFF], 1u);
@@ -39,13 +36,7 @@ __device__ __forceinline__ void hist_row(uint32_t (*h)[kRadix], int32_t s, int32
 
 __global__ void __launch_bounds__(kHistThreads) k_histogram(Ctl* __restrict__ ctl) {
   __shared__ uint32_t h[kOutPasses][kRadix];
-  __shared__ uint32_t s_lo, s_hi;
   for (int i = threadIdx.x; i < kOutPasses * kRadix; i += kHistThreads) (&h[0][0])[i] = 0;
-  if (threadIdx.x == 0) {
-    s_lo = 0xFFFFFFFFu;
-    s_hi = 0;
-  }
-  uint32_t lo = 0xFFFFFFFFu, hi = 0;
   __syncthreads();
   const int32_t* __restrict__ src = ctl->src;
   const int32_t* __restrict__ dst = ctl->dst;
@@ -61,28 +52,16 @@ __global__ void __launch_bounds__(kHistThreads) k_histogram(Ctl* __restrict__ ct
     for (size_t i = t0; i < n4; i += stride) {
       const int4 a = __ldcs(s4 + i);
       const int4 b = __ldcs(d4 + i);
-      hist_row(h, a.x, b.x, lo, hi);
-      hist_row(h, a.y, b.y, lo, hi);
-      hist_row(h, a.z, b.z, lo, hi);
-      hist_row(h, a.w, b.w, lo, hi);
+      hist_row(h, a.x, b.x);
+      hist_row(h, a.y, b.y);
+      hist_row(h, a.z, b.z);
+      hist_row(h, a.w, b.w);
     }
     done = n4 * 4;
   }
-  for (size_t i = done + t0; i < n; i += stride) hist_row(h, src[i], dst[i], lo, hi);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
-    hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMin(&s_lo, lo);
-    atomicMax(&s_hi, hi);
-  }
+  for (size_t i = done + t0; i < n; i += stride) hist_row(h, src[i], dst[i]);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    atomicMin(&ctl->id_lo, s_lo);
-    atomicMax(&ctl->id_hi, s_hi);
-  }
+
   for (int i = threadIdx.x; i < kOutPasses * kRadix; i += kHistThreads) {
     const uint32_t c = (&h[0][0])[i];
     if (c) atomicAdd(&ctl->out_sort.hist[0][0] + i, c);
@@ -104,9 +83,11 @@ void launch_histogram(Ctl* ctl, uint32_t n_rows, cudaStream_t s) {
 // device, which passes move keys: a pass whose digit is the same for every
 // key is the identity and is skipped.  Also fixes the ping-pong buffers.
 //   which = 0: out-sort of n_rows keys packed from the columns, digits at
-//              bits 0..63; buffers keysA, keysB.
+//              bits 0..63 (passes 0-3: dst, 4-7: src); between pass 3 and
+//              pass 4 the dst-rank step always runs (it also packs from the
+//              columns when every dst pass was skipped); buffers keysA/keysB.
 //   which = 1: in-sort of E keys held in the out-sort's spare buffer,
-//              digits at bits 32..63 (the dst half).
+//              digits at bits 32..63 (the dst-run half).
 __global__ void __launch_bounds__(kRadix) k_plan(Ctl* __restrict__ ctl, int which) {
   __shared__ uint32_t sw[kRadix / 32 + 1];
   __shared__ uint32_t trivial[kOutPasses];
@@ -138,8 +119,14 @@ __global__ void __launch_bounds__(kRadix) k_plan(Ctl* __restrict__ ctl, int whic
     sc.pass[p].out = nullptr;
   }
   for (int p = 0; p < npass; ++p) {
-    const bool last_chance = (p == npass - 1) && active == 0;
-    if (trivial[p] && !last_chance) continue;
+    if (which == 0 && p == 4) {
+      ctl->rank_step.in = cur;
+      ctl->rank_step.out = next;
+      ctl->rank_step.active = 1;
+      cur = next;
+      next = (next == b0) ? b1 : b0;
+    }
+    if (trivial[p]) continue;
     sc.pass[p].active = 1;
     sc.pass[p].in = cur;
     sc.pass[p].out = next;
