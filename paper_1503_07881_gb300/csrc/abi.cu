@@ -64,7 +64,9 @@ int make_empty(ringo_graph* g) {
 }
 
 struct WsLayout {
-  size_t ctl, keysA, keysB, st0, st1, sc0, sc1, sc2, usrc, usrc_start, udst, udst_start, total;
+  size_t ctl, keysA, keysB, st0, st1, ch0, ch1, sc0, sc1, sc2, usrc, usrc_start, udst, udst_start,
+      total;
+  size_t chunks, chunk_bytes;
 };
 
 WsLayout layout_for(uint32_t n) {
@@ -77,6 +79,10 @@ WsLayout layout_for(uint32_t n) {
   L.keysB = o; o = align_up(o + sizeof(uint64_t) * ((size_t)n + 1));
   L.st0 = o; o = align_up(o + sizeof(uint32_t) * tiles * kRadix);
   L.st1 = o; o = align_up(o + sizeof(uint32_t) * tiles * kRadix);
+  L.chunks = (tiles + kChunkTiles - 1) / kChunkTiles;
+  L.chunk_bytes = align_up(sizeof(uint32_t) * L.chunks * (2 * kRadix + 1));
+  L.ch0 = o; o = align_up(o + L.chunk_bytes);
+  L.ch1 = o; o = align_up(o + L.chunk_bytes);
   L.sc0 = o; o = align_up(o + sizeof(uint64_t) * tiles);
   L.sc1 = o; o = align_up(o + sizeof(uint64_t) * tiles);
   L.sc2 = o; o = align_up(o + sizeof(uint64_t) * mtiles);
@@ -129,6 +135,13 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
     hctl->status[0] = (uint32_t*)(ws + L.st0);
     hctl->status[1] = (uint32_t*)(ws + L.st1);
     hctl->status_rows = tiles;
+    for (int r = 0; r < 2; ++r) {
+      uint32_t* ch = (uint32_t*)(ws + (r ? L.ch1 : L.ch0));
+      hctl->chunk_agg[r] = ch;
+      hctl->chunk_inc[r] = ch + L.chunks * kRadix;
+      hctl->chunk_cnt[r] = ch + 2 * L.chunks * kRadix;
+    }
+    hctl->chunk_rows = (uint32_t)L.chunks;
     hctl->scan_status[0] = (uint64_t*)(ws + L.sc0);
     hctl->scan_status[1] = (uint64_t*)(ws + L.sc1);
     hctl->scan_status[2] = (uint64_t*)(ws + L.sc2);
@@ -150,6 +163,7 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
     TRY(cudaMemcpyAsync(dctl, hctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     // status region 0 must start clear; each pass clears the other region
     TRY(cudaMemsetAsync(ws + L.st0, 0, L.st1 - L.st0, s));
+    TRY(cudaMemsetAsync(ws + L.ch0, 0, L.chunk_bytes, s));
     TRY(cudaMemsetAsync(ws + L.sc0, 0, L.usrc - L.sc0, s));
     if ((rc = enqueue_phase1(dctl, n, s)) != RINGO_OK) goto done;
     TRY(cudaMemcpyAsync(hctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));

@@ -238,27 +238,32 @@ void launch_dst_rank(Ctl* ctl, uint32_t grid, cudaStream_t s) {
 // first in-edge udst_start[d] = k (udst_start[Vd] = E).  Every dst-run index
 // occurs, so no compaction is needed.
 __global__ void __launch_bounds__(256) k_dst_runs(Ctl* __restrict__ ctl) {
-  const uint32_t E = ctl->E;
+  const uint32_t E = ctl->E, Vd = ctl->Vd;
   const uint64_t* __restrict__ keys = ctl->in_sort.result;
   int32_t* __restrict__ in_nbr = ctl->in_nbr;
   int32_t* __restrict__ ustart = ctl->udst_start;
   const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t0 == 0) ustart[ctl->Vd] = (int32_t)E;
+  if (t0 == 0) ustart[Vd] = (int32_t)E;
+  // a dst-run index is always below Vd; anything else is recorded, not written
+  auto put = [&](uint32_t d, uint32_t k) {
+    if (d < Vd) ustart[d] = (int32_t)k;
+    else atomicOr(&ctl->err, kErrRemap);
+  };
   const uint32_t E2 = E / 2;
   for (uint32_t q = t0; q < E2; q += gridDim.x * blockDim.x) {
     const ulonglong2 kk = __ldcs(reinterpret_cast<const ulonglong2*>(keys) + q);
     const uint32_t k = 2 * q;
     const uint32_t d0 = (uint32_t)(kk.x >> 32), d1 = (uint32_t)(kk.y >> 32);
     const uint32_t dp = k ? (uint32_t)(keys[k - 1] >> 32) : 0xFFFFFFFFu;
-    if (k == 0 || d0 != dp) ustart[d0] = (int32_t)k;
-    if (d1 != d0) ustart[d1] = (int32_t)(k + 1);
+    if (k == 0 || d0 != dp) put(d0, k);
+    if (d1 != d0) put(d1, k + 1);
     reinterpret_cast<int2*>(in_nbr)[q] = make_int2((int32_t)(uint32_t)kk.x, (int32_t)(uint32_t)kk.y);
   }
   if ((E & 1) && t0 == 0) {
     const uint32_t k = E - 1;
     const uint64_t key = keys[k];
     const uint32_t d = (uint32_t)(key >> 32);
-    if (k == 0 || d != (uint32_t)(keys[k - 1] >> 32)) ustart[d] = (int32_t)k;
+    if (k == 0 || d != (uint32_t)(keys[k - 1] >> 32)) put(d, k);
     in_nbr[k] = (int32_t)(uint32_t)key;
   }
 }
@@ -409,54 +414,50 @@ void launch_rank_blocks(Ctl* ctl, uint32_t Vs, uint32_t Vd, cudaStream_t s) {
 // index.  Eight edges per thread; the block tables are small enough to stay
 // in L2, and the full maps are read only inside blocks with a gap.
 __device__ __forceinline__ int32_t map_index(const uint32_t* __restrict__ blk,
-                                             const int32_t* __restrict__ map, uint32_t j) {
+                                             const int32_t* __restrict__ map, uint32_t len,
+                                             uint32_t j, uint32_t* err) {
+  if (j >= len) {  // never for a correct run index: recorded, not read
+    atomicOr(err, kErrRemap);
+    return 0;
+  }
   const uint32_t p = __ldg(blk + (j >> kBlkShift));
   if (p & kBlkDense) return (int32_t)((p & ~kBlkDense) + (j & 31));
   return __ldg(map + j);
 }
 
-__global__ void __launch_bounds__(256) k_remap(Ctl* __restrict__ ctl) {
-  const uint32_t E = ctl->E;
-  const uint32_t* __restrict__ sb = ctl->src_blk;
-  const uint32_t* __restrict__ db = ctl->dst_blk;
-  const int32_t* __restrict__ sr = ctl->src_rank;
-  const int32_t* __restrict__ dr = ctl->dst_rank;
-  int32_t* __restrict__ on = ctl->out_nbr;
-  int32_t* __restrict__ in = ctl->in_nbr;
+// One direction of the remap, in place, eight entries per thread.
+__device__ __forceinline__ void remap_array(int32_t* __restrict__ a, uint32_t E,
+                                            const uint32_t* __restrict__ blk,
+                                            const int32_t* __restrict__ map, uint32_t len,
+                                            uint32_t* err) {
   const uint32_t E8 = E / 8;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < E8; q += stride) {
-    const int4* on4 = reinterpret_cast<const int4*>(on) + 2 * (size_t)q;
-    const int4* in4 = reinterpret_cast<const int4*>(in) + 2 * (size_t)q;
-    int4 a0 = __ldcs(on4), a1 = __ldcs(on4 + 1);
-    int4 b0 = __ldcs(in4), b1 = __ldcs(in4 + 1);
-    a0.x = map_index(db, dr, a0.x);
-    a0.y = map_index(db, dr, a0.y);
-    a0.z = map_index(db, dr, a0.z);
-    a0.w = map_index(db, dr, a0.w);
-    a1.x = map_index(db, dr, a1.x);
-    a1.y = map_index(db, dr, a1.y);
-    a1.z = map_index(db, dr, a1.z);
-    a1.w = map_index(db, dr, a1.w);
-    b0.x = map_index(sb, sr, b0.x);
-    b0.y = map_index(sb, sr, b0.y);
-    b0.z = map_index(sb, sr, b0.z);
-    b0.w = map_index(sb, sr, b0.w);
-    b1.x = map_index(sb, sr, b1.x);
-    b1.y = map_index(sb, sr, b1.y);
-    b1.z = map_index(sb, sr, b1.z);
-    b1.w = map_index(sb, sr, b1.w);
-    int4* on4w = reinterpret_cast<int4*>(on) + 2 * (size_t)q;
-    int4* in4w = reinterpret_cast<int4*>(in) + 2 * (size_t)q;
-    __stcs(on4w, a0);
-    __stcs(on4w + 1, a1);
-    __stcs(in4w, b0);
-    __stcs(in4w + 1, b1);
+    const int4* p4 = reinterpret_cast<const int4*>(a) + 2 * (size_t)q;
+    int4 x0 = __ldcs(p4), x1 = __ldcs(p4 + 1);
+    x0.x = map_index(blk, map, len, (uint32_t)x0.x, err);
+    x0.y = map_index(blk, map, len, (uint32_t)x0.y, err);
+    x0.z = map_index(blk, map, len, (uint32_t)x0.z, err);
+    x0.w = map_index(blk, map, len, (uint32_t)x0.w, err);
+    x1.x = map_index(blk, map, len, (uint32_t)x1.x, err);
+    x1.y = map_index(blk, map, len, (uint32_t)x1.y, err);
+    x1.z = map_index(blk, map, len, (uint32_t)x1.z, err);
+    x1.w = map_index(blk, map, len, (uint32_t)x1.w, err);
+    int4* w4 = reinterpret_cast<int4*>(a) + 2 * (size_t)q;
+    __stcs(w4, x0);
+    __stcs(w4 + 1, x1);
   }
-  for (uint32_t e = E8 * 8 + blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride) {
-    on[e] = map_index(db, dr, (uint32_t)on[e]);
-    in[e] = map_index(sb, sr, (uint32_t)in[e]);
-  }
+  for (uint32_t e = E8 * 8 + blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride)
+    a[e] = map_index(blk, map, len, (uint32_t)a[e], err);
+}
+
+// When every node is a source (Vs == V) the source-run index already is the
+// node index and in_nbr is left as it is; likewise out_nbr when Vd == V.
+__global__ void __launch_bounds__(256) k_remap(Ctl* __restrict__ ctl) {
+  const uint32_t E = ctl->E, V = ctl->V, Vs = ctl->Vs, Vd = ctl->Vd;
+  uint32_t* err = &ctl->err;
+  if (Vd != V) remap_array(ctl->out_nbr, E, ctl->dst_blk, ctl->dst_rank, Vd, err);
+  if (Vs != V) remap_array(ctl->in_nbr, E, ctl->src_blk, ctl->src_rank, Vs, err);
 }
 
 void launch_remap(Ctl* ctl, uint32_t E, cudaStream_t s) {

@@ -31,6 +31,8 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys
 constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kChunkShift = 5;               // 32 tiles per look-back chunk
+constexpr int kChunkTiles = 1 << kChunkShift;
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
@@ -104,6 +106,12 @@ struct Ctl {
   uint64_t* keysB;            // [n_rows + 1]
   uint32_t* status[2];        // [status_rows][kRadix] each, alternating passes
   uint32_t status_rows;
+  // chunk level of the radix look-back (kChunkTiles tiles per chunk), two
+  // regions alternating with the passes like `status`:
+  uint32_t* chunk_agg[2];     // [chunks][kRadix] digit counts added by the chunk's tiles
+  uint32_t* chunk_inc[2];     // [chunks][kRadix] kStInc | inclusive prefix, once known
+  uint32_t* chunk_cnt[2];     // [chunks] tiles that have added their counts
+  uint32_t chunk_rows;
   uint64_t* scan_status[3];   // [tiles] each: dedup, dst_rank, merge
   int32_t* usrc;              // [n_rows + 1] distinct src IDs, ascending
   int32_t* usrc_start;        // [n_rows + 1] first out-edge of each source run

@@ -2,15 +2,15 @@
 //
 // The paper's conversion sorts copies of the source and destination columns
 // (Section 3.4, sort-first).  Here both columns are sorted at once as packed
-// 64-bit keys with a onesweep radix sort (Adinets & Merrill 2022): one kernel
+// 64-bit keys with onesweep radix passes (Adinets & Merrill 2022): one kernel
 // reads the columns once and builds the digit histograms of every pass; then
-// each pass is a single kernel that ranks a 4096-key tile in shared memory
-// with warp match/ballot digit counts, obtains its global digit offsets from
-// a decoupled look-back over the tiles before it, and scatters the tile,
-// staged in digit order in shared memory, with coalesced stores.
+// each pass is a single kernel that brings a 4096-key tile into shared memory
+// with a bulk asynchronous copy, counts and ranks its digits with warp-level
+// peer masks, obtains the global digit offsets from a two-level decoupled
+// look-back (tiles within a 32-tile chunk, then chunk aggregates), and
+// scatters the tile, staged in digit order, with coalesced stores.
 #include <cuda_runtime.h>
 #include <stdint.h>
-#include <stdlib.h>
 
 #include "device_util.cuh"
 #include "ringo_internal.cuh"
@@ -165,417 +165,293 @@ void launch_plan(Ctl* ctl, int which, cudaStream_t s) {
 // is held by a running block that never waits on a larger tile, so the
 // waits always end.
 
-// Decoupled look-back for one digit: the count of digit `d` in tiles
-// [0, tile).  Reads kLookWindow predecessor statuses per round trip, adding
-// aggregates until it meets an inclusive prefix; an unpublished status is
-// re-polled with backoff.  Bounded: gives up after kSpinLimit polls, or once
-// another block has recorded an error.
-constexpr int kLookWindow = 16;
-__device__ __forceinline__ uint32_t digit_lookback(const uint32_t* __restrict__ st,
-                                                   uint32_t tile, uint32_t d, Ctl* ctl) {
-  uint32_t excl = 0;
-  int64_t j = (int64_t)tile - 1;
-  uint32_t spins = 0;
+// Two-level decoupled look-back for digit d of `tile`: first over the
+// earlier tiles of the tile's own chunk (their aggregates or an inclusive
+// prefix), then over earlier chunks: a chunk whose tiles have all added their
+// counts contributes its aggregate, a chunk whose inclusive prefix is known
+// ends the walk.  A chunk's aggregate is complete soon after its tiles have
+// counted, so no wait follows the chain of inclusive prefixes tile by tile.
+// Bounded like every wait here.
+__device__ __forceinline__ uint32_t digit_lookback2(const uint32_t* __restrict__ st,
+                                                    const uint32_t* __restrict__ cagg,
+                                                    const uint32_t* __restrict__ cinc,
+                                                    const uint32_t* __restrict__ ccnt,
+                                                    uint32_t tile, uint32_t ntiles, uint32_t d,
+                                                    Ctl* ctl) {
+  constexpr int W = kChunkTiles / 2;
   const volatile uint32_t* verr = &ctl->err;
-  while (j >= 0) {
-    uint32_t v[kLookWindow];
+  uint32_t excl = 0, spins = 0;
+  const uint32_t c = tile >> kChunkShift;
+  const uint32_t first = c << kChunkShift;
+  // 1. tiles [first, tile) of this chunk
+  int64_t j = (int64_t)tile - 1;
+  while (j >= (int64_t)first) {
+    uint32_t v[W];
 #pragma unroll
-    for (int k = 0; k < kLookWindow; ++k)
-      v[k] = (j - k >= 0) ? ld_relaxed_u32(st + (size_t)(j - k) * kRadix + d) : kStInc;
-    int k = 0;
-    bool done = false;
+    for (int k = 0; k < W; ++k)
+      v[k] = (j - k >= (int64_t)first) ? ld_relaxed_u32(st + (size_t)(j - k) * kRadix + d) : 0u;
+    int used = 0;
+    bool done = false, stall = false;
 #pragma unroll
-    for (int q = 0; q < kLookWindow; ++q) {
-      if (done || k != q) continue;
+    for (int q = 0; q < W; ++q) {
+      if (done || stall || j - q < (int64_t)first) continue;
       const uint32_t x = v[q];
-      if (x == 0) continue;  // not yet published: stop here
-      if (x & kStInc) {
+      if (x == 0) {
+        stall = true;
+      } else if (x & kStInc) {
         excl += x & ~kStInc;
         done = true;
       } else {
         excl += x - 1u;
-        k = q + 1;
+        used = q + 1;
       }
     }
-    if (done) break;
-    j -= k;
-    if (k < kLookWindow) {
+    if (done) return excl;
+    j -= used;
+    if (stall) {
       if (spin_backoff(spins) || ((spins & 255) == 0 && *verr)) {
         atomicOr(&ctl->err, kErrLookback);
-        break;
+        return excl;
       }
+    }
+  }
+  // 2. chunks c-1, c-2, ...
+  int64_t cc = (int64_t)c - 1;
+  while (cc >= 0) {
+    const uint32_t inc = ld_relaxed_u32(cinc + (size_t)cc * kRadix + d);
+    if (inc & kStInc) return excl + (inc & ~kStInc);
+    const uint32_t cnt = ld_acquire_u32(ccnt + cc);
+    const uint32_t need = min((uint32_t)kChunkTiles, ntiles - ((uint32_t)cc << kChunkShift));
+    if (cnt >= need) {
+      excl += ld_relaxed_u32(cagg + (size_t)cc * kRadix + d);
+      --cc;
+      continue;
+    }
+    if (spin_backoff(spins) || ((spins & 255) == 0 && *verr)) {
+      atomicOr(&ctl->err, kErrLookback);
+      return excl;
     }
   }
   return excl;
 }
 
-struct SweepSmem {
-  uint64_t buf[2][kSortTile];
+// The pass as used by default.  One 4096-key tile per block, four blocks per
+// SM.  Per tile:
+//   0. the tile arrives in shared memory by one bulk asynchronous copy
+//      (cp.async.bulk + mbarrier; the first pass copies the two columns);
+//   1. digit counts per warp (shared-memory reductions), published at once,
+//      also into the chunk aggregate of the two-level look-back;
+//   2. warp offsets within each digit plus the tile's digit starts;
+//   3. ranks: the lanes of a warp holding the same digit find each other
+//      through a shared peer mask (atomicOr of lane bits), the highest of
+//      them advances the warp's digit offset for the group;
+//   4. the keys move to their ranked places in the same buffer;
+//   5. two-level look-back;
+//   6. coalesced scatter of the staged tile.
+// Keys sit in registers only during step 4, so a block needs few registers.
+struct SweepV6Smem {
+  uint64_t keys[kSortTile];               // the tile: input, then staged in digit order
   uint32_t whist[kSortWarps][kRadix];
+  uint32_t mask[kSortWarps][kRadix + 1];  // slot kRadix: lanes past the end
   int32_t delta[kRadix];
-  uint32_t binstart[kRadix];
   uint32_t sw[kSortWarps + 1];
-  uint32_t next_tile[2];
-  uint32_t bulk_cnt[2];
+  uint32_t tile;
   uint32_t ok;
-  uint64_t bar[2];
+  uint64_t bar;
 };
 
-__device__ __forceinline__ void sweep_issue(SweepSmem& S, int b, uint32_t tile, uint32_t n,
-                                            const uint64_t* in, const int32_t* src,
-                                            const int32_t* dst, bool cols_bulk) {
-  const uint32_t base = tile * (uint32_t)kSortTile;
-  const uint32_t cnt = min((uint32_t)kSortTile, n - base);
-  uint32_t bulk, bytes;
-  if (in) {
-    bulk = cnt & ~1u;                    // 8-byte keys: an even count is 16-byte sized
-    bytes = bulk * 8u;
-  } else if (cols_bulk) {
-    bulk = cnt & ~3u;                    // 4-byte IDs: a multiple of 4
-    bytes = bulk * 8u;                   // both columns
-  } else {
-    bulk = 0;
-    bytes = 0;
-  }
-  S.bulk_cnt[b] = bulk;
-  fence_proxy_async_smem();
-  mbar_arrive_expect_tx(&S.bar[b], bytes);
-  if (bulk) {
-    if (in) {
-      bulk_g2s(&S.buf[b][0], in + base, bulk * 8u, &S.bar[b]);
-    } else {
-      int32_t* cols = reinterpret_cast<int32_t*>(&S.buf[b][0]);
-      bulk_g2s(cols, src + base, bulk * 4u, &S.bar[b]);
-      bulk_g2s(cols + kSortTile, dst + base, bulk * 4u, &S.bar[b]);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kSortThreads, 2)
-    k_onesweep_persistent(Ctl* __restrict__ ctl, int which, int pass, int gpass) {
+__global__ void __launch_bounds__(kSortThreads, 4)
+    k_onesweep(Ctl* __restrict__ ctl, int which, int pass, int gpass) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  SweepSmem& S = *reinterpret_cast<SweepSmem*>(smem_raw);
+  SweepV6Smem& S = *reinterpret_cast<SweepV6Smem*>(smem_raw);
   SortCtl& sc = which ? ctl->in_sort : ctl->out_sort;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const PassDesc pd = sc.pass[pass];
-  const uint32_t n = sc.n;
-  const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
-  uint32_t* __restrict__ st_next = ctl->status[(gpass + 1) & 1];
-  if (!pd.active) {
-    const size_t rows = (size_t)ntiles * kRadix;
-    for (size_t i = (size_t)blockIdx.x * kSortThreads + tid; i < rows;
-         i += (size_t)gridDim.x * kSortThreads)
-      st_next[i] = 0;
-    return;
-  }
-  uint32_t* __restrict__ st = ctl->status[gpass & 1];
-  const uint64_t* __restrict__ in = pd.in;
-  const int32_t* __restrict__ src = ctl->src;
-  const int32_t* __restrict__ dst = ctl->dst;
-  const bool cols_bulk = ((((uintptr_t)src) | ((uintptr_t)dst)) & 15) == 0;
-  const uint32_t shift = pd.shift;
-  uint64_t* __restrict__ out = pd.out;
-  const volatile uint32_t* verr = &ctl->err;
-
   if (tid == 0) {
-    mbar_init(&S.bar[0], 1);
-    mbar_init(&S.bar[1], 1);
+    S.tile = atomicAdd(&sc.tile_counter[pass], 1u);
+    mbar_init(&S.bar, 1);
     mbar_init_fence();
-    const uint32_t t0 = atomicAdd(&sc.tile_counter[pass], 1u);
-    S.next_tile[0] = t0;
-    if (t0 < ntiles) sweep_issue(S, 0, t0, n, in, src, dst, cols_bulk);
   }
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) {
+    S.whist[w][tid] = 0;
+    S.mask[w][tid] = 0;
+  }
+  if (tid < kSortWarps) S.mask[tid][kRadix] = 0;
   __syncthreads();
-  uint32_t tile = S.next_tile[0];
-  int b = 0;
-  uint32_t phase0 = 0, phase1 = 0;
-  while (tile < ntiles) {
-    // claim the next tile and start its load into the other buffer
-    if (tid == 0) {
-      const uint32_t nt = atomicAdd(&sc.tile_counter[pass], 1u);
-      S.next_tile[b ^ 1] = nt;
-      if (nt < ntiles) sweep_issue(S, b ^ 1, nt, n, in, src, dst, cols_bulk);
+  const uint32_t tile = S.tile;
+  const int reg = gpass & 1, nreg = reg ^ 1;
+  if (tile < ctl->status_rows) {
+    // clear this tile's row (and, for a chunk's first tile, the chunk's row)
+    // of the other region for the next pass
+    ctl->status[nreg][(size_t)tile * kRadix + tid] = 0;
+    if ((tile & (kChunkTiles - 1)) == 0) {
+      const uint32_t cidx = tile >> kChunkShift;
+      ctl->chunk_agg[nreg][(size_t)cidx * kRadix + tid] = 0;
+      ctl->chunk_inc[nreg][(size_t)cidx * kRadix + tid] = 0;
+      if (tid == 0) ctl->chunk_cnt[nreg][cidx] = 0;
     }
-    st_next[(size_t)tile * kRadix + tid] = 0;
-#pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) S.whist[w][tid] = 0;
-    const uint32_t base = tile * (uint32_t)kSortTile;
-    const uint32_t cnt = min((uint32_t)kSortTile, n - base);
-    {
-      // thread 0 waits (bounded) and tells the block; the others then see a
-      // completed phase at once
-      const uint32_t par = b ? phase1 : phase0;
-      if (tid == 0) S.ok = mbar_wait_bounded(&S.bar[b], par, verr) ? 1u : 0u;
-      __syncthreads();
-      if (!S.ok) {
-        if (tid == 0) {
-          atomicOr(&ctl->err, kErrLookback);
-          // let this block's own copies land before it exits
-          mbar_wait_bounded(&S.bar[b], par, nullptr);
-          if (S.next_tile[b ^ 1] < ntiles)
-            mbar_wait_bounded(&S.bar[b ^ 1], b ? phase0 : phase1, nullptr);
-        }
-        return;
-      }
-      while (!mbar_try_wait(&S.bar[b], par)) {
-      }
-      if (b) phase1 ^= 1u; else phase0 ^= 1u;
-    }
-    // the part of the tile the bulk copy did not cover (ragged tail or
-    // unaligned columns) comes in with plain loads
-    const uint32_t bulk = S.bulk_cnt[b];
-    if (in) {
-      for (uint32_t j = bulk + tid; j < cnt; j += kSortThreads) S.buf[b][j] = in[base + j];
-    } else {
-      int32_t* cols = reinterpret_cast<int32_t*>(&S.buf[b][0]);
-      for (uint32_t j = bulk + tid; j < cnt; j += kSortThreads) {
-        cols[j] = src[base + j];
-        cols[kSortTile + j] = dst[base + j];
-      }
-    }
-    __syncthreads();
-
-    // keys into registers, warp-striped: item i of lane l is tile slot
-    // 512 warp + 32 i + l
-    uint64_t key[kSortItems];
-    uint32_t valid = 0;
-    const uint32_t wslot = warp * (kSortItems * 32);
-    if (in) {
-#pragma unroll
-      for (int i = 0; i < kSortItems; ++i) {
-        const uint32_t j = wslot + i * 32 + lane;
-        key[i] = S.buf[b][j];
-        if (j < cnt) valid |= 1u << i;
-      }
-    } else {
-      const int32_t* cols = reinterpret_cast<const int32_t*>(&S.buf[b][0]);
-#pragma unroll
-      for (int i = 0; i < kSortItems; ++i) {
-        const uint32_t j = wslot + i * 32 + lane;
-        const uint32_t sb = (uint32_t)cols[j] ^ kBias;
-        const uint32_t db = (uint32_t)cols[kSortTile + j] ^ kBias;
-        key[i] = ((uint64_t)sb << 32) | db;
-        if (j < cnt) valid |= 1u << i;
-      }
-    }
-    uint16_t rank[kSortItems];
-    const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-      const bool ok = (valid >> i) & 1u;
-      const uint32_t dig = ok ? (uint32_t)(key[i] >> shift) & (kRadix - 1) : kRadix;
-      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dig);
-      const int leader = 31 - __clz(peers);
-      uint32_t old = 0;
-      if (lane == leader && ok) old = atomicAdd(&S.whist[warp][dig], (uint32_t)__popc(peers));
-      old = __shfl_sync(0xFFFFFFFFu, old, leader);
-      rank[i] = (uint16_t)(old + __popc(peers & lt));
-    }
-    __syncthreads();
-
-    uint32_t bin_total = 0;
-#pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-      const uint32_t c = S.whist[w][tid];
-      S.whist[w][tid] = bin_total;
-      bin_total += c;
-    }
-    uint32_t* my_st = st + (size_t)tile * kRadix + tid;
-    st_relaxed_u32(my_st, tile == 0 ? (kStInc | bin_total) : (1u + bin_total));
-    uint32_t tile_total;
-    const uint32_t bin_start = block_exclusive_sum<kSortThreads>(bin_total, S.sw, tile_total);
-    S.binstart[tid] = bin_start;
-    uint32_t excl = 0;
-    if (tile > 0) {
-      excl = digit_lookback(st, tile, tid, ctl);
-      st_relaxed_u32(my_st, kStInc | (excl + bin_total));
-    }
-    S.delta[tid] = (int32_t)(sc.base[pass][tid] + excl) - (int32_t)bin_start;
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-      if ((valid >> i) & 1u) {
-        const uint32_t dig = (uint32_t)(key[i] >> shift) & (kRadix - 1);
-        S.buf[b][S.binstart[dig] + S.whist[warp][dig] + rank[i]] = key[i];
-      }
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (uint32_t j = tid; j < cnt; j += kSortThreads) {
-      const uint64_t k = S.buf[b][j];
-      const uint32_t dig = (uint32_t)(k >> shift) & (kRadix - 1);
-      out[(uint32_t)(S.delta[dig] + (int32_t)j)] = k;
-    }
-    fence_proxy_async_smem();  // this buffer is the target of a later bulk copy
-    __syncthreads();
-    tile = S.next_tile[b ^ 1];
-    b ^= 1;
   }
-}
-
-
-// Lanes of the warp whose 8-bit digit (plus a validity bit) equals this
-// lane's: nine ballots, one per bit, each kept or inverted by the lane's own
-// bit.
-__device__ __forceinline__ uint32_t digit_peers(uint32_t dig, bool ok) {
-  uint32_t peers = ok ? __ballot_sync(0xFFFFFFFFu, ok) : ~__ballot_sync(0xFFFFFFFFu, ok);
-#pragma unroll
-  for (int b = 0; b < kRadixBits; ++b) {
-    const bool bit = (dig >> b) & 1u;
-    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, bit);
-    peers &= bit ? bal : ~bal;
-  }
-  return peers;
-}
-
-// The same pass with one tile per block: several blocks per SM overlap
-// their phases.  Digit counts are taken first and published at once (so
-// later tiles find them already visible when they look back), then keys are
-// ranked with ballot-built peer masks, then the look-back runs.
-__global__ void __launch_bounds__(kSortThreads, 3)
-    k_onesweep_blocked(Ctl* __restrict__ ctl, int which, int pass, int gpass) {
-  __shared__ uint64_t s_keys[kSortTile];
-  __shared__ uint32_t s_whist[kSortWarps][kRadix];
-  __shared__ int32_t s_delta[kRadix];
-  __shared__ uint32_t s_binstart[kRadix];
-  __shared__ uint32_t s_sw[kSortWarps + 1];
-  __shared__ uint32_t s_tile;
-
-  SortCtl& sc = which ? ctl->in_sort : ctl->out_sort;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(&sc.tile_counter[pass], 1u);
-#pragma unroll
-  for (int w = 0; w < kSortWarps; ++w) s_whist[w][tid] = 0;
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  if (tile < ctl->status_rows)
-    ctl->status[(gpass + 1) & 1][(size_t)tile * kRadix + tid] = 0;
   const PassDesc pd = sc.pass[pass];
   const uint32_t n = sc.n;
   const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
   if (!pd.active || tile >= ntiles) return;
-  uint32_t* __restrict__ st = ctl->status[gpass & 1];
+  uint32_t* __restrict__ st = ctl->status[reg];
   const uint32_t base = tile * (uint32_t)kSortTile;
-  const uint32_t wbase = base + warp * (kSortItems * 32);
+  const uint32_t cnt = min((uint32_t)kSortTile, n - base);
   const uint32_t shift = pd.shift;
+  const uint64_t* __restrict__ in = pd.in;
+  const int32_t* __restrict__ src = ctl->src;
+  const int32_t* __restrict__ dst = ctl->dst;
+  int32_t* cols = reinterpret_cast<int32_t*>(&S.keys[0]);  // first pass: src | dst
 
-  uint64_t key[kSortItems];
-  uint32_t valid = 0;
-  if (pd.in) {
-    const uint64_t* __restrict__ in = pd.in;
-#pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-      const uint32_t pos = wbase + i * 32 + lane;
-      if (pos < n) {
-        key[i] = __ldcs(in + pos);
-        valid |= 1u << i;
+  // 0. bulk copy of the tile (what is not a multiple of 16 bytes, or not
+  //    16-byte aligned, comes in with plain loads)
+  uint32_t bulk;
+  if (in) bulk = cnt & ~1u;
+  else bulk = ((((uintptr_t)src) | ((uintptr_t)dst)) & 15) == 0 ? (cnt & ~3u) : 0u;
+  if (tid == 0) {
+    const uint32_t bytes = bulk * 8u;  // 8-byte keys, or two 4-byte columns
+    mbar_arrive_expect_tx(&S.bar, bytes);
+    if (bulk) {
+      if (in) {
+        bulk_g2s(&S.keys[0], in + base, bulk * 8u, &S.bar);
       } else {
-        key[i] = 0;
+        bulk_g2s(cols, src + base, bulk * 4u, &S.bar);
+        bulk_g2s(cols + kSortTile, dst + base, bulk * 4u, &S.bar);
       }
     }
+    S.ok = mbar_wait_bounded(&S.bar, 0, &ctl->err) ? 1u : 0u;
+  }
+  if (in) {
+    for (uint32_t j = bulk + tid; j < cnt; j += kSortThreads) S.keys[j] = in[base + j];
   } else {
-    const int32_t* __restrict__ src = ctl->src;
-    const int32_t* __restrict__ dst = ctl->dst;
-#pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-      const uint32_t pos = wbase + i * 32 + lane;
-      if (pos < n) {
-        const uint32_t sb = (uint32_t)__ldcs(src + pos) ^ kBias;
-        const uint32_t db = (uint32_t)__ldcs(dst + pos) ^ kBias;
-        key[i] = ((uint64_t)sb << 32) | db;
-        valid |= 1u << i;
-      } else {
-        key[i] = 0;
-      }
+    for (uint32_t j = bulk + tid; j < cnt; j += kSortThreads) {
+      cols[j] = src[base + j];
+      cols[kSortTile + j] = dst[base + j];
     }
   }
-  // 1. digit counts per warp (shared-memory reductions, no return values)
-#pragma unroll
-  for (int i = 0; i < kSortItems; ++i)
-    if ((valid >> i) & 1u) atomicAdd(&s_whist[warp][(uint32_t)(key[i] >> shift) & (kRadix - 1)], 1u);
   __syncthreads();
-  // 2. thread tid owns digit tid: warp prefixes, tile count, publish
+  if (!S.ok) {  // the copy did not land in time (never expected)
+    if (tid == 0) {
+      atomicOr(&ctl->err, kErrLookback);
+      mbar_wait_bounded(&S.bar, 0, nullptr);
+    }
+    return;
+  }
+  while (!mbar_try_wait(&S.bar, 0)) {
+  }
+  auto digit_at = [&](uint32_t j) -> uint32_t {
+    if (in) return (uint32_t)(S.keys[j] >> shift) & (kRadix - 1);
+    // packed key = bias(src) << 32 | bias(dst)
+    const uint32_t v = shift >= 32 ? ((uint32_t)cols[j] ^ kBias) : ((uint32_t)cols[kSortTile + j] ^ kBias);
+    return (v >> (shift & 31)) & (kRadix - 1);
+  };
+  const uint32_t wslot = warp * (kSortItems * 32);
+  // 1. counts
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const uint32_t j = wslot + i * 32 + lane;
+    if (j < cnt) atomicAdd(&S.whist[warp][digit_at(j)], 1u);
+  }
+  __syncthreads();
+  // 2. thread tid owns digit tid
   uint32_t bin_total = 0;
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w) {
-    const uint32_t c = s_whist[w][tid];
-    s_whist[w][tid] = bin_total;
+    const uint32_t c = S.whist[w][tid];
+    S.whist[w][tid] = bin_total;
     bin_total += c;
   }
   uint32_t* my_st = st + (size_t)tile * kRadix + tid;
   st_relaxed_u32(my_st, tile == 0 ? (kStInc | bin_total) : (1u + bin_total));
+  const uint32_t chunk = tile >> kChunkShift;
+  uint32_t* cagg = ctl->chunk_agg[reg];
+  uint32_t* cinc = ctl->chunk_inc[reg];
+  uint32_t* ccnt = ctl->chunk_cnt[reg];
+  if (bin_total) atomicAdd(cagg + (size_t)chunk * kRadix + tid, bin_total);
+  __threadfence();  // the counts above are visible before the chunk counter moves
   uint32_t tile_total;
-  const uint32_t bin_start = block_exclusive_sum<kSortThreads>(bin_total, s_sw, tile_total);
-  s_binstart[tid] = bin_start;
+  const uint32_t bin_start = block_exclusive_sum<kSortThreads>(bin_total, S.sw, tile_total);
+  if (tid == 0) atomicAdd(ccnt + chunk, 1u);
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) S.whist[w][tid] += bin_start;
   __syncthreads();
-  // 3. stable ranks: within a warp, position order is (item, lane); the
-  //    highest peer advances the warp's running offset for the digit
-  uint16_t lpos[kSortItems];
+  // 3. ranks
   const uint32_t lt = lanemask_lt();
+  uint32_t* wmask = S.mask[warp];
+  uint32_t* whist = S.whist[warp];
+  uint32_t lpos[kSortItems / 2];  // two 16-bit positions per register
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
-    const bool ok = (valid >> i) & 1u;
-    const uint32_t dig = (uint32_t)(key[i] >> shift) & (kRadix - 1);
-    const uint32_t peers = digit_peers(dig, ok);
+    const uint32_t j = wslot + i * 32 + lane;
+    const bool ok = j < cnt;
+    const uint32_t dig = ok ? digit_at(j) : kRadix;
+    atomicOr(&wmask[dig], 1u << lane);
+    __syncwarp();
+    const uint32_t peers = wmask[dig];
+    __syncwarp();
     const int leader = 31 - __clz(peers);
     uint32_t old = 0;
-    if (lane == leader && ok) old = atomicAdd(&s_whist[warp][dig], (uint32_t)__popc(peers));
+    if (lane == leader) {
+      wmask[dig] = 0;
+      if (ok) old = atomicAdd(&whist[dig], (uint32_t)__popc(peers));
+    }
+    __syncwarp();
     old = __shfl_sync(0xFFFFFFFFu, old, leader);
-    lpos[i] = (uint16_t)(s_binstart[dig] + old + __popc(peers & lt));
+    const uint32_t pos = old + __popc(peers & lt);
+    if (i & 1) lpos[i >> 1] |= pos << 16;
+    else lpos[i >> 1] = pos;
   }
-  // 4. look-back for the digit's offset in earlier tiles
+  // 4. move the keys to their ranked places
+  uint64_t key[kSortItems];
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const uint32_t j = wslot + i * 32 + lane;
+    if (in) {
+      key[i] = S.keys[j];
+    } else {
+      key[i] = ((uint64_t)((uint32_t)cols[j] ^ kBias) << 32) | ((uint32_t)cols[kSortTile + j] ^ kBias);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const uint32_t j = wslot + i * 32 + lane;
+    if (j < cnt) S.keys[(lpos[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu] = key[i];
+  }
+  // 5. look-back
   uint32_t excl = 0;
   if (tile > 0) {
-    excl = digit_lookback(st, tile, tid, ctl);
+    excl = digit_lookback2(st, cagg, cinc, ccnt, tile, ntiles, tid, ctl);
     st_relaxed_u32(my_st, kStInc | (excl + bin_total));
   }
-  s_delta[tid] = (int32_t)(sc.base[pass][tid] + excl) - (int32_t)bin_start;
-  // 5. stage in digit order, then write out
-#pragma unroll
-  for (int i = 0; i < kSortItems; ++i)
-    if ((valid >> i) & 1u) s_keys[lpos[i]] = key[i];
+  if ((tile & (kChunkTiles - 1)) == 0 && chunk > 0)
+    st_relaxed_u32(cinc + (size_t)(chunk - 1) * kRadix + tid, kStInc | excl);
+  if ((tile & (kChunkTiles - 1)) == kChunkTiles - 1 || tile == ntiles - 1)
+    st_relaxed_u32(cinc + (size_t)chunk * kRadix + tid, kStInc | (excl + bin_total));
+  S.delta[tid] = (int32_t)(sc.base[pass][tid] + excl) - (int32_t)bin_start;
   __syncthreads();
-  const uint32_t nvalid = min((uint32_t)kSortTile, n - base);
+  // 6. scatter
   uint64_t* __restrict__ out = pd.out;
 #pragma unroll 4
-  for (uint32_t j = tid; j < nvalid; j += kSortThreads) {
-    const uint64_t k = s_keys[j];
+  for (uint32_t j = tid; j < cnt; j += kSortThreads) {
+    const uint64_t k = S.keys[j];
     const uint32_t dig = (uint32_t)(k >> shift) & (kRadix - 1);
-    out[(uint32_t)(s_delta[dig] + (int32_t)j)] = k;
+    const uint32_t pos = (uint32_t)(S.delta[dig] + (int32_t)j);
+    if (pos < n) out[pos] = k;
   }
 }
 
-static int g_sweep_blocks_per_sm = 0;
-static int g_sweep_variant = -1;  // 0: one tile per block, 1: persistent
-
-int onesweep_variant() {
-  if (g_sweep_variant < 0) {
-    const char* v = getenv("RINGO_ONESWEEP");
-    g_sweep_variant = (v && v[0] == 'p') ? 1 : 0;
-  }
-  return g_sweep_variant;
-}
+static bool g_sweep_attr = false;
 
 void launch_onesweep(Ctl* ctl, int which, int pass, int gpass, uint32_t tiles, cudaStream_t s) {
   if (tiles == 0) return;
-  if (onesweep_variant() == 0) {
-    k_onesweep_blocked<<<tiles, kSortThreads, 0, s>>>(ctl, which, pass, gpass);
-    return;
+  if (!g_sweep_attr) {
+    cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(SweepV6Smem));
+    g_sweep_attr = true;
   }
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (g_sweep_blocks_per_sm == 0) {
-    cudaFuncSetAttribute(k_onesweep_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(SweepSmem));
-    int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_onesweep_persistent, kSortThreads,
-                                                  sizeof(SweepSmem));
-    g_sweep_blocks_per_sm = per > 0 ? per : 1;
-  }
-  uint32_t grid = (uint32_t)sms * (uint32_t)g_sweep_blocks_per_sm;
-  if (grid > tiles) grid = tiles;
-  k_onesweep_persistent<<<grid, kSortThreads, sizeof(SweepSmem), s>>>(ctl, which, pass, gpass);
+  k_onesweep<<<tiles, kSortThreads, sizeof(SweepV6Smem), s>>>(ctl, which, pass, gpass);
 }
 
 }  // namespace ringo
