@@ -69,6 +69,22 @@ struct WsLayout {
   size_t chunks, chunk_bytes;
 };
 
+size_t chunks_for(size_t tiles) { return (tiles + kChunkTiles - 1) / kChunkTiles; }
+size_t scan_bytes(size_t tiles) {
+  const size_t c = chunks_for(tiles);
+  return align_up(8 * tiles) + align_up(8 * c) + align_up(8 * c) + align_up(4 * c);
+}
+void place_scan(Ctl* h, int i, char* p, size_t tiles) {
+  const size_t c = chunks_for(tiles);
+  h->scan_status[i] = (uint64_t*)p;
+  p += align_up(8 * tiles);
+  h->scan_chunk_agg[i] = (uint64_t*)p;
+  p += align_up(8 * c);
+  h->scan_chunk_inc[i] = (uint64_t*)p;
+  p += align_up(8 * c);
+  h->scan_chunk_cnt[i] = (uint32_t*)p;
+}
+
 WsLayout layout_for(uint32_t n) {
   const size_t tiles = (n + kSortTile - 1) / kSortTile;
   const size_t mtiles = ((size_t)2 * n + kMergeTile - 1) / kMergeTile + 1;
@@ -83,9 +99,10 @@ WsLayout layout_for(uint32_t n) {
   L.chunk_bytes = align_up(sizeof(uint32_t) * L.chunks * (2 * kRadix + 1));
   L.ch0 = o; o = align_up(o + L.chunk_bytes);
   L.ch1 = o; o = align_up(o + L.chunk_bytes);
-  L.sc0 = o; o = align_up(o + sizeof(uint64_t) * tiles);
-  L.sc1 = o; o = align_up(o + sizeof(uint64_t) * tiles);
-  L.sc2 = o; o = align_up(o + sizeof(uint64_t) * mtiles);
+  // per scan: tile statuses, then chunk sums, chunk prefixes, chunk counters
+  L.sc0 = o; o = align_up(o + scan_bytes(tiles));
+  L.sc1 = o; o = align_up(o + scan_bytes(tiles));
+  L.sc2 = o; o = align_up(o + scan_bytes(mtiles));
   L.usrc = o; o = align_up(o + sizeof(int32_t) * ((size_t)n + 1));
   L.usrc_start = o; o = align_up(o + sizeof(int32_t) * ((size_t)n + 1));
   L.udst = o; o = align_up(o + sizeof(int32_t) * ((size_t)n + 1));
@@ -142,9 +159,9 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
       hctl->chunk_cnt[r] = ch + 2 * L.chunks * kRadix;
     }
     hctl->chunk_rows = (uint32_t)L.chunks;
-    hctl->scan_status[0] = (uint64_t*)(ws + L.sc0);
-    hctl->scan_status[1] = (uint64_t*)(ws + L.sc1);
-    hctl->scan_status[2] = (uint64_t*)(ws + L.sc2);
+    place_scan(hctl, 0, ws + L.sc0, tiles);
+    place_scan(hctl, 1, ws + L.sc1, tiles);
+    place_scan(hctl, 2, ws + L.sc2, ((size_t)2 * n + kMergeTile - 1) / kMergeTile + 1);
     hctl->usrc = (int32_t*)(ws + L.usrc);
     hctl->usrc_start = (int32_t*)(ws + L.usrc_start);
     hctl->udst = (int32_t*)(ws + L.udst);

@@ -1,6 +1,8 @@
 // Small device-side building blocks: relaxed GPU-scope loads/stores, lane
-// masks, block scans and the single-pass (decoupled look-back) tile prefix
-// used by the compaction kernels.
+// masks, block scans, bulk asynchronous copies, and the single-pass
+// (decoupled look-back, Merrill & Garland 2016) tile prefix used by the
+// compaction kernels, here in a two-level form (tiles within a chunk, then
+// chunk aggregates).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -134,45 +136,109 @@ __device__ __forceinline__ T block_exclusive_sum(T v, T* sw, T& total) {
   return sw[w] + x - v;
 }
 
-// Single-pass tile prefix (decoupled look-back, Merrill & Garland 2016) over a
-// 64-bit packed status array.  Called by warp 0 of the tile's block; every
-// lane returns the exclusive prefix of `agg` over tiles [0, tile).  Waits are
-// bounded: on expiry the error bit is raised and the partial prefix is used
-// (the host then reports RINGO_ETIMEOUT and discards the result).
-__device__ __forceinline__ uint64_t warp_lookback(uint64_t* status, uint32_t tile,
-                                                  uint64_t agg, uint32_t* err) {
+// Chunk arrays of the two-level single-value look-back (one set per scan).
+struct ScanChunks {
+  uint64_t* agg;   // [chunks] packed sums added by the chunk's tiles
+  uint64_t* inc;   // [chunks] kScanInc | inclusive prefix once known
+  uint32_t* cnt;   // [chunks] tiles that have added their value
+};
+
+// Two-level tile prefix for the compaction kernels: like warp_lookback, but a
+// tile walks back only within its kChunkTiles-tile chunk and then over chunk
+// aggregates (complete once every tile of the chunk has added its value), so
+// no tile waits on the chain of inclusive prefixes of all its predecessors.
+// Called by warp 0 of the block; all lanes return the exclusive prefix.
+__device__ __forceinline__ uint64_t warp_lookback2(uint64_t* status, ScanChunks ch, uint32_t tile,
+                                                   uint32_t ntiles, uint64_t agg, uint32_t* err) {
   const int lane = threadIdx.x & 31;
-  if (tile == 0) {
-    if (lane == 0) st_relaxed_u64(status, kScanInc | agg);
-    return 0;
+  const uint32_t c = tile >> kChunkShift;
+  const uint32_t first = c << kChunkShift;
+  // publish this tile's value, and add it to the chunk aggregate
+  if (lane == 0) {
+    st_relaxed_u64(status + tile, (tile == 0 ? kScanInc : kScanAgg) | agg);
+    if (agg) atomicAdd((unsigned long long*)(ch.agg + c), (unsigned long long)agg);
+    __threadfence();
+    atomicAdd(ch.cnt + c, 1u);
   }
-  if (lane == 0) st_relaxed_u64(status + tile, kScanAgg | agg);
   uint64_t excl = 0;
-  int64_t j = (int64_t)tile - 1;
+  if (tile == 0) return 0;
   uint32_t spins = 0;
-  bool gave_up = false;
-  while (true) {
-    const int64_t idx = j - lane;
-    uint64_t s = idx >= 0 ? ld_relaxed_u64(status + idx) : kScanInc;
-    while (__any_sync(0xFFFFFFFFu, (s >> 62) == 0)) {
-      if (spin_backoff(spins) || ((spins & 255) == 0 && *(volatile uint32_t*)err)) {
-        gave_up = true;
-        break;
+  const volatile uint32_t* verr = err;
+  // 1. earlier tiles of this chunk (at most 31: one warp-wide read).  Lane l
+  //    reads tile - 1 - l; the nearest inclusive prefix ends the sum, and
+  //    every tile before it (in lane order) must have published.
+  const int cnt_in = (int)(tile - first);
+  if (cnt_in > 0) {
+    while (true) {
+      const bool in_chunk = lane < cnt_in;
+      const uint64_t s = in_chunk ? ld_relaxed_u64(status + (tile - 1 - lane)) : 0;
+      const uint32_t incm = __ballot_sync(0xFFFFFFFFu, in_chunk && (s >> 62) == 2);
+      const int stop = incm ? __ffs(incm) - 1 : cnt_in;
+      const uint32_t missing = __ballot_sync(0xFFFFFFFFu, lane < stop && (s >> 62) == 0);
+      if (missing) {
+        if (spin_backoff(spins) || ((spins & 255) == 0 && *verr)) {
+          if (lane == 0) atomicOr(err, kErrScan);
+          return excl;
+        }
+        continue;
       }
-      if ((s >> 62) == 0) s = ld_relaxed_u64(status + idx);
+      const uint64_t v = (lane < stop || (incm && lane == stop)) ? (s & kScanValMask) : 0;
+      excl = warp_sum(v);
+      if (incm) return excl;
+      break;
     }
-    if (gave_up) {
-      if (lane == 0) atomicOr(err, kErrScan);
-      if ((s >> 62) == 0) s = kScanInc;  // treat as zero-valued end
-    }
-    const uint32_t inc = __ballot_sync(0xFFFFFFFFu, (s >> 62) == 2);
-    const int first = inc ? __ffs(inc) - 1 : 32;
-    uint64_t v = lane <= first ? (s & kScanValMask) : 0;
-    excl += warp_sum(v);
-    if (inc) break;
-    j -= 32;
   }
-  if (lane == 0) st_relaxed_u64(status + tile, kScanInc | (excl + agg));
+  // 2. earlier chunks, 32 per round
+  int64_t cc = (int64_t)c - 1;
+  while (cc >= 0) {
+    const int64_t k = cc - lane;
+    uint64_t inc = 0;
+    uint32_t done = 0;
+    if (k >= 0) {
+      inc = ld_relaxed_u64(ch.inc + k);
+      const uint32_t need = min((uint32_t)kChunkTiles, ntiles - ((uint32_t)k << kChunkShift));
+      done = ld_acquire_u32(ch.cnt + k) >= need ? 1u : 0u;
+    }
+    const uint32_t incm = __ballot_sync(0xFFFFFFFFu, k >= 0 && (inc >> 62) == 2);
+    const int stop = incm ? __ffs(incm) - 1 : 32;
+    const uint32_t ready = __ballot_sync(0xFFFFFFFFu, k < 0 || done || lane >= stop);
+    if (ready != 0xFFFFFFFFu) {
+      if (spin_backoff(spins) || ((spins & 255) == 0 && *verr)) {
+        if (lane == 0) atomicOr(err, kErrScan);
+        return excl;
+      }
+      continue;
+    }
+    uint64_t v = 0;
+    if (k >= 0 && lane < stop) v = ld_relaxed_u64(ch.agg + k);
+    if (lane == stop) v = inc & kScanValMask;
+    excl += warp_sum(v);
+    if (incm) return excl;
+    cc -= 32;
+  }
+  return excl;
+}
+
+// After its look-back the first tile of a chunk knows the previous chunk's
+// inclusive prefix, and the last tile knows its own chunk's.
+__device__ __forceinline__ void publish_chunk_inc(ScanChunks ch, uint32_t tile, uint32_t ntiles,
+                                                  uint64_t excl, uint64_t agg) {
+  const uint32_t c = tile >> kChunkShift;
+  if ((tile & (kChunkTiles - 1)) == 0 && c > 0) st_relaxed_u64(ch.inc + c - 1, kScanInc | excl);
+  if ((tile & (kChunkTiles - 1)) == kChunkTiles - 1 || tile == ntiles - 1)
+    st_relaxed_u64(ch.inc + c, kScanInc | (excl + agg));
+}
+
+// Exclusive prefix of `agg` over earlier tiles (two-level look-back) and the
+// publication of this tile's (and, where it knows one, a chunk's) inclusive
+// prefix.  Warp 0 only; every lane returns the prefix.
+__device__ __forceinline__ uint64_t scan_prefix(uint64_t* status, ScanChunks ch, uint32_t tile,
+                                                uint32_t ntiles, uint64_t agg, uint32_t* err) {
+  const uint64_t excl = warp_lookback2(status, ch, tile, ntiles, agg, err);
+  if ((threadIdx.x & 31) == 0) {
+    st_relaxed_u64(status + tile, kScanInc | (excl + agg));
+    publish_chunk_inc(ch, tile, ntiles, excl, agg);
+  }
   return excl;
 }
 

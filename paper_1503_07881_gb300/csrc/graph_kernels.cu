@@ -20,6 +20,9 @@ namespace {
 constexpr int kWarps = kScanThreads / 32;
 
 __device__ __forceinline__ int32_t unbias(uint32_t b) { return (int32_t)(b ^ kBias); }
+__device__ __forceinline__ ScanChunks chunks_of(const Ctl* ctl, int i) {
+  return ScanChunks{ctl->scan_chunk_agg[i], ctl->scan_chunk_inc[i], ctl->scan_chunk_cnt[i]};
+}
 }  // namespace
 
 // ------------------------------------------------------------------ K3 ----
@@ -89,7 +92,8 @@ __global__ void __launch_bounds__(kScanThreads) k_dedup(Ctl* __restrict__ ctl) {
     const uint32_t s = lane < kWarps ? s_ws[lane] : 0;
     const uint32_t ei = warp_inclusive_sum(e), si = warp_inclusive_sum(s);
     const uint32_t te = __shfl_sync(0xFFFFFFFFu, ei, 31), ts = __shfl_sync(0xFFFFFFFFu, si, 31);
-    const uint64_t excl = warp_lookback(ctl->scan_status[0], tile, pack2(te, ts), &ctl->err);
+    const uint64_t excl = scan_prefix(ctl->scan_status[0], chunks_of(ctl, 0), tile, ntiles,
+                                      pack2(te, ts), &ctl->err);
     __syncwarp();
     if (lane < kWarps) {
       s_we[lane] = ei - e;
@@ -206,7 +210,8 @@ __global__ void __launch_bounds__(kScanThreads) k_dst_rank(Ctl* __restrict__ ctl
     const uint32_t c = lane < kWarps ? s_w[lane] : 0;
     const uint32_t ci = warp_inclusive_sum(c);
     const uint32_t tc = __shfl_sync(0xFFFFFFFFu, ci, 31);
-    const uint64_t excl = warp_lookback(ctl->scan_status[1], tile, pack2(0, tc), &ctl->err);
+    const uint64_t excl = scan_prefix(ctl->scan_status[1], chunks_of(ctl, 1), tile, ntiles,
+                                      pack2(0, tc), &ctl->err);
     __syncwarp();
     if (lane < kWarps) s_w[lane] = ci - c;
     if (lane == 0) {
@@ -341,7 +346,8 @@ __global__ void __launch_bounds__(kScanThreads) k_merge(Ctl* __restrict__ ctl) {
   uint32_t total;
   const uint32_t local = block_exclusive_sum<kScanThreads>(cnt, s_sw, total);
   if (warp == 0) {
-    const uint64_t excl = warp_lookback(ctl->scan_status[2], tile, pack2(0, total), &ctl->err);
+    const uint64_t excl = scan_prefix(ctl->scan_status[2], chunks_of(ctl, 2), tile, ntiles,
+                                      pack2(0, total), &ctl->err);
     if (lane == 0) {
       s_prefix = excl;
       if (tile == ntiles - 1) {

@@ -53,9 +53,24 @@ constexpr size_t kChunkBytes = up(4 * kChunks * (2 * kRadix + 1));
 constexpr size_t kOffCh0 = up(kOffSt1 + 4 * kTiles * kRadix);
 constexpr size_t kOffCh1 = up(kOffCh0 + kChunkBytes);
 constexpr size_t kOffSc0 = up(kOffCh1 + kChunkBytes);
-constexpr size_t kOffSc1 = up(kOffSc0 + 8 * kTiles);
-constexpr size_t kOffSc2 = up(kOffSc1 + 8 * kTiles);
-constexpr size_t kOffUsrc = up(kOffSc2 + 8 * kMergeTiles);
+constexpr size_t chunks_for(size_t tiles) { return (tiles + kChunkTiles - 1) / kChunkTiles; }
+constexpr size_t scan_bytes(size_t tiles) {
+  return up(8 * tiles) + up(8 * chunks_for(tiles)) * 2 + up(4 * chunks_for(tiles));
+}
+constexpr size_t kOffSc1 = up(kOffSc0 + scan_bytes(kTiles));
+constexpr size_t kOffSc2 = up(kOffSc1 + scan_bytes(kTiles));
+constexpr size_t kOffUsrc = up(kOffSc2 + scan_bytes(kMergeTiles));
+
+void place_scan(Ctl* h, int i, unsigned char* p, size_t tiles) {
+  const size_t c = chunks_for(tiles);
+  h->scan_status[i] = (uint64_t*)p;
+  p += up(8 * tiles);
+  h->scan_chunk_agg[i] = (uint64_t*)p;
+  p += up(8 * c);
+  h->scan_chunk_inc[i] = (uint64_t*)p;
+  p += up(8 * c);
+  h->scan_chunk_cnt[i] = (uint32_t*)p;
+}
 constexpr size_t kOffUsrcStart = up(kOffUsrc + 4 * ((size_t)kMaxRows + 1));
 constexpr size_t kOffUdst = up(kOffUsrcStart + 4 * ((size_t)kMaxRows + 1));
 constexpr size_t kOffUdstStart = up(kOffUdst + 4 * ((size_t)kMaxRows + 1));
@@ -155,9 +170,9 @@ extern "C" int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* d
     h.chunk_cnt[r] = ch + 2 * chunks * kRadix;
   }
   h.chunk_rows = (uint32_t)chunks;
-  h.scan_status[0] = (uint64_t*)(ws + kOffSc0);
-  h.scan_status[1] = (uint64_t*)(ws + kOffSc1);
-  h.scan_status[2] = (uint64_t*)(ws + kOffSc2);
+  place_scan(&h, 0, ws + kOffSc0, tiles);
+  place_scan(&h, 1, ws + kOffSc1, tiles);
+  place_scan(&h, 2, ws + kOffSc2, ((size_t)2 * n + kMergeTile - 1) / kMergeTile + 1);
   h.usrc = (int32_t*)(ws + kOffUsrc);
   h.usrc_start = (int32_t*)(ws + kOffUsrcStart);
   h.udst = (int32_t*)(ws + kOffUdst);

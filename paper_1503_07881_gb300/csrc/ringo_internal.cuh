@@ -113,6 +113,9 @@ struct Ctl {
   uint32_t* chunk_cnt[2];     // [chunks] tiles that have added their counts
   uint32_t chunk_rows;
   uint64_t* scan_status[3];   // [tiles] each: dedup, dst_rank, merge
+  uint64_t* scan_chunk_agg[3];  // [chunks of those tiles] packed sums
+  uint64_t* scan_chunk_inc[3];  // [chunks] inclusive prefix, flagged
+  uint32_t* scan_chunk_cnt[3];  // [chunks] tiles that have added their sum
   int32_t* usrc;              // [n_rows + 1] distinct src IDs, ascending
   int32_t* usrc_start;        // [n_rows + 1] first out-edge of each source run
   int32_t* udst;              // [n_rows + 1] distinct dst IDs, ascending
