@@ -177,12 +177,13 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
       goto done;                       \
     }                                  \
   } while (0)
+    const Launch run = solo_launch(dctl, hctl, n);
     TRY(cudaMemcpyAsync(dctl, hctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     // status region 0 must start clear; each pass clears the other region
     TRY(cudaMemsetAsync(ws + L.st0, 0, L.st1 - L.st0, s));
     TRY(cudaMemsetAsync(ws + L.ch0, 0, L.chunk_bytes, s));
     TRY(cudaMemsetAsync(ws + L.sc0, 0, L.usrc - L.sc0, s));
-    if ((rc = enqueue_phase1(dctl, n, s)) != RINGO_OK) goto done;
+    if ((rc = enqueue_phase1(run, s)) != RINGO_OK) goto done;
     TRY(cudaMemcpyAsync(hctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
     if (hctl->err) {
@@ -209,7 +210,7 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
     hctl->in_off = g->in_off;
     place_rank_region(hctl, ranks, hctl->Vs, hctl->Vd);
     TRY(cudaMemcpyAsync(dctl, hctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-    if ((rc = enqueue_phase2(dctl, hctl->Vs, hctl->Vd, hctl->E, s)) != RINGO_OK) goto done;
+    if ((rc = enqueue_phase2(run, s)) != RINGO_OK) goto done;
     TRY(cudaMemcpyAsync(hctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
     if (hctl->err & (kErrLookback | kErrScan)) {

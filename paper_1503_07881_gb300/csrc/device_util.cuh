@@ -242,4 +242,34 @@ __device__ __forceinline__ uint64_t scan_prefix(uint64_t* status, ScanChunks ch,
   return excl;
 }
 
+// Largest s with m.start[s] <= g (binary search over the segment starts).
+__device__ __forceinline__ uint32_t seg_of(SegMap m, uint32_t g) {
+  uint32_t lo = 0, hi = m.nseg;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(m.start + mid) <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Thread 0 claims the next global slot and resolves it; the result is
+// shared through `out` (shared memory) after the caller's barrier.
+struct Claim {
+  uint32_t seg;
+  uint32_t tile;   // local tile of the segment
+  uint32_t valid;  // 0: past the last slot
+};
+__device__ __forceinline__ void claim_slot(SegMap m, uint32_t* counter, Claim* out) {
+  const uint32_t g = atomicAdd(counter, 1u);
+  if (g >= __ldg(m.start + m.nseg)) {
+    out->valid = 0;
+    return;
+  }
+  const uint32_t sidx = seg_of(m, g);
+  out->seg = sidx;
+  out->tile = g - __ldg(m.start + sidx);
+  out->valid = 1;
+}
+
 }  // namespace ringo

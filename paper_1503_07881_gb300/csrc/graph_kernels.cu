@@ -33,16 +33,19 @@ __device__ __forceinline__ ScanChunks chunks_of(const Ctl* ctl, int i) {
 //   out_nbr[e]               = dst-run index (turned into a node index later)
 //   usrc[s], usrc_start[s]   = src ID and its first edge; usrc_start[Vs] = E
 //   in_sort.hist             = digit histograms of the in-sort passes
-__global__ void __launch_bounds__(kScanThreads) k_dedup(Ctl* __restrict__ ctl) {
+__global__ void __launch_bounds__(kScanThreads)
+    k_dedup(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
   __shared__ uint32_t s_hist[kInPasses][kRadix];
   __shared__ uint32_t s_we[kWarps], s_ws[kWarps];
   __shared__ uint64_t s_prefix;
-  __shared__ uint32_t s_tile;
+  __shared__ Claim s_cl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(&ctl->scan_counter[0], 1u);
+  if (tid == 0) claim_slot(m, counter, &s_cl);
   for (int i = tid; i < kInPasses * kRadix; i += kScanThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
-  const uint32_t tile = s_tile;
+  if (!s_cl.valid) return;
+  Ctl* __restrict__ ctl = ctls + s_cl.seg;
+  const uint32_t tile = s_cl.tile;
   const uint32_t n = ctl->n_rows;
   const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
   if (tile >= ntiles) return;
@@ -142,8 +145,8 @@ __global__ void __launch_bounds__(kScanThreads) k_dedup(Ctl* __restrict__ ctl) {
   }
 }
 
-void launch_dedup(Ctl* ctl, uint32_t grid, cudaStream_t s) {
-  if (grid) k_dedup<<<grid, kScanThreads, 0, s>>>(ctl);
+void launch_dedup(const Launch& L, uint32_t* counter, cudaStream_t s) {
+  if (L.row_slots) k_dedup<<<L.row_slots, kScanThreads, 0, s>>>(L.ctls, L.rows, counter);
 }
 
 // ------------------------------------------------------------- dst rank ---
@@ -154,14 +157,17 @@ void launch_dedup(Ctl* ctl, uint32_t grid, cudaStream_t s) {
 // Reads rank_step.in (or packs from the columns when every dst pass was
 // trivial) and writes rank_step.out.  Single-pass compaction count with
 // decoupled look-back.
-__global__ void __launch_bounds__(kScanThreads) k_dst_rank(Ctl* __restrict__ ctl) {
+__global__ void __launch_bounds__(kScanThreads)
+    k_dst_rank(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
   __shared__ uint32_t s_w[kWarps];
   __shared__ uint64_t s_prefix;
-  __shared__ uint32_t s_tile;
+  __shared__ Claim s_cl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(&ctl->scan_counter[1], 1u);
+  if (tid == 0) claim_slot(m, counter, &s_cl);
   __syncthreads();
-  const uint32_t tile = s_tile;
+  if (!s_cl.valid) return;
+  Ctl* __restrict__ ctl = ctls + s_cl.seg;
+  const uint32_t tile = s_cl.tile;
   const uint32_t n = ctl->n_rows;
   const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
   if (tile >= ntiles) return;
@@ -232,8 +238,8 @@ __global__ void __launch_bounds__(kScanThreads) k_dst_rank(Ctl* __restrict__ ctl
   }
 }
 
-void launch_dst_rank(Ctl* ctl, uint32_t grid, cudaStream_t s) {
-  if (grid) k_dst_rank<<<grid, kScanThreads, 0, s>>>(ctl);
+void launch_dst_rank(const Launch& L, uint32_t* counter, cudaStream_t s) {
+  if (L.row_slots) k_dst_rank<<<L.row_slots, kScanThreads, 0, s>>>(L.ctls, L.rows, counter);
 }
 
 // ------------------------------------------------------------------ K5 ----
@@ -242,44 +248,35 @@ void launch_dst_rank(Ctl* ctl, uint32_t grid, cudaStream_t s) {
 // into a node index later) and, at each change of dst-run index d, the run's
 // first in-edge udst_start[d] = k (udst_start[Vd] = E).  Every dst-run index
 // occurs, so no compaction is needed.
-__global__ void __launch_bounds__(256) k_dst_runs(Ctl* __restrict__ ctl) {
+__global__ void __launch_bounds__(256)
+    k_dst_runs(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
+  __shared__ Claim s_cl;
+  if (threadIdx.x == 0) claim_slot(m, counter, &s_cl);
+  __syncthreads();
+  if (!s_cl.valid) return;
+  Ctl* __restrict__ ctl = ctls + s_cl.seg;
   const uint32_t E = ctl->E, Vd = ctl->Vd;
+  const uint32_t base = s_cl.tile * (uint32_t)kScanTile;
+  if (base >= E) return;
+  const uint32_t end = min(E, base + (uint32_t)kScanTile);
   const uint64_t* __restrict__ keys = ctl->in_sort.result;
   int32_t* __restrict__ in_nbr = ctl->in_nbr;
   int32_t* __restrict__ ustart = ctl->udst_start;
-  const uint32_t t0 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t0 == 0) ustart[Vd] = (int32_t)E;
+  if (base == 0 && threadIdx.x == 0) ustart[Vd] = (int32_t)E;
   // a dst-run index is always below Vd; anything else is recorded, not written
-  auto put = [&](uint32_t d, uint32_t k) {
-    if (d < Vd) ustart[d] = (int32_t)k;
-    else atomicOr(&ctl->err, kErrRemap);
-  };
-  const uint32_t E2 = E / 2;
-  for (uint32_t q = t0; q < E2; q += gridDim.x * blockDim.x) {
-    const ulonglong2 kk = __ldcs(reinterpret_cast<const ulonglong2*>(keys) + q);
-    const uint32_t k = 2 * q;
-    const uint32_t d0 = (uint32_t)(kk.x >> 32), d1 = (uint32_t)(kk.y >> 32);
-    const uint32_t dp = k ? (uint32_t)(keys[k - 1] >> 32) : 0xFFFFFFFFu;
-    if (k == 0 || d0 != dp) put(d0, k);
-    if (d1 != d0) put(d1, k + 1);
-    reinterpret_cast<int2*>(in_nbr)[q] = make_int2((int32_t)(uint32_t)kk.x, (int32_t)(uint32_t)kk.y);
-  }
-  if ((E & 1) && t0 == 0) {
-    const uint32_t k = E - 1;
-    const uint64_t key = keys[k];
+  for (uint32_t k = base + threadIdx.x; k < end; k += blockDim.x) {
+    const uint64_t key = __ldcs(keys + k);
     const uint32_t d = (uint32_t)(key >> 32);
-    if (k == 0 || d != (uint32_t)(keys[k - 1] >> 32)) put(d, k);
+    if (k == 0 || d != (uint32_t)(keys[k - 1] >> 32)) {
+      if (d < Vd) ustart[d] = (int32_t)k;
+      else atomicOr(&ctl->err, kErrRemap);
+    }
     in_nbr[k] = (int32_t)(uint32_t)key;
   }
 }
 
-void launch_dst_runs(Ctl* ctl, uint32_t n_rows, cudaStream_t s) {
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  uint32_t want = (n_rows / 2 + 255) / 256 + 1;
-  uint32_t cap = (uint32_t)sms * 8;
-  k_dst_runs<<<want < cap ? want : cap, 256, 0, s>>>(ctl);
+void launch_dst_runs(const Launch& L, uint32_t* counter, cudaStream_t s) {
+  if (L.row_slots) k_dst_runs<<<L.row_slots, 256, 0, s>>>(L.ctls, L.rows, counter);
 }
 
 // ----------------------------------------------------------- node merge ---
@@ -303,14 +300,9 @@ __device__ __forceinline__ uint32_t merge_path(const int32_t* __restrict__ a, ui
   return lo;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_merge(Ctl* __restrict__ ctl) {
-  __shared__ uint32_t s_sw[kWarps + 1];
-  __shared__ uint64_t s_prefix;
-  __shared__ uint32_t s_tile;
+__device__ __forceinline__ void merge_tile(Ctl* __restrict__ ctl, uint32_t tile, uint32_t* s_sw,
+                                           uint64_t* s_prefix) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(&ctl->scan_counter[2], 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
   const uint32_t Vs = ctl->Vs, Vd = ctl->Vd, M = Vs + Vd;
   const uint32_t ntiles = (M + kMergeTile - 1) / kMergeTile;
   if (tile >= ntiles) return;
@@ -349,7 +341,7 @@ __global__ void __launch_bounds__(kScanThreads) k_merge(Ctl* __restrict__ ctl) {
     const uint64_t excl = scan_prefix(ctl->scan_status[2], chunks_of(ctl, 2), tile, ntiles,
                                       pack2(0, total), &ctl->err);
     if (lane == 0) {
-      s_prefix = excl;
+      *s_prefix = excl;
       if (tile == ntiles - 1) {
         const uint32_t V = unpackB(excl) + total;
         ctl->V = V;
@@ -359,7 +351,7 @@ __global__ void __launch_bounds__(kScanThreads) k_merge(Ctl* __restrict__ ctl) {
     }
   }
   __syncthreads();
-  uint32_t r = unpackB(s_prefix) + local;  // nodes emitted before this item
+  uint32_t r = unpackB(*s_prefix) + local;  // nodes emitted before this item
   const int32_t* __restrict__ us = ctl->usrc_start;
   const int32_t* __restrict__ ud = ctl->udst_start;
 #pragma unroll
@@ -381,19 +373,95 @@ __global__ void __launch_bounds__(kScanThreads) k_merge(Ctl* __restrict__ ctl) {
   }
 }
 
-void launch_merge(Ctl* ctl, uint32_t grid, cudaStream_t s) {
-  if (grid) k_merge<<<grid, kScanThreads, 0, s>>>(ctl);
+// Persistent: blocks claim merge slots in order until none is left.
+__global__ void __launch_bounds__(kScanThreads)
+    k_merge(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
+  __shared__ uint32_t s_sw[kWarps + 1];
+  __shared__ uint64_t s_prefix;
+  __shared__ Claim s_cl;
+  while (true) {
+    if (threadIdx.x == 0) claim_slot(m, counter, &s_cl);
+    __syncthreads();
+    if (!s_cl.valid) return;
+    merge_tile(ctls + s_cl.seg, s_cl.tile, s_sw, &s_prefix);
+    __syncthreads();
+  }
+}
+
+// Slot maps of phase 2 from the sizes phase 1 left in each control block:
+// merge tiles cover Vs + Vd items, block-table pieces cover max(Vs, Vd) / 32
+// words.  One block; segments in order.
+__global__ void k_phase2_maps(Ctl* __restrict__ ctls, uint32_t nseg, uint32_t* merge_start,
+                              uint32_t* block_start) {
+  __shared__ uint32_t s_sw[32 + 1], s_sw2[32 + 1];
+  __shared__ uint32_t carry_m, carry_b;
+  if (threadIdx.x == 0) {
+    carry_m = 0;
+    carry_b = 0;
+  }
+  __syncthreads();
+  for (uint32_t b0 = 0; b0 < nseg; b0 += blockDim.x) {
+    const uint32_t sidx = b0 + threadIdx.x;
+    uint32_t mt = 0, bt = 0;
+    if (sidx < nseg) {
+      const Ctl* c = ctls + sidx;
+      mt = (c->Vs + c->Vd + kMergeTile - 1) / kMergeTile;
+      const uint32_t words = ((c->Vs > c->Vd ? c->Vs : c->Vd) + 31) >> kBlkShift;
+      bt = (words + kScanTile - 1) / kScanTile;
+    }
+    uint32_t tm, tb;
+    const uint32_t em = block_exclusive_sum<1024>(mt, s_sw, tm);
+    const uint32_t eb = block_exclusive_sum<1024>(bt, s_sw2, tb);
+    if (sidx < nseg) {
+      merge_start[sidx] = carry_m + em;
+      block_start[sidx] = carry_b + eb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      carry_m += tm;
+      carry_b += tb;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    merge_start[nseg] = carry_m;
+    block_start[nseg] = carry_b;
+  }
+}
+
+void launch_phase2_maps(const Launch& L, cudaStream_t s) {
+  k_phase2_maps<<<1, 1024, 0, s>>>(L.ctls, L.nseg, const_cast<uint32_t*>(L.merge.start),
+                                   const_cast<uint32_t*>(L.blocks.start));
+}
+
+static uint32_t persistent_grid(uint32_t per_sm) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return (uint32_t)sms * per_sm;
+}
+
+void launch_merge(const Launch& L, uint32_t* counter, cudaStream_t s) {
+  k_merge<<<persistent_grid(8), kScanThreads, 0, s>>>(L.ctls, L.merge, counter);
 }
 
 // ---------------------------------------------------------- block tables --
 // blk[k] = map[32k], with kBlkDense set when the 32 entries from 32k are
 // consecutive node indices (no node of the other kind lies between them);
 // then map[j] = (blk[j >> 5] & ~kBlkDense) + (j & 31) without reading map.
-__global__ void k_rank_blocks(Ctl* __restrict__ ctl) {
+__global__ void __launch_bounds__(256)
+    k_rank_blocks(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
+  __shared__ Claim s_cl;
+  while (true) {
+  if (threadIdx.x == 0) claim_slot(m, counter, &s_cl);
+  __syncthreads();
+  if (!s_cl.valid) return;
+  Ctl* __restrict__ ctl = ctls + s_cl.seg;
   const uint32_t Vs = ctl->Vs, Vd = ctl->Vd;
   const uint32_t ns = (Vs + 31) >> kBlkShift, nd = (Vd + 31) >> kBlkShift;
-  const uint32_t nmax = ns > nd ? ns : nd;
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nmax; k += gridDim.x * blockDim.x) {
+  const uint32_t k0 = s_cl.tile * (uint32_t)kScanTile;
+  const uint32_t k1 = k0 + (uint32_t)kScanTile;
+  for (uint32_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     if (k < ns) {
       const uint32_t a = k << kBlkShift, e = min(a + 32, Vs) - 1;
       const int32_t r0 = ctl->src_rank[a], r1 = ctl->src_rank[e];
@@ -405,14 +473,12 @@ __global__ void k_rank_blocks(Ctl* __restrict__ ctl) {
       ctl->dst_blk[k] = (uint32_t)r0 | ((uint32_t)(r1 - r0) == e - a ? kBlkDense : 0u);
     }
   }
+  __syncthreads();
+  }
 }
 
-void launch_rank_blocks(Ctl* ctl, uint32_t Vs, uint32_t Vd, cudaStream_t s) {
-  const uint32_t n = ((Vs > Vd ? Vs : Vd) + 31) >> kBlkShift;
-  if (n == 0) return;
-  uint32_t grid = (n + 255) / 256;
-  if (grid > 4096) grid = 4096;
-  k_rank_blocks<<<grid, 256, 0, s>>>(ctl);
+void launch_rank_blocks(const Launch& L, uint32_t* counter, cudaStream_t s) {
+  k_rank_blocks<<<persistent_grid(4), 256, 0, s>>>(L.ctls, L.blocks, counter);
 }
 
 // ---------------------------------------------------------------- remap ---
@@ -431,49 +497,46 @@ __device__ __forceinline__ int32_t map_index(const uint32_t* __restrict__ blk,
   return __ldg(map + j);
 }
 
-// One direction of the remap, in place, eight entries per thread.
-__device__ __forceinline__ void remap_array(int32_t* __restrict__ a, uint32_t E,
+// One direction of the remap over entries [base, end), in place.
+__device__ __forceinline__ void remap_range(int32_t* __restrict__ a, uint32_t base, uint32_t end,
                                             const uint32_t* __restrict__ blk,
                                             const int32_t* __restrict__ map, uint32_t len,
                                             uint32_t* err) {
-  const uint32_t E8 = E / 8;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < E8; q += stride) {
-    const int4* p4 = reinterpret_cast<const int4*>(a) + 2 * (size_t)q;
-    int4 x0 = __ldcs(p4), x1 = __ldcs(p4 + 1);
-    x0.x = map_index(blk, map, len, (uint32_t)x0.x, err);
-    x0.y = map_index(blk, map, len, (uint32_t)x0.y, err);
-    x0.z = map_index(blk, map, len, (uint32_t)x0.z, err);
-    x0.w = map_index(blk, map, len, (uint32_t)x0.w, err);
-    x1.x = map_index(blk, map, len, (uint32_t)x1.x, err);
-    x1.y = map_index(blk, map, len, (uint32_t)x1.y, err);
-    x1.z = map_index(blk, map, len, (uint32_t)x1.z, err);
-    x1.w = map_index(blk, map, len, (uint32_t)x1.w, err);
-    int4* w4 = reinterpret_cast<int4*>(a) + 2 * (size_t)q;
-    __stcs(w4, x0);
-    __stcs(w4 + 1, x1);
+  for (uint32_t e = base + threadIdx.x * 4; e < end; e += blockDim.x * 4) {
+    if (e + 4 <= end && (e & 3) == 0) {
+      int4 x = __ldcs(reinterpret_cast<const int4*>(a + e));
+      x.x = map_index(blk, map, len, (uint32_t)x.x, err);
+      x.y = map_index(blk, map, len, (uint32_t)x.y, err);
+      x.z = map_index(blk, map, len, (uint32_t)x.z, err);
+      x.w = map_index(blk, map, len, (uint32_t)x.w, err);
+      __stcs(reinterpret_cast<int4*>(a + e), x);
+    } else {
+      for (uint32_t q = e; q < min(e + 4, end); ++q)
+        a[q] = map_index(blk, map, len, (uint32_t)a[q], err);
+    }
   }
-  for (uint32_t e = E8 * 8 + blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride)
-    a[e] = map_index(blk, map, len, (uint32_t)a[e], err);
 }
 
 // When every node is a source (Vs == V) the source-run index already is the
 // node index and in_nbr is left as it is; likewise out_nbr when Vd == V.
-__global__ void __launch_bounds__(256) k_remap(Ctl* __restrict__ ctl) {
+__global__ void __launch_bounds__(256)
+    k_remap(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
+  __shared__ Claim s_cl;
+  if (threadIdx.x == 0) claim_slot(m, counter, &s_cl);
+  __syncthreads();
+  if (!s_cl.valid) return;
+  Ctl* __restrict__ ctl = ctls + s_cl.seg;
   const uint32_t E = ctl->E, V = ctl->V, Vs = ctl->Vs, Vd = ctl->Vd;
+  const uint32_t base = s_cl.tile * (uint32_t)kScanTile;
+  if (base >= E) return;
+  const uint32_t end = min(E, base + (uint32_t)kScanTile);
   uint32_t* err = &ctl->err;
-  if (Vd != V) remap_array(ctl->out_nbr, E, ctl->dst_blk, ctl->dst_rank, Vd, err);
-  if (Vs != V) remap_array(ctl->in_nbr, E, ctl->src_blk, ctl->src_rank, Vs, err);
+  if (Vd != V) remap_range(ctl->out_nbr, base, end, ctl->dst_blk, ctl->dst_rank, Vd, err);
+  if (Vs != V) remap_range(ctl->in_nbr, base, end, ctl->src_blk, ctl->src_rank, Vs, err);
 }
 
-void launch_remap(Ctl* ctl, uint32_t E, cudaStream_t s) {
-  if (E == 0) return;
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  uint32_t want = (E / 8 + 255) / 256 + 1;
-  uint32_t cap = (uint32_t)sms * 8;
-  k_remap<<<want < cap ? want : cap, 256, 0, s>>>(ctl);
+void launch_remap(const Launch& L, uint32_t* counter, cudaStream_t s) {
+  if (L.row_slots) k_remap<<<L.row_slots, 256, 0, s>>>(L.ctls, L.rows, counter);
 }
 
 // -------------------------------------------------------------- degrees ---

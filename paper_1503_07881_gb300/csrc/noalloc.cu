@@ -181,11 +181,12 @@ extern "C" int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* d
   h.in_nbr = in_nbr;
   // state left by the previous call: the control block is rewritten whole,
   // status region 0 and the scan statuses are cleared
+  const Launch run = solo_launch(dctl, &h, n);
   NA_TRY(cudaMemcpyAsync(dctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
   NA_TRY(cudaMemsetAsync(ws + kOffSt0, 0, 4 * (size_t)tiles * kRadix, s));
   NA_TRY(cudaMemsetAsync(ws + kOffCh0, 0, 4 * chunks * (2 * kRadix + 1), s));
   NA_TRY(cudaMemsetAsync(ws + kOffSc0, 0, kOffUsrc - kOffSc0, s));
-  if ((rc = enqueue_phase1(dctl, n, s)) != RINGO_OK) return rc;
+  if ((rc = enqueue_phase1(run, s)) != RINGO_OK) return rc;
   NA_TRY(cudaMemcpyAsync(&h, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
   NA_TRY(cudaStreamSynchronize(s));
   if (h.err) {
@@ -207,7 +208,7 @@ extern "C" int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* d
   h.src_blk = (uint32_t*)(h.dst_rank + up4(h.Vd));
   h.dst_blk = h.src_blk + up4((h.Vs + 31) / 32);
   NA_TRY(cudaMemcpyAsync(dctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-  if ((rc = enqueue_phase2(dctl, h.Vs, h.Vd, h.E, s)) != RINGO_OK) return rc;
+  if ((rc = enqueue_phase2(run, s)) != RINGO_OK) return rc;
   NA_TRY(cudaMemcpyAsync(&h, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
   NA_TRY(cudaStreamSynchronize(s));
 #undef NA_TRY

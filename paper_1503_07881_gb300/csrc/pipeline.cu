@@ -27,31 +27,33 @@ namespace ringo {
   } while (0)
 
 // histogram, out-sort dst passes, dst ranks, out-sort src passes, dedup,
-// in-sort passes, destination-run starts.  Afterwards E, Vs, Vd are final.
-int enqueue_phase1(Ctl* dctl, uint32_t n, cudaStream_t s) {
-  const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
+// in-sort passes, destination-run starts.  Afterwards E, Vs, Vd are final in
+// every segment's control block.  Counter i belongs to the i-th launch.
+int enqueue_phase1(const Launch& L, cudaStream_t s) {
   static_assert(kSortTile == kScanTile, "sort and scan tiles are the same rows");
-  RINGO_ENQUEUE("histogram", launch_histogram(dctl, n, s));
-  RINGO_ENQUEUE("plan", launch_plan(dctl, 0, s));
-  for (int p = 0; p < 4; ++p) RINGO_ENQUEUE("onesweep", launch_onesweep(dctl, 0, p, p, tiles, s));
-  RINGO_ENQUEUE("dst_rank", launch_dst_rank(dctl, tiles, s));
+  uint32_t* c = L.counters;
+  int k = 0;
+  RINGO_ENQUEUE("histogram", launch_histogram(L, c + k++, s));
+  RINGO_ENQUEUE("plan", launch_plan(L, 0, s));
+  for (int p = 0; p < 4; ++p) RINGO_ENQUEUE("onesweep", launch_onesweep(L, 0, p, p, c + k++, s));
+  RINGO_ENQUEUE("dst_rank", launch_dst_rank(L, c + k++, s));
   for (int p = 4; p < kOutPasses; ++p)
-    RINGO_ENQUEUE("onesweep", launch_onesweep(dctl, 0, p, p, tiles, s));
-  RINGO_ENQUEUE("dedup", launch_dedup(dctl, tiles, s));
-  RINGO_ENQUEUE("plan", launch_plan(dctl, 1, s));
+    RINGO_ENQUEUE("onesweep", launch_onesweep(L, 0, p, p, c + k++, s));
+  RINGO_ENQUEUE("dedup", launch_dedup(L, c + k++, s));
+  RINGO_ENQUEUE("plan", launch_plan(L, 1, s));
   for (int p = 0; p < kInPasses; ++p)
-    RINGO_ENQUEUE("onesweep", launch_onesweep(dctl, 1, p, kOutPasses + p, tiles, s));
-  RINGO_ENQUEUE("dst_runs", launch_dst_runs(dctl, n, s));
+    RINGO_ENQUEUE("onesweep", launch_onesweep(L, 1, p, kOutPasses + p, c + k++, s));
+  RINGO_ENQUEUE("dst_runs", launch_dst_runs(L, c + k++, s));
   return RINGO_OK;
 }
 
 // merge into the node list, block tables of the two rank maps, remap.
-int enqueue_phase2(Ctl* dctl, uint32_t Vs, uint32_t Vd, uint32_t E, cudaStream_t s) {
-  const uint64_t M = (uint64_t)Vs + Vd;
-  const uint32_t mgrid = (uint32_t)((M + kMergeTile - 1) / kMergeTile);
-  RINGO_ENQUEUE("merge", launch_merge(dctl, mgrid, s));
-  RINGO_ENQUEUE("rank_blocks", launch_rank_blocks(dctl, Vs, Vd, s));
-  RINGO_ENQUEUE("remap", launch_remap(dctl, E, s));
+int enqueue_phase2(const Launch& L, cudaStream_t s) {
+  uint32_t* c = L.counters + 20;
+  RINGO_ENQUEUE("phase2_maps", launch_phase2_maps(L, s));
+  RINGO_ENQUEUE("merge", launch_merge(L, c + 0, s));
+  RINGO_ENQUEUE("rank_blocks", launch_rank_blocks(L, c + 1, s));
+  RINGO_ENQUEUE("remap", launch_remap(L, c + 2, s));
   return RINGO_OK;
 }
 

@@ -89,7 +89,6 @@ struct SortCtl {
   uint64_t* spare;            // the other ping-pong buffer
   uint32_t hist[kOutPasses][kRadix];
   uint32_t base[kOutPasses][kRadix];
-  uint32_t tile_counter[kOutPasses];
 };
 
 struct Ctl {
@@ -97,7 +96,6 @@ struct Ctl {
   uint32_t n_rows;
   uint32_t E, Vs, Vd, V;
   uint32_t err;
-  uint32_t scan_counter[4];   // dynamic tile counters: dedup, dst_rank, merge
   // inputs
   const int32_t* src;
   const int32_t* dst;
@@ -135,22 +133,74 @@ struct Ctl {
   int64_t* in_off;
   SortCtl out_sort;
   SortCtl in_sort;
+  // used when this control block runs alone (a single table): its slot maps
+  // and claim counters
+  uint32_t solo_rows[2];
+  uint32_t solo_merge[2];
+  uint32_t solo_blocks[2];
+  uint32_t solo_counters[32];
 };
 
 constexpr uint32_t kBlkDense = 0x80000000u;
+
 constexpr int kBlkShift = 5;  // 32 map entries per block-table word
 
+// ------------------------------------------------------- multi-segment map --
+// Every pipeline kernel runs over a table of segments at once (one segment
+// for a single table, thousands for a batch): segment s owns the global tile
+// slots [start[s], start[s+1]), a multiple of kChunkTiles, and blocks claim
+// slots in increasing order from a per-launch counter, so a tile only ever
+// waits on earlier tiles of its own segment, all claimed before it.
+struct SegMap {
+  const uint32_t* start;  // [nseg + 1], device
+  uint32_t nseg;
+};
+
+// The segment table and slot maps of one run, and its claim counters.
+struct Launch {
+  Ctl* ctls;              // [nseg] device control blocks
+  SegMap rows;            // 4096-row tiles of each segment
+  SegMap merge;           // 2048-item tiles of each segment's node merge
+  SegMap blocks;          // 4096-word pieces of each segment's block tables
+  uint32_t row_slots;     // rows.start[nseg]
+  uint32_t nseg;
+  uint32_t* counters;     // [kNumCounters] device, zero at the start of a run
+};
+// merge.start and blocks.start are written on the device after phase 1
+// (from Vs and Vd); their kernels are persistent and loop over the slots.
+constexpr int kNumCounters = 32;
+
+// A single table: one segment whose maps and counters live in its own block.
+// `dctl` is the device address of the block, `h` its host copy (the row map
+// is filled in `h`, which the caller uploads).
+inline Launch solo_launch(Ctl* dctl, Ctl* h, uint32_t n_rows) {
+  const uint32_t tiles = (n_rows + kSortTile - 1) / kSortTile;
+  h->solo_rows[0] = 0;
+  h->solo_rows[1] = tiles;
+  Launch L;
+  L.ctls = dctl;
+  L.nseg = 1;
+  L.rows = SegMap{dctl->solo_rows, 1};
+  L.merge = SegMap{dctl->solo_merge, 1};
+  L.blocks = SegMap{dctl->solo_blocks, 1};
+  L.row_slots = tiles;
+  L.counters = dctl->solo_counters;
+  return L;
+}
+
 // --------------------------------------------------------- host launchers --
-// Each enqueues one kernel on `s`; `ctl` is the device copy of the block.
-void launch_histogram(Ctl* ctl, uint32_t n_rows, cudaStream_t s);
-void launch_plan(Ctl* ctl, int which, cudaStream_t s);
-void launch_onesweep(Ctl* ctl, int which, int pass, int gpass, uint32_t grid, cudaStream_t s);
-void launch_dst_rank(Ctl* ctl, uint32_t grid, cudaStream_t s);
-void launch_dedup(Ctl* ctl, uint32_t grid, cudaStream_t s);
-void launch_dst_runs(Ctl* ctl, uint32_t n_rows, cudaStream_t s);
-void launch_merge(Ctl* ctl, uint32_t grid, cudaStream_t s);
-void launch_rank_blocks(Ctl* ctl, uint32_t Vs, uint32_t Vd, cudaStream_t s);
-void launch_remap(Ctl* ctl, uint32_t E, cudaStream_t s);
+// Each enqueues one kernel on `s`; `counter` is the launch's claim counter.
+void launch_histogram(const Launch& L, uint32_t* counter, cudaStream_t s);
+void launch_plan(const Launch& L, int which, cudaStream_t s);
+void launch_onesweep(const Launch& L, int which, int pass, int gpass, uint32_t* counter,
+                     cudaStream_t s);
+void launch_dst_rank(const Launch& L, uint32_t* counter, cudaStream_t s);
+void launch_dedup(const Launch& L, uint32_t* counter, cudaStream_t s);
+void launch_dst_runs(const Launch& L, uint32_t* counter, cudaStream_t s);
+void launch_phase2_maps(const Launch& L, cudaStream_t s);
+void launch_merge(const Launch& L, uint32_t* counter, cudaStream_t s);
+void launch_rank_blocks(const Launch& L, uint32_t* counter, cudaStream_t s);
+void launch_remap(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_degrees(const int32_t* node_ids, const int64_t* off, uint32_t V,
                     const int32_t* ids, uint32_t n, int64_t* deg, cudaStream_t s);
 int launch_topk(const int32_t* node_ids, const int64_t* off, uint32_t V, uint32_t k,
@@ -161,8 +211,8 @@ size_t topk_scratch_bytes(uint32_t V, uint32_t k);
 // The launch sequence, shared by every entry point (pipeline.cu).
 //   phase 1: histogram .. destination runs; afterwards E, Vs, Vd are final
 //   phase 2: merge, block tables, remap; needs node arrays and rank maps set
-//            in the control block (by the caller, after reading Vs and Vd)
-int enqueue_phase1(Ctl* dctl, uint32_t n_rows, cudaStream_t s);
-int enqueue_phase2(Ctl* dctl, uint32_t Vs, uint32_t Vd, uint32_t E, cudaStream_t s);
+//            in every control block (sized from Vs, Vd or from upper bounds)
+int enqueue_phase1(const Launch& L, cudaStream_t s);
+int enqueue_phase2(const Launch& L, cudaStream_t s);
 
 }  // namespace ringo

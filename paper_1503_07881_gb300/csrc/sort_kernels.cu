@@ -20,6 +20,9 @@ namespace ringo {
 // ---------------------------------------------------------------- K1 ------
 // Digit histograms of all eight out-sort passes from one read of the columns.
 // Pass p looks at bits [8p, 8p+8) of key = bias(src) << 32 | bias(dst).
+// Persistent blocks claim 4096-row tiles in order and keep a shared
+// histogram while the tiles belong to one segment, adding it to that
+// segment's control block when the segment changes and at the end.
 constexpr int kHistThreads = 512;
 
 __device__ __forceinline__ void hist_row(uint32_t (*h)[kRadix], int32_t s, int32_t d) {
@@ -34,48 +37,68 @@ __device__ __forceinline__ void hist_row(uint32_t (*h)[kRadix], int32_t s, int32
   atomicAdd(&h[7][sb >> 24], 1u);
 }
 
-__global__ void __launch_bounds__(kHistThreads) k_histogram(Ctl* __restrict__ ctl) {
+__global__ void __launch_bounds__(kHistThreads)
+    k_histogram(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
   __shared__ uint32_t h[kOutPasses][kRadix];
+  __shared__ Claim cl;
+  __shared__ uint32_t cur_seg;
   for (int i = threadIdx.x; i < kOutPasses * kRadix; i += kHistThreads) (&h[0][0])[i] = 0;
-  __syncthreads();
-  const int32_t* __restrict__ src = ctl->src;
-  const int32_t* __restrict__ dst = ctl->dst;
-  const uint32_t n = ctl->n_rows;
-  const size_t stride = (size_t)gridDim.x * kHistThreads;
-  const size_t t0 = (size_t)blockIdx.x * kHistThreads + threadIdx.x;
-  const bool vec = ((((uintptr_t)src) | ((uintptr_t)dst)) & 15) == 0;
-  size_t done = 0;
-  if (vec) {
-    const size_t n4 = n / 4;
-    const int4* s4 = reinterpret_cast<const int4*>(src);
-    const int4* d4 = reinterpret_cast<const int4*>(dst);
-    for (size_t i = t0; i < n4; i += stride) {
-      const int4 a = __ldcs(s4 + i);
-      const int4 b = __ldcs(d4 + i);
-      hist_row(h, a.x, b.x);
-      hist_row(h, a.y, b.y);
-      hist_row(h, a.z, b.z);
-      hist_row(h, a.w, b.w);
+  if (threadIdx.x == 0) cur_seg = 0xFFFFFFFFu;
+  auto flush = [&](uint32_t sidx) {
+    uint32_t* dst = &ctls[sidx].out_sort.hist[0][0];
+    for (int i = threadIdx.x; i < kOutPasses * kRadix; i += kHistThreads) {
+      const uint32_t c = (&h[0][0])[i];
+      if (c) {
+        atomicAdd(dst + i, c);
+        (&h[0][0])[i] = 0;
+      }
     }
-    done = n4 * 4;
+  };
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) claim_slot(m, counter, &cl);
+    __syncthreads();
+    if (!cl.valid) break;
+    if (cl.seg != cur_seg) {
+      if (cur_seg != 0xFFFFFFFFu) flush(cur_seg);
+      __syncthreads();
+      if (threadIdx.x == 0) cur_seg = cl.seg;
+    }
+    const Ctl* ctl = ctls + cl.seg;
+    const uint32_t n = ctl->n_rows;
+    const uint32_t base = cl.tile * (uint32_t)kSortTile;
+    if (base >= n) continue;
+    const uint32_t cnt = min((uint32_t)kSortTile, n - base);
+    const int32_t* __restrict__ src = ctl->src + base;
+    const int32_t* __restrict__ dst = ctl->dst + base;
+    const bool vec = ((((uintptr_t)src) | ((uintptr_t)dst)) & 15) == 0;
+    uint32_t done = 0;
+    if (vec) {
+      const uint32_t n4 = cnt / 4;
+      for (uint32_t i = threadIdx.x; i < n4; i += kHistThreads) {
+        const int4 a = __ldcs(reinterpret_cast<const int4*>(src) + i);
+        const int4 b = __ldcs(reinterpret_cast<const int4*>(dst) + i);
+        hist_row(h, a.x, b.x);
+        hist_row(h, a.y, b.y);
+        hist_row(h, a.z, b.z);
+        hist_row(h, a.w, b.w);
+      }
+      done = n4 * 4;
+    }
+    for (uint32_t i = done + threadIdx.x; i < cnt; i += kHistThreads) hist_row(h, src[i], dst[i]);
   }
-  for (size_t i = done + t0; i < n; i += stride) hist_row(h, src[i], dst[i]);
   __syncthreads();
-
-  for (int i = threadIdx.x; i < kOutPasses * kRadix; i += kHistThreads) {
-    const uint32_t c = (&h[0][0])[i];
-    if (c) atomicAdd(&ctl->out_sort.hist[0][0] + i, c);
-  }
+  if (cur_seg != 0xFFFFFFFFu) flush(cur_seg);
 }
 
-void launch_histogram(Ctl* ctl, uint32_t n_rows, cudaStream_t s) {
+void launch_histogram(const Launch& L, uint32_t* counter, cudaStream_t s) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  uint32_t want = (n_rows + kHistThreads * 16 - 1) / (kHistThreads * 16);
-  uint32_t grid = want < (uint32_t)sms * 4 ? want : (uint32_t)sms * 4;
-  if (grid == 0) grid = 1;
-  k_histogram<<<grid, kHistThreads, 0, s>>>(ctl);
+  uint32_t grid = (uint32_t)sms * 4;
+  if (grid > L.row_slots) grid = L.row_slots;
+  if (grid == 0) return;
+  k_histogram<<<grid, kHistThreads, 0, s>>>(L.ctls, L.rows, counter);
 }
 
 // ---------------------------------------------------------------- plan ----
@@ -88,7 +111,8 @@ void launch_histogram(Ctl* ctl, uint32_t n_rows, cudaStream_t s) {
 //              columns when every dst pass was skipped); buffers keysA/keysB.
 //   which = 1: in-sort of E keys held in the out-sort's spare buffer,
 //              digits at bits 32..63 (the dst-run half).
-__global__ void __launch_bounds__(kRadix) k_plan(Ctl* __restrict__ ctl, int which) {
+__global__ void __launch_bounds__(kRadix) k_plan(Ctl* __restrict__ ctls, int which) {
+  Ctl* __restrict__ ctl = ctls + blockIdx.x;
   __shared__ uint32_t sw[kRadix / 32 + 1];
   __shared__ uint32_t trivial[kOutPasses];
   SortCtl& sc = which ? ctl->in_sort : ctl->out_sort;
@@ -139,8 +163,8 @@ __global__ void __launch_bounds__(kRadix) k_plan(Ctl* __restrict__ ctl, int whic
   sc.spare = (cur == b0) ? b1 : b0;
 }
 
-void launch_plan(Ctl* ctl, int which, cudaStream_t s) {
-  k_plan<<<1, kRadix, 0, s>>>(ctl, which);
+void launch_plan(const Launch& L, int which, cudaStream_t s) {
+  if (L.nseg) k_plan<<<L.nseg, kRadix, 0, s>>>(L.ctls, which);
 }
 
 // ---------------------------------------------------------------- K2/K4 ---
@@ -255,19 +279,19 @@ struct SweepV6Smem {
   uint32_t mask[kSortWarps][kRadix + 1];  // slot kRadix: lanes past the end
   int32_t delta[kRadix];
   uint32_t sw[kSortWarps + 1];
-  uint32_t tile;
+  Claim claim;
   uint32_t ok;
   uint64_t bar;
 };
 
 __global__ void __launch_bounds__(kSortThreads, 4)
-    k_onesweep(Ctl* __restrict__ ctl, int which, int pass, int gpass) {
+    k_onesweep(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter, int which, int pass,
+               int gpass) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   SweepV6Smem& S = *reinterpret_cast<SweepV6Smem*>(smem_raw);
-  SortCtl& sc = which ? ctl->in_sort : ctl->out_sort;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
-    S.tile = atomicAdd(&sc.tile_counter[pass], 1u);
+    claim_slot(m, counter, &S.claim);
     mbar_init(&S.bar, 1);
     mbar_init_fence();
   }
@@ -278,7 +302,10 @@ __global__ void __launch_bounds__(kSortThreads, 4)
   }
   if (tid < kSortWarps) S.mask[tid][kRadix] = 0;
   __syncthreads();
-  const uint32_t tile = S.tile;
+  if (!S.claim.valid) return;
+  Ctl* __restrict__ ctl = ctls + S.claim.seg;
+  SortCtl& sc = which ? ctl->in_sort : ctl->out_sort;
+  const uint32_t tile = S.claim.tile;
   const int reg = gpass & 1, nreg = reg ^ 1;
   if (tile < ctl->status_rows) {
     // clear this tile's row (and, for a chunk's first tile, the chunk's row)
@@ -444,14 +471,16 @@ __global__ void __launch_bounds__(kSortThreads, 4)
 
 static bool g_sweep_attr = false;
 
-void launch_onesweep(Ctl* ctl, int which, int pass, int gpass, uint32_t tiles, cudaStream_t s) {
-  if (tiles == 0) return;
+void launch_onesweep(const Launch& L, int which, int pass, int gpass, uint32_t* counter,
+                     cudaStream_t s) {
+  if (L.row_slots == 0) return;
   if (!g_sweep_attr) {
     cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(SweepV6Smem));
     g_sweep_attr = true;
   }
-  k_onesweep<<<tiles, kSortThreads, sizeof(SweepV6Smem), s>>>(ctl, which, pass, gpass);
+  k_onesweep<<<L.row_slots, kSortThreads, sizeof(SweepV6Smem), s>>>(L.ctls, L.rows, counter,
+                                                                    which, pass, gpass);
 }
 
 }  // namespace ringo
