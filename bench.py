@@ -38,6 +38,11 @@ WORKLOADS = {
           "out/in weights (exponent 2.3, max 20K), 1% duplicates, random order",
     "tiny": "1M-row edge table, 100K distinct 31-bit IDs, Zipf(1.1) src, uniform dst, "
             "5% duplicates, 0.1% self-loops",
+    "batched": "resident 200M-row base table {src, dst int32 Chung-Lu over 16M IDs, ts int64 "
+               "uniform over 5 years, tag int32 Zipf over 10K}; 4096 tag/time-window "
+               "selections, sizes log-uniform 1K-4M rows, converted as one batch",
+    "served": "the same resident base table; open-loop Poisson select+convert+top-k(100) "
+              "requests, sizes log-uniform 10K-50M rows, 120 GB budget",
 }
 # the paper's own table->graph rates (Table 5, 4x Xeon E7-4870, real graphs)
 PAPER_RATE = {"twitter": 18.0e6, "lj": 13.0e6}
@@ -281,6 +286,11 @@ def run_ours(args, world, rank, local):
                          f"(std::sort + std::unique + std::map), {dt:.1f}s"}
 
     launches = sum(p["launches"] for p in prof)
+    batched = served = None
+    if world == 1 and not (args.no_batched and args.no_served):
+        del src, dst
+        torch.cuda.empty_cache()
+        batched, served = run_base_workloads(args)
     line = {
         "metric": "table->graph edges/s",
         "value": value,
@@ -311,9 +321,225 @@ def run_ours(args, world, rank, local):
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
+        "batched": batched,
+        "served": served,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_base_only(args):
+    """--workload batched|served: one JSON line for that form alone."""
+    from paper_1503_07881_gb300 import ringo
+    ringo.load()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    batched, served = run_base_workloads(args)
+    clocks = sampler.stop()
+    if args.workload == "batched":
+        b = batched
+        ok = b and "error" not in b
+        line = {"metric": "table->graph edges/s, batched", "value": b["value"] if ok else None,
+                "unit": "edges/s", "n_gpus": 1, "steps": args.batch_steps, "warmup": 1,
+                "ms_per_step": b["ms_per_step"] if ok else None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": WORKLOADS["batched"]}, "batched": b, "clocks": clocks}
+    else:
+        line = {"metric": "served select+convert+top-k latency and edges/s", "value": None,
+                "unit": "edges/s", "n_gpus": 1, "higher_is_better": True, "dtype": "int32",
+                "data": "synthetic", "config": {"workload": WORKLOADS["served"]},
+                "served": served, "clocks": clocks}
+        if served and "error" not in served:
+            line["value"] = served["rates"][-1]["server"]["edges_per_s"]
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------ batched / served --
+BATCH_PREDS, BATCH_LO, BATCH_HI = 4096, 1_000, 4_000_000
+SERVE_LO, SERVE_HI, SERVE_TOPK, SERVE_BUDGET = 10_000, 50_000_000, 100, 120 << 30
+
+
+def load_base(seed: int):
+    """The 200M-row base table, generated on the device and loaded (clustered)."""
+    from paper_1503_07881_gb300 import ringo, tablegen
+    spec = tablegen.BaseSpec()
+    cols = tablegen.make_base_table(spec, seed=seed, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    base = ringo.BaseTable(*cols)
+    load_ms = (time.perf_counter() - t0) * 1e3
+    del cols
+    torch.cuda.empty_cache()
+    return spec, base, load_ms
+
+
+def plain_convert(ringo, base, pred, count: int, topk: int = 0):
+    """One selection converted by the plain single-table calls (the loop the
+    batched and served forms are compared with)."""
+    src, dst = base.select_gather(pred, cap=max(1, count))
+    g = ringo.ringo_table_to_graph(src, dst)
+    if topk:
+        g.degree_topk(0, topk)
+        g.degree_topk(1, topk)
+    g.free()
+
+
+def run_batched(args, spec, base, steps: int, warmup: int) -> dict:
+    from paper_1503_07881_gb300 import ringo, tablegen
+    preds = tablegen.make_predicates(spec, BATCH_PREDS, BATCH_LO, BATCH_HI, seed=args.seed)
+    counts = base.select_count(preds)
+    R = int(counts.sum())
+    peak, peak_kind = measured_peak_hbm()
+    stream = torch.cuda.current_stream()
+    info = None
+    for _ in range(max(1, warmup)):
+        bt = base.convert_batch(preds)
+        if info is None:
+            info = [bt.info(i) for i in range(len(preds))]
+        bt.free()
+    V = np.array([x["num_nodes"] for x in info], np.float64)
+    E = np.array([x["num_edges"] for x in info], np.float64)
+    N = counts.astype(np.float64)
+    b0 = float((8 * N + 20 * V + 16 * (N > 0) + 8 * E).sum())
+    bmodel = b0 + float((104 * N + 64 * E).sum())
+    torch.cuda.synchronize()
+    ringo.ringo_profile_start()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        base.convert_batch(preds).free()
+    end.record(stream)
+    torch.cuda.synchronize()
+    prof = ringo.ringo_profile_stop()
+    ms = start.elapsed_time(end) / steps
+    waves = sum(p["launches"] for p in prof if p["name"] == "batch_wave") // steps
+    # the plain loop: select, gather and convert each table on its own
+    for i in range(min(64, len(preds))):
+        plain_convert(ringo, base, preds[i], int(counts[i]))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, p in enumerate(preds):
+        plain_convert(ringo, base, p, int(counts[i]))
+    torch.cuda.synchronize()
+    plain_ms = (time.perf_counter() - t0) * 1e3
+    return {
+        "workload": WORKLOADS["batched"], "predicates": len(preds), "selected_rows": R,
+        "base_rows": spec.rows, "base_load_ms": None, "steps": steps,
+        "ms_per_step": round(ms, 3), "value": R / (ms / 1e3), "unit": "edges/s",
+        "waves_per_step": waves, "graphs_per_wave_launch": "one CUDA graph per wave",
+        "b0_frac": b0 / (ms / 1e3) / 1e9 / peak, "model_frac": bmodel / (ms / 1e3) / 1e9 / peak,
+        "peak_gbs": peak, "peak_source": peak_kind,
+        "plain_loop": {"ms": round(plain_ms, 1), "value": R / (plain_ms / 1e3),
+                       "unit": "edges/s",
+                       "calls": "select_count + select_gather + ringo_table_to_graph per table"},
+        "speedup_vs_plain": plain_ms / ms,
+    }
+
+
+def poisson_arrivals(rate: float, duration: float, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    n = int(rate * duration * 1.2) + 16
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    return t[t < duration]
+
+
+def serve_with_server(ringo, base, preds, arrivals, workers: int) -> dict:
+    import threading
+    srv = ringo.Server(base, SERVE_BUDGET, workers=workers)
+    tickets = [None] * len(preds)
+    results = [None] * len(preds)
+    t0 = ringo.clock_ns() + 20_000_000
+
+    def collect():
+        for i in range(len(preds)):
+            while tickets[i] is None:
+                time.sleep(0.0002)
+            results[i] = srv.wait(tickets[i])
+
+    th = threading.Thread(target=collect)
+    th.start()
+    for i, p in enumerate(preds):
+        due = t0 + int(arrivals[i] * 1e9)
+        while True:
+            dt = due - ringo.clock_ns()
+            if dt <= 0:
+                break
+            time.sleep(min(dt / 1e9, 0.001) if dt > 200_000 else 0)
+        tickets[i] = srv.submit(p, topk=SERVE_TOPK)
+    th.join()
+    st = srv.stats()
+    srv.close()
+    lat = np.array([(r["t_done_ns"] - (t0 + int(a * 1e9))) / 1e6 for r, a in zip(results, arrivals)])
+    rows = sum(r["nrows"] for r in results)
+    span = (max(r["t_done_ns"] for r in results) - t0) / 1e9
+    bad = sum(r["status"] != 0 for r in results)
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "edges_per_s": rows / span, "failed": bad,
+            "batches": st["batches"], "mean_batch": len(preds) / max(1, st["batches"]),
+            "max_concurrent_batches": st["max_concurrent_batches"],
+            "max_inflight_gb": st["max_inflight_bytes"] / 1e9}
+
+
+def serve_plain(ringo, base, preds, arrivals) -> dict:
+    counts = base.select_count(preds)
+    t0 = ringo.clock_ns() + 20_000_000
+    lat = []
+    for i, p in enumerate(preds):
+        due = t0 + int(arrivals[i] * 1e9)
+        while ringo.clock_ns() < due:
+            time.sleep(0.0002)
+        plain_convert(ringo, base, p, int(counts[i]), SERVE_TOPK)
+        lat.append((ringo.clock_ns() - due) / 1e6)
+    span = (ringo.clock_ns() - t0) / 1e9
+    lat = np.array(lat)
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "edges_per_s": float(counts.sum()) / span}
+
+
+def run_served(args, spec, base, rates, duration: float) -> dict:
+    from paper_1503_07881_gb300 import ringo, tablegen
+    out = []
+    for k, rate in enumerate(rates):
+        arr = poisson_arrivals(rate, duration, args.seed + k)
+        preds = tablegen.make_predicates(spec, len(arr), SERVE_LO, SERVE_HI, seed=args.seed + 100 + k)
+        warm = tablegen.make_predicates(spec, 8, SERVE_LO, SERVE_HI, seed=args.seed + 999)
+        srv = ringo.Server(base, SERVE_BUDGET)
+        for p in warm:
+            srv.wait(srv.submit(p, topk=SERVE_TOPK))
+        srv.close()
+        server = serve_with_server(ringo, base, preds, arr, workers=2)
+        plain = serve_plain(ringo, base, preds, arr)
+        out.append({"rate_per_s": rate, "duration_s": duration, "requests": len(preds),
+                    "server": server, "plain_loop": plain,
+                    "p99_speedup_vs_plain": plain["p99_ms"] / server["p99_ms"]})
+    return {"workload": WORKLOADS["served"], "budget_bytes": SERVE_BUDGET, "topk": SERVE_TOPK,
+            "latency": "scheduled arrival to result ready (no coordinated omission)",
+            "rates": out}
+
+
+def run_base_workloads(args) -> tuple[dict | None, dict | None]:
+    """Batched and served runs on the resident base table."""
+    batched = served = None
+    only = args.workload in ("batched", "served")
+    do_batched = args.workload == "batched" or (not only and not args.no_batched)
+    do_served = args.workload == "served" or (not only and not args.no_served)
+    spec, base, load_ms = load_base(args.seed)
+    try:
+        if do_batched:
+            try:
+                batched = run_batched(args, spec, base, steps=args.batch_steps, warmup=1)
+                batched["base_load_ms"] = round(load_ms, 1)
+            except Exception as e:  # reported, not fatal to the plain line
+                batched = {"error": f"{type(e).__name__}: {e}"}
+        if do_served:
+            try:
+                served = run_served(args, spec, base, args.serve_rates, args.serve_seconds)
+            except Exception as e:
+                served = {"error": f"{type(e).__name__}: {e}"}
+    finally:
+        base.free()
+        torch.cuda.empty_cache()
+    return batched, served
 
 
 # ------------------------------------------------------- reference arm ----
@@ -324,6 +550,8 @@ def run_reference(args, rank):
     import oracle
     from paper_1503_07881_gb300 import tablegen
 
+    if args.workload in ("batched", "served"):
+        return run_reference_base(args)
     spec = tablegen.SPECS[args.workload]
     S = min(spec.rows, REF_SAMPLE_ROWS[args.workload])
     n_slices = args.warmup + args.steps
@@ -364,6 +592,51 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_base(args):
+    """The oracle on the selections of a bounded base table of the same shape
+    (1M rows, 10K Zipf tags, five years of timestamps): each step converts
+    the next batch of selections, host-side select included."""
+    import oracle
+    from paper_1503_07881_gb300 import tablegen
+
+    spec = tablegen.BaseSpec(rows=1_000_000, nodes=80_000, tags=10_000)
+    src, dst, ts, tag = (c.numpy() for c in tablegen.make_base_table(spec, seed=args.seed))
+    lo, hi = (BATCH_LO, BATCH_HI) if args.workload == "batched" else (SERVE_LO, SERVE_HI)
+    scale = spec.rows / tablegen.BaseSpec().rows
+    preds = tablegen.make_predicates(spec, 64 * (args.warmup + args.steps),
+                                     max(1, int(lo * scale)), max(2, int(hi * scale)),
+                                     seed=args.seed)
+
+    def step(ps):
+        rows = 0
+        for tags, t0, t1 in ps:
+            m = np.isin(tag, np.asarray(tags, np.int32)) & (ts >= t0) & (ts < t1)
+            oracle.table_to_graph(src[m], dst[m])
+            rows += int(m.sum())
+        return rows
+
+    for k in range(args.warmup):
+        step(preds[64 * k:64 * (k + 1)])
+    t0 = time.perf_counter()
+    rows = 0
+    for k in range(args.warmup, args.warmup + args.steps):
+        rows += step(preds[64 * k:64 * (k + 1)])
+    dt = time.perf_counter() - t0
+    value = rows / dt
+    line = {"impl": "reference", "metric": f"table->graph edges/s, {args.workload}",
+            "value": value, "unit": "edges/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload],
+                       "note": "64 selections per step from a 1M-row base table of the same shape"},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": "64 selections per step, sizes scaled by 1/200"},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,6 +647,12 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched summary")
+    ap.add_argument("--no-served", action="store_true", help="skip the served summary")
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--serve-rates", type=lambda x: [float(v) for v in x.split(",")],
+                    default=[100.0, 500.0])
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
     args = ap.parse_args()
     if args.warmup < 3:
         log("note: fewer than 3 warm-up steps requested; using 3")
@@ -383,7 +662,11 @@ def main():
         return
     world, rank, local = dist_setup(args)
     try:
-        run_ours(args, world, rank, local)
+        if args.workload in ("batched", "served"):
+            if rank == 0:
+                run_base_only(args)
+        else:
+            run_ours(args, world, rank, local)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -178,6 +178,209 @@ RINGO_API int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* ds
                                            int64_t node_capacity, int64_t edge_capacity,
                                            int64_t* num_nodes, int64_t* num_edges);
 
+/* ------------------------------------------------------------------------
+ * Base tables, selection and batched conversion.
+ *
+ * The paper builds graphs from tables after relational operations such as
+ * select (Section 3.3 "Tables in Ringo"; rows keep persistent IDs there so
+ * that selections can work in place).  A base table of edge rows with a
+ * timestamp and a tag is loaded once and kept resident on the device,
+ * clustered by (tag, ts); a predicate (a set of tags and a time window)
+ * selects a sub-table, and a batch converts many selected sub-tables
+ * (Section 3.4) at once, every kernel running over all of them.
+ * ---------------------------------------------------------------------- */
+typedef struct ringo_base ringo_base;
+typedef struct ringo_batch ringo_batch;
+
+/* A predicate: the rows with tag in tags[0 .. ntags) and t0 <= ts < t1.
+ * tags is a caller-owned host array read during the call only; a repeated
+ * value counts once; ntags == 0 or t1 <= t0 selects nothing. */
+typedef struct {
+  const int32_t* tags;
+  int32_t ntags;
+  int64_t t0;
+  int64_t t1;
+} ringo_select;
+
+/*
+ * ringo_base_table_load -- copy a base table of nrows rows from device
+ * columns src, dst (int32 node IDs), ts (int64) and tag (int32), all of
+ * length nrows and caller-owned, into library-owned device memory clustered
+ * by (tag, ts) (two stable radix sorts; equal keys keep their row order).
+ * The caller's columns are only read and may be freed on return.  Blocks
+ * until done; *out owns the copy until ringo_base_table_free.
+ * Errors: EINVAL (NULL out, nrows < 0, NULL column with nrows > 0), ERANGE
+ * (nrows >= 2^31, or max(ts) - min(ts) >= 2^32), ENOMEM, ECUDA.
+ */
+RINGO_API int ringo_base_table_load(const int32_t* src, const int32_t* dst, const int64_t* ts,
+                                    const int32_t* tag, int64_t nrows, void* stream,
+                                    ringo_base** out);
+/* Row count of a loaded base table (EINVAL on NULL). */
+RINGO_API int ringo_base_table_rows(const ringo_base* b, int64_t* nrows);
+/* Releases the table (waits for the device); NULL is a no-op. */
+RINGO_API void ringo_base_table_free(ringo_base* b);
+
+/*
+ * ringo_select_count -- the number of rows each of preds[0 .. npred)
+ * selects, written to the host array counts[npred].  One binary search per
+ * (predicate, tag) pair on the device; blocks until done.
+ * Errors: EINVAL (NULL b, NULL preds or counts with npred > 0, npred < 0,
+ * ntags < 0, NULL tags with ntags > 0), ENOMEM, ECUDA.
+ */
+RINGO_API int ringo_select_count(const ringo_base* b, const ringo_select* preds, int32_t npred,
+                                 void* stream, int64_t* counts);
+
+/*
+ * ringo_select_gather -- the rows one predicate selects, written as an edge
+ * table into caller-owned device columns d_src[cap], d_dst[cap]: the tags in
+ * ascending order, each tag's rows in ts order.  *n receives the row count.
+ * Errors: as ringo_select_count; ERANGE if the count exceeds cap (nothing is
+ * written, *n still holds the count).
+ */
+RINGO_API int ringo_select_gather(const ringo_base* b, const ringo_select* pred, int32_t* d_src,
+                                  int32_t* d_dst, int64_t cap, int64_t* n, void* stream);
+
+/*
+ * ringo_convert_batch -- select and convert npred sub-tables in one batch:
+ * graph i is the Section 3.4 conversion of the rows predicate i selects,
+ * identical to ringo_table_to_graph of those rows.  All kernels run over
+ * every sub-table at once; predicates are taken in order in waves of at most
+ * `wave_rows` selected rows (0: the tuned or memory-derived size, see
+ * ringo_batch_autotune; a larger single selection forms a wave of its own),
+ * which bounds the scratch memory.  Each wave is recorded as one
+ * CUDA graph and launched once.  Blocks until done; *out owns the npred
+ * graphs until ringo_batch_free.
+ * Errors: as ringo_select_count; ERANGE (a selection of 2^31 rows or more),
+ * ETIMEOUT (a bounded device wait expired), ENOMEM, ECUDA.  On error *out is
+ * NULL and nothing is left allocated.
+ */
+RINGO_API int ringo_convert_batch(const ringo_base* b, const ringo_select* preds, int32_t npred,
+                                  int64_t wave_rows, void* stream, ringo_batch** out);
+/*
+ * ringo_batch_autotune -- picks the wave size for this predicate set: times
+ * ringo_convert_batch with up to four candidate sizes (the largest that fits
+ * in device memory, then halves, not below 2^24 rows) and keeps the fastest
+ * for later ringo_convert_batch calls with wave_rows == 0 on the same device,
+ * predicate count and row-count octave.  Without a tuned choice, wave_rows ==
+ * 0 means the largest wave that fits in 85% of the available device memory.
+ * Errors: as ringo_convert_batch; ENOMEM if no candidate fits.
+ */
+RINGO_API int ringo_batch_autotune(const ringo_base* b, const ringo_select* preds, int32_t npred,
+                                   void* stream, int64_t* best_wave_rows, double* best_ms);
+/* Number of graphs in a batch (= npred). */
+RINGO_API int ringo_batch_num_graphs(const ringo_batch* bt, int32_t* n);
+/* Sizes and pass counts of graph i, as ringo_graph_get_info gives them for
+ * a single graph (EINVAL if i is out of range). */
+RINGO_API int ringo_batch_graph_info(const ringo_batch* bt, int32_t i, ringo_graph_info* info);
+/* Copies graph i to caller-owned host arrays sized from ringo_batch_graph_info
+ * (node_ids[V], offsets[V + 1], neighbours[E]); a NULL array is skipped. */
+RINGO_API int ringo_batch_copy_graph_to_host(const ringo_batch* bt, int32_t i,
+                                             int32_t* h_node_ids, int64_t* h_out_off,
+                                             int32_t* h_out_nbr, int64_t* h_in_off,
+                                             int32_t* h_in_nbr);
+/* Top-k degrees of graph i (same contract as ringo_graph_degree_topk). */
+RINGO_API int ringo_batch_degree_topk(const ringo_batch* bt, int32_t i, int dir, int32_t k,
+                                      int32_t* h_ids, int64_t* h_degs, int32_t* n_out);
+/* Releases every graph of the batch; NULL is a no-op. */
+RINGO_API void ringo_batch_free(ringo_batch* bt);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop over a resident base table.
+ *
+ * A request is select (a predicate as above) + convert (Section 3.4) + the
+ * top-k degrees of the graph in both directions.  Worker threads, each with
+ * its own CUDA stream, take every request that has arrived when they become
+ * free (continuous batching), count the rows each selects, admit requests in
+ * arrival order while the device bytes of everything in flight stay within
+ * the budget, and run the admitted requests as one wave of the batched
+ * pipeline (one CUDA graph).  A request's result is identical to converting
+ * its selection alone.  The paper has no serving layer; this is the
+ * interactive use of Sections 3.3-3.4 (queries against resident tables).
+ * ---------------------------------------------------------------------- */
+typedef struct ringo_server ringo_server;
+typedef struct ringo_result ringo_result;
+
+typedef struct {
+  int32_t workers;         /* concurrent batches (threads and streams); 0: 2, at most 16 */
+  int32_t max_batch;       /* requests per batch; 0: 1024 */
+  int64_t max_batch_rows;  /* selected rows per batch (a larger single request
+                              runs alone); 0: 2^28 */
+} ringo_server_config;
+
+/* submit flag: keep the converted graph with the result (its bytes stay
+ * charged to the budget until ringo_result_free). */
+#define RINGO_SERVE_KEEP_GRAPH 1
+
+typedef struct {
+  int32_t status;          /* RINGO_OK, ENOMEM (larger than the whole budget),
+                              ERANGE (2^31 rows or more), ETIMEOUT, ECUDA */
+  int32_t batch_requests;  /* requests in the batch that served it */
+  int64_t batch_rows;      /* selected rows of that batch */
+  int64_t nrows;           /* rows this request selected */
+  int64_t num_nodes;       /* V of its graph */
+  int64_t num_edges;       /* E of its graph */
+  int32_t k_out, k_in;     /* entries in the two top-k lists (min(k, V)) */
+  int64_t t_submit_ns;     /* ringo_clock_ns() at submit, admission, completion */
+  int64_t t_admit_ns;
+  int64_t t_done_ns;
+} ringo_result_info;
+
+typedef struct {
+  int64_t submitted, completed, failed;
+  int64_t batches;                 /* waves run */
+  int64_t rows;                    /* selected rows converted */
+  int64_t max_concurrent_batches;  /* most batches in flight at once */
+  int64_t inflight_bytes;          /* bytes charged to the budget now */
+  int64_t max_inflight_bytes;      /* and at most */
+  int64_t pending;                 /* submitted, not yet admitted */
+} ringo_server_stats;
+
+/* Monotonic clock (nanoseconds) of the result timestamps. */
+RINGO_API int64_t ringo_clock_ns(void);
+
+/*
+ * ringo_server_create -- starts the workers on the current device.  b stays
+ * owned by the caller and must outlive the server.  cfg may be NULL
+ * (defaults).  Errors: EINVAL (NULL b or out, budget <= 0, negative config
+ * field), ERANGE (more than 16 workers).
+ */
+RINGO_API int ringo_server_create(const ringo_base* b, int64_t hbm_budget_bytes,
+                                  const ringo_server_config* cfg, ringo_server** out);
+/*
+ * ringo_server_submit -- queues one request (the predicate's tags are copied)
+ * and returns at once with its ticket.  0 <= topk <= 4096 (ERANGE above);
+ * flags 0 or RINGO_SERVE_KEEP_GRAPH.  EBUSY once the server is stopping.
+ */
+RINGO_API int ringo_server_submit(ringo_server* srv, const ringo_select* pred, int32_t topk,
+                                  int32_t flags, uint64_t* ticket);
+/*
+ * ringo_server_wait -- waits up to timeout_us (< 0: no limit) for a ticket's
+ * result and hands it to the caller (free with ringo_result_free).  ETIMEOUT
+ * if not ready (the ticket stays valid); ENOTFOUND for an unknown or already
+ * claimed ticket.  A request's own failure is reported in its info.status.
+ */
+RINGO_API int ringo_server_wait(ringo_server* srv, uint64_t ticket, int64_t timeout_us,
+                                ringo_result** out);
+RINGO_API int ringo_server_get_stats(const ringo_server* srv, ringo_server_stats* st);
+/* Finishes every submitted request, stops the workers and frees the results
+ * nobody claimed.  A request that cannot be admitted because kept graphs the
+ * caller still holds fill the budget ends with status EBUSY.  NULL is a
+ * no-op. */
+RINGO_API void ringo_server_destroy(ringo_server* srv);
+
+RINGO_API int ringo_result_get_info(const ringo_result* r, ringo_result_info* info);
+/* Top-k of one direction into caller-owned host arrays of cap entries,
+ * degree descending then ID ascending; ERANGE if cap < *n_out. */
+RINGO_API int ringo_result_topk(const ringo_result* r, int dir, int32_t* h_ids, int64_t* h_degs,
+                                int32_t cap, int32_t* n_out);
+/* The kept graph (RINGO_SERVE_KEEP_GRAPH only, else EINVAL), as
+ * ringo_batch_copy_graph_to_host. */
+RINGO_API int ringo_result_copy_graph_to_host(const ringo_result* r, int32_t* h_node_ids,
+                                              int64_t* h_out_off, int32_t* h_out_nbr,
+                                              int64_t* h_in_off, int32_t* h_in_nbr);
+/* Frees a result (and its kept graph, returning its bytes to the budget). */
+RINGO_API void ringo_result_free(ringo_result* r);
+
 /*
  * Kernel timing.  While profiling is on, every kernel the library launches is
  * bracketed by CUDA events on its own stream.  ringo_profile_stop()

@@ -56,6 +56,13 @@ void* pool_alloc(size_t bytes, cudaStream_t s) {
   void* p = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync(&p, bytes ? bytes : 256, pool, s);
   if (e != cudaSuccess) {
+    // the pool keeps freed memory; give back what is unused and retry once
+    cudaGetLastError();
+    cudaStreamSynchronize(s);
+    cudaMemPoolTrimTo(pool, 0);
+    e = cudaMallocFromPoolAsync(&p, bytes ? bytes : 256, pool, s);
+  }
+  if (e != cudaSuccess) {
     cudaGetLastError();
     set_error(std::string("device allocation of ") + std::to_string(bytes) +
               " bytes failed: " + cudaGetErrorString(e));
@@ -66,6 +73,25 @@ void* pool_alloc(size_t bytes, cudaStream_t s) {
 
 void pool_free(void* p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
+}
+
+// Device bytes a new allocation can get: free device memory plus what the
+// pool holds unused.
+uint64_t pool_available() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  uint64_t held = 0, used = 0;
+  cudaMemPool_t pool = device_pool(dev);
+  if (pool) {
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &held);
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+  }
+  return (uint64_t)free_b + (held > used ? held - used : 0);
 }
 
 // ------------------------------------------------------------ pinned ------
@@ -121,6 +147,11 @@ bool profiling_enabled() { return g_prof_on; }
 
 ProfScope::ProfScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
   if (!g_prof_on) return;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s_, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;  // kernels recorded into a graph are timed around the graph launch
+  }
   std::lock_guard<std::mutex> lk(g_prof_mu);
   start_ = get_event();
   cudaEventRecord(start_, s_);

@@ -17,6 +17,8 @@ const char* last_error();
 // cached for the next call.  Returns nullptr on failure (message recorded).
 void* pool_alloc(size_t bytes, cudaStream_t s);
 void pool_free(void* p, cudaStream_t s);
+// Free device memory plus the pool's cached, unused bytes.
+uint64_t pool_available();
 
 // Pinned host staging buffers, cached and reused.
 void* pinned_get(size_t bytes);

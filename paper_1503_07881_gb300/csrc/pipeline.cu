@@ -47,6 +47,18 @@ int enqueue_phase1(const Launch& L, cudaStream_t s) {
   return RINGO_OK;
 }
 
+int enqueue_sort_only(const Launch& L, cudaStream_t s) {
+  uint32_t* c = L.counters;
+  int k = 0;
+  RINGO_ENQUEUE("histogram", launch_histogram(L, c + k++, s));
+  RINGO_ENQUEUE("plan", launch_plan(L, 0, s));
+  for (int p = 0; p < 4; ++p) RINGO_ENQUEUE("onesweep", launch_onesweep(L, 0, p, p, c + k++, s));
+  RINGO_ENQUEUE("dst_rank", launch_dst_rank(L, c + k++, s));
+  for (int p = 4; p < kOutPasses; ++p)
+    RINGO_ENQUEUE("onesweep", launch_onesweep(L, 0, p, p, c + k++, s));
+  return RINGO_OK;
+}
+
 // merge into the node list, block tables of the two rank maps, remap.
 int enqueue_phase2(const Launch& L, cudaStream_t s) {
   uint32_t* c = L.counters + 20;

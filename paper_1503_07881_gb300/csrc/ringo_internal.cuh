@@ -91,7 +91,7 @@ struct SortCtl {
   uint32_t base[kOutPasses][kRadix];
 };
 
-struct Ctl {
+struct alignas(16) Ctl {
   // sizes (device-side truth)
   uint32_t n_rows;
   uint32_t E, Vs, Vd, V;
@@ -214,5 +214,10 @@ size_t topk_scratch_bytes(uint32_t V, uint32_t k);
 //            in every control block (sized from Vs, Vd or from upper bounds)
 int enqueue_phase1(const Launch& L, cudaStream_t s);
 int enqueue_phase2(const Launch& L, cudaStream_t s);
+// histogram, plan, the four dst passes, the rank step, the four src passes:
+// the out-sort alone (its keys end in out_sort.result)
+int enqueue_sort_only(const Launch& L, cudaStream_t s);
+// one-time kernel attributes, set before any stream capture
+void prepare_launches();
 
 }  // namespace ringo

@@ -12,6 +12,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
+
 #include "device_util.cuh"
 #include "ringo_internal.cuh"
 
@@ -469,16 +472,26 @@ __global__ void __launch_bounds__(kSortThreads, 4)
   }
 }
 
-static bool g_sweep_attr = false;
+static std::mutex g_sweep_attr_mu;
+static uint64_t g_sweep_attr_devs = 0;  // bit d: set on device d
+
+// The onesweep kernel's dynamic shared memory limit, set once per device
+// (not a stream operation, so it must happen before any stream capture).
+void prepare_launches() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_sweep_attr_mu);
+  if (dev < 64 && !((g_sweep_attr_devs >> dev) & 1)) {
+    cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(SweepV6Smem));
+    g_sweep_attr_devs |= 1ull << dev;
+  }
+}
 
 void launch_onesweep(const Launch& L, int which, int pass, int gpass, uint32_t* counter,
                      cudaStream_t s) {
   if (L.row_slots == 0) return;
-  if (!g_sweep_attr) {
-    cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(SweepV6Smem));
-    g_sweep_attr = true;
-  }
+  prepare_launches();
   k_onesweep<<<L.row_slots, kSortThreads, sizeof(SweepV6Smem), s>>>(L.ctls, L.rows, counter,
                                                                     which, pass, gpass);
 }

@@ -71,6 +71,28 @@ SIGNATURES = {
     "ringo_graph_free": (None, [_P]),
     "ringo_table_to_graph_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P, _P, _P, _I64,
                                                     _I64, _P, _P]),
+    "ringo_base_table_load": (ctypes.c_int, [_P, _P, _P, _P, _I64, _P, _PP]),
+    "ringo_base_table_rows": (ctypes.c_int, [_P, _P]),
+    "ringo_base_table_free": (None, [_P]),
+    "ringo_select_count": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
+    "ringo_select_gather": (ctypes.c_int, [_P, _P, _P, _P, _I64, _P, _P]),
+    "ringo_convert_batch": (ctypes.c_int, [_P, _P, _I32, _I64, _P, _PP]),
+    "ringo_batch_autotune": (ctypes.c_int, [_P, _P, _I32, _P, _P, _P]),
+    "ringo_batch_num_graphs": (ctypes.c_int, [_P, _P]),
+    "ringo_batch_graph_info": (ctypes.c_int, [_P, _I32, ctypes.POINTER(GraphInfo)]),
+    "ringo_batch_copy_graph_to_host": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _P]),
+    "ringo_batch_degree_topk": (ctypes.c_int, [_P, _I32, ctypes.c_int, _I32, _P, _P, _P]),
+    "ringo_batch_free": (None, [_P]),
+    "ringo_clock_ns": (ctypes.c_int64, []),
+    "ringo_server_create": (ctypes.c_int, [_P, _I64, _P, _PP]),
+    "ringo_server_submit": (ctypes.c_int, [_P, _P, _I32, _I32, ctypes.POINTER(ctypes.c_uint64)]),
+    "ringo_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, _I64, _PP]),
+    "ringo_server_get_stats": (ctypes.c_int, [_P, _P]),
+    "ringo_server_destroy": (None, [_P]),
+    "ringo_result_get_info": (ctypes.c_int, [_P, _P]),
+    "ringo_result_topk": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _I32, _P]),
+    "ringo_result_copy_graph_to_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "ringo_result_free": (None, [_P]),
     "ringo_profile_start": (ctypes.c_int, []),
     "ringo_profile_stop": (ctypes.c_int, [ctypes.POINTER(KernelStat), _I32, _P]),
 }
@@ -312,3 +334,238 @@ def ringo_table_to_graph_noalloc(src: torch.Tensor, dst: torch.Tensor, out: dict
         out["node_ids"].numel(), min(out["out_nbr"].numel(), out["in_nbr"].numel()),
         ctypes.byref(v), ctypes.byref(e)), "ringo_table_to_graph_noalloc")
     return v.value, e.value
+
+
+# ------------------------------------------------------------ batches ------
+class SelectC(ctypes.Structure):
+    _fields_ = [("tags", ctypes.POINTER(ctypes.c_int32)), ("ntags", ctypes.c_int32),
+                ("t0", ctypes.c_int64), ("t1", ctypes.c_int64)]
+
+
+def _preds_c(preds):
+    """Marshal [(tags, t0, t1), ...] into a ringo_select array (kept alive by
+    the returned tuple)."""
+    keep = []
+    arr = (SelectC * max(1, len(preds)))()
+    for i, (tags, t0, t1) in enumerate(preds):
+        t = np.ascontiguousarray(np.asarray(tags, np.int32))
+        keep.append(t)
+        arr[i].tags = t.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        arr[i].ntags = t.size
+        arr[i].t0 = int(t0)
+        arr[i].t1 = int(t1)
+    return arr, keep
+
+
+class BaseTable:
+    """A resident base table (src, dst, ts, tag) clustered by (tag, ts)."""
+
+    def __init__(self, src: torch.Tensor, dst: torch.Tensor, ts: torch.Tensor, tag: torch.Tensor,
+                 stream=None):
+        n = src.numel()
+        if not (dst.numel() == ts.numel() == tag.numel() == n):
+            raise ValueError("columns differ in length")
+        if ts.dtype != torch.int64 or not ts.is_cuda:
+            raise ValueError("ts must be a CUDA int64 tensor")
+        h = ctypes.c_void_p()
+        _check(load().ringo_base_table_load(
+            _col_ptr(src, "src") if n else None, _col_ptr(dst, "dst") if n else None,
+            ts.data_ptr() if n else None, _col_ptr(tag, "tag") if n else None, n,
+            _stream_ptr(stream), ctypes.byref(h)), "ringo_base_table_load")
+        self._h = h
+        self.nrows = n
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().ringo_base_table_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def select_count(self, preds, stream=None) -> np.ndarray:
+        arr, keep = _preds_c(preds)
+        out = np.zeros(max(1, len(preds)), np.int64)
+        _check(load().ringo_select_count(self._h, arr, len(preds), _stream_ptr(stream),
+                                         out.ctypes.data), "ringo_select_count")
+        return out[:len(preds)]
+
+    def select_gather(self, pred, cap: int, stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+        arr, keep = _preds_c([pred])
+        src = torch.empty(max(1, cap), dtype=torch.int32, device="cuda")
+        dst = torch.empty(max(1, cap), dtype=torch.int32, device="cuda")
+        n = ctypes.c_int64()
+        _check(load().ringo_select_gather(self._h, arr, src.data_ptr(), dst.data_ptr(), cap,
+                                          ctypes.byref(n), _stream_ptr(stream)),
+               "ringo_select_gather")
+        return src[:n.value], dst[:n.value]
+
+    def autotune(self, preds, stream=None) -> tuple[int, float]:
+        """Times candidate wave sizes on these predicates; later convert_batch
+        calls with wave_rows=0 use the fastest.  Returns (wave_rows, ms)."""
+        arr, keep = _preds_c(preds)
+        w = ctypes.c_int64()
+        ms = ctypes.c_double()
+        _check(load().ringo_batch_autotune(self._h, arr, len(preds), _stream_ptr(stream),
+                                           ctypes.byref(w), ctypes.byref(ms)),
+               "ringo_batch_autotune")
+        return w.value, ms.value
+
+    def convert_batch(self, preds, wave_rows: int = 0, stream=None) -> "Batch":
+        arr, keep = _preds_c(preds)
+        h = ctypes.c_void_p()
+        _check(load().ringo_convert_batch(self._h, arr, len(preds), int(wave_rows),
+                                          _stream_ptr(stream), ctypes.byref(h)),
+               "ringo_convert_batch")
+        return Batch(h.value)
+
+
+class Batch:
+    """Owner of a ringo_batch*: one graph per predicate."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().ringo_batch_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __len__(self) -> int:
+        n = ctypes.c_int32()
+        _check(load().ringo_batch_num_graphs(self._h, ctypes.byref(n)), "ringo_batch_num_graphs")
+        return n.value
+
+    def info(self, i: int) -> dict:
+        gi = GraphInfo()
+        _check(load().ringo_batch_graph_info(self._h, i, ctypes.byref(gi)),
+               "ringo_batch_graph_info")
+        return {f: getattr(gi, f) for f, _ in GraphInfo._fields_}
+
+    def copy_to_host(self, i: int) -> dict:
+        inf = self.info(i)
+        V, E = inf["num_nodes"], inf["num_edges"]
+        out = {"node_ids": np.empty(V, np.int32), "out_off": np.empty(V + 1, np.int64),
+               "out_nbr": np.empty(E, np.int32), "in_off": np.empty(V + 1, np.int64),
+               "in_nbr": np.empty(E, np.int32)}
+        _check(load().ringo_batch_copy_graph_to_host(
+            self._h, i, out["node_ids"].ctypes.data, out["out_off"].ctypes.data,
+            out["out_nbr"].ctypes.data, out["in_off"].ctypes.data, out["in_nbr"].ctypes.data),
+            "ringo_batch_copy_graph_to_host")
+        out["num_nodes"], out["num_edges"] = V, E
+        return out
+
+    def degree_topk(self, i: int, direction: int, k: int) -> tuple[np.ndarray, np.ndarray]:
+        ids = np.zeros(max(k, 1), np.int32)
+        degs = np.zeros(max(k, 1), np.int64)
+        n = ctypes.c_int32()
+        _check(load().ringo_batch_degree_topk(self._h, i, direction, int(k), ids.ctypes.data,
+                                              degs.ctypes.data, ctypes.byref(n)),
+               "ringo_batch_degree_topk")
+        return ids[:n.value].copy(), degs[:n.value].copy()
+
+
+# ------------------------------------------------------------- serving -----
+RINGO_SERVE_KEEP_GRAPH = 1
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("max_batch_rows", ctypes.c_int64)]
+
+
+class ResultInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("batch_requests", ctypes.c_int32),
+                ("batch_rows", ctypes.c_int64), ("nrows", ctypes.c_int64),
+                ("num_nodes", ctypes.c_int64), ("num_edges", ctypes.c_int64),
+                ("k_out", ctypes.c_int32), ("k_in", ctypes.c_int32),
+                ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in (
+        "submitted", "completed", "failed", "batches", "rows", "max_concurrent_batches",
+        "inflight_bytes", "max_inflight_bytes", "pending")]
+
+
+def clock_ns() -> int:
+    """The monotonic clock of the server's timestamps."""
+    return int(load().ringo_clock_ns())
+
+
+class Server:
+    """Request server over a resident BaseTable (select + convert + top-k)."""
+
+    def __init__(self, base: BaseTable, budget_bytes: int, workers: int = 0, max_batch: int = 0,
+                 max_batch_rows: int = 0):
+        cfg = ServerConfig(workers, max_batch, max_batch_rows)
+        h = ctypes.c_void_p()
+        _check(load().ringo_server_create(base._h, int(budget_bytes), ctypes.byref(cfg),
+                                          ctypes.byref(h)), "ringo_server_create")
+        self._h = h
+        self._base = base  # the base table must outlive the server
+        self._kept = set()
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().ringo_server_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def submit(self, pred, topk: int = 100, keep_graph: bool = False) -> int:
+        arr, keep = _preds_c([pred])
+        t = ctypes.c_uint64()
+        _check(load().ringo_server_submit(self._h, arr, int(topk),
+                                          RINGO_SERVE_KEEP_GRAPH if keep_graph else 0,
+                                          ctypes.byref(t)), "ringo_server_submit")
+        if keep_graph:
+            self._kept.add(t.value)
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> dict:
+        """The result of a ticket as a dict (info fields, top-k lists and, for
+        keep_graph requests, the graph's host arrays)."""
+        lib = load()
+        r = ctypes.c_void_p()
+        _check(lib.ringo_server_wait(self._h, ticket, int(timeout_us), ctypes.byref(r)),
+               "ringo_server_wait")
+        try:
+            inf = ResultInfo()
+            _check(lib.ringo_result_get_info(r, ctypes.byref(inf)), "ringo_result_get_info")
+            out = {f: getattr(inf, f) for f, _ in ResultInfo._fields_}
+            for d, name in ((RINGO_OUT, "topk_out"), (RINGO_IN, "topk_in")):
+                k = out["k_out"] if d == RINGO_OUT else out["k_in"]
+                ids = np.zeros(max(k, 1), np.int32)
+                degs = np.zeros(max(k, 1), np.int64)
+                n = ctypes.c_int32()
+                _check(lib.ringo_result_topk(r, d, ids.ctypes.data, degs.ctypes.data, k,
+                                             ctypes.byref(n)), "ringo_result_topk")
+                out[name] = (ids[:n.value].copy(), degs[:n.value].copy())
+            out["graph"] = None
+            kept = ticket in self._kept
+            self._kept.discard(ticket)
+            if kept and out["status"] == RINGO_OK:
+                V, E = out["num_nodes"], out["num_edges"]
+                g = {"node_ids": np.empty(V, np.int32), "out_off": np.empty(V + 1, np.int64),
+                     "out_nbr": np.empty(E, np.int32), "in_off": np.empty(V + 1, np.int64),
+                     "in_nbr": np.empty(E, np.int32)}
+                rc = lib.ringo_result_copy_graph_to_host(
+                    r, g["node_ids"].ctypes.data, g["out_off"].ctypes.data,
+                    g["out_nbr"].ctypes.data, g["in_off"].ctypes.data, g["in_nbr"].ctypes.data)
+                if rc == RINGO_OK:
+                    g["num_nodes"], g["num_edges"] = V, E
+                    out["graph"] = g
+            return out
+        finally:
+            lib.ringo_result_free(r)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load().ringo_server_get_stats(self._h, ctypes.byref(st)), "ringo_server_get_stats")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}

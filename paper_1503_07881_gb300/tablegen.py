@@ -264,3 +264,74 @@ def signed_table(rows: int, nodes: int, seed: int = 1, device="cpu") -> tuple:
     d = ids[_draw(uniform32(j, seed, 25), nodes, (None, None))]
     d = torch.where(uniform32(j, seed, 26) < int(0.01 * TWO32), s, d)
     return s.to(torch.int32), d.to(torch.int32)
+
+
+# ------------------------------------------------------------ base tables --
+FIVE_YEARS = 5 * 365 * 24 * 3600
+TS0 = 1_420_070_400  # 2015-01-01T00:00:00Z, seconds
+
+
+@dataclasses.dataclass(frozen=True)
+class BaseSpec:
+    """A resident base table {src, dst, ts, tag}: src/dst drawn Chung-Lu style
+    from truncated power-law weights (as in the LiveJournal shape), ts uniform
+    over five years (seconds), tag Zipf(s) over `tags` values."""
+    rows: int = 200_000_000
+    nodes: int = 16_000_000
+    tags: int = 10_000
+    tag_s: float = 1.0
+
+
+def make_base_table(spec: BaseSpec = BaseSpec(), seed: int = 1, device="cpu",
+                    chunk: int = 1 << 25):
+    device = torch.device(device)
+    edge = TableSpec("base", spec.rows, spec.nodes, ("powerlaw", 2.3, 20_000.0),
+                     ("powerlaw", 2.3, 20_000.0), 0.0, 0.0)
+    src, dst = make_table(edge, seed=seed, device=device, chunk=chunk)
+    ts = torch.empty(spec.rows, dtype=torch.int64, device=device)
+    tag = torch.empty(spec.rows, dtype=torch.int32, device=device)
+    tag_t = torch.from_numpy(zipf_thresholds(spec.tags, spec.tag_s)).to(device)
+    for lo in range(0, spec.rows, chunk):
+        hi = min(spec.rows, lo + chunk)
+        i = torch.arange(lo, hi, dtype=torch.int64, device=device)
+        ts[lo:hi] = TS0 + ((uniform32(i, seed, 41) * FIVE_YEARS) >> 32)
+        tag[lo:hi] = torch.clamp(torch.searchsorted(tag_t, uniform32(i, seed, 42), right=True),
+                                 max=spec.tags - 1).to(torch.int32)
+    return src, dst, ts, tag
+
+
+def tag_row_counts(spec: BaseSpec) -> np.ndarray:
+    """Expected rows per tag (Zipf shares of the row count)."""
+    r = np.arange(1, spec.tags + 1, dtype=np.float64)
+    w = r ** (-spec.tag_s)
+    return spec.rows * w / w.sum()
+
+
+def make_predicates(spec: BaseSpec, npred: int, lo: int, hi: int, seed: int = 1,
+                    max_tags: int = 8):
+    """Predicates (tags, t0, t1) whose expected selection sizes are
+    log-uniform in [lo, hi]: tags are added in a random order until their rows
+    reach the target, then the time window is the matching fraction of five
+    years at a random start."""
+    rng = np.random.default_rng(seed)
+    counts = tag_row_counts(spec)
+    preds = []
+    for _ in range(npred):
+        target = float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        order = rng.integers(0, spec.tags, 4 * max_tags)
+        tags, total = [], 0.0
+        for t in order:
+            if total >= target or len(tags) >= max_tags:
+                break
+            if int(t) in tags:
+                continue
+            tags.append(int(t))
+            total += counts[t]
+        if total < target:  # take the biggest tags instead
+            tags = [int(t) for t in np.argsort(-counts)[:max_tags]]
+            total = float(counts[tags].sum())
+        frac = min(1.0, target / total)
+        span = max(1, int(frac * FIVE_YEARS))
+        t0 = TS0 + int(rng.integers(0, max(1, FIVE_YEARS - span + 1)))
+        preds.append((sorted(tags), t0, t0 + span))
+    return preds
