@@ -147,6 +147,20 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- roofline ---
+def host_cpu() -> dict:
+    """The host the CPU baseline ran on: logical cores and CPU model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
 def measured_peak_hbm() -> tuple[float, str]:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -281,7 +295,7 @@ def run_ours(args, world, rank, local):
         t1 = time.perf_counter()
         oracle.table_to_graph(s_h, d_h)
         dt = time.perf_counter() - t1
-        cpu = {"value": S / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": S / dt, "unit": "edges/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"first {S} rows of the same table, one oracle run "
                          f"(std::sort + std::unique + std::map), {dt:.1f}s"}
 
@@ -413,6 +427,10 @@ def run_batched(args, spec, base, steps: int, warmup: int) -> dict:
     prof = ringo.ringo_profile_stop()
     ms = start.elapsed_time(end) / steps
     waves = sum(p["launches"] for p in prof if p["name"] == "batch_wave") // steps
+    if args.no_plain:
+        return {"workload": WORKLOADS["batched"], "predicates": len(preds), "selected_rows": R,
+                "ms_per_step": round(ms, 3), "value": R / (ms / 1e3), "unit": "edges/s",
+                "waves_per_step": waves}
     # the plain loop: select, gather and convert each table on its own
     for i in range(min(64, len(preds))):
         plain_convert(ringo, base, preds[i], int(counts[i]))
@@ -457,6 +475,7 @@ def serve_with_server(ringo, base, preds, arrivals, workers: int) -> dict:
             results[i] = srv.wait(tickets[i])
 
     th = threading.Thread(target=collect)
+    ringo.ringo_profile_start()
     th.start()
     for i, p in enumerate(preds):
         due = t0 + int(arrivals[i] * 1e9)
@@ -469,6 +488,9 @@ def serve_with_server(ringo, base, preds, arrivals, workers: int) -> dict:
     th.join()
     st = srv.stats()
     srv.close()
+    prof = {p["name"]: {"n": p["launches"], "ms": round(p["total_ms"], 2)}
+            for p in ringo.ringo_profile_stop()
+            if p["name"].startswith("host:") or p["name"] == "batch_wave"}
     lat = np.array([(r["t_done_ns"] - (t0 + int(a * 1e9))) / 1e6 for r, a in zip(results, arrivals)])
     rows = sum(r["nrows"] for r in results)
     span = (max(r["t_done_ns"] for r in results) - t0) / 1e9
@@ -477,7 +499,7 @@ def serve_with_server(ringo, base, preds, arrivals, workers: int) -> dict:
             "mean_ms": float(lat.mean()), "edges_per_s": rows / span, "failed": bad,
             "batches": st["batches"], "mean_batch": len(preds) / max(1, st["batches"]),
             "max_concurrent_batches": st["max_concurrent_batches"],
-            "max_inflight_gb": st["max_inflight_bytes"] / 1e9}
+            "max_inflight_gb": st["max_inflight_bytes"] / 1e9, "time_split": prof}
 
 
 def serve_plain(ringo, base, preds, arrivals) -> dict:
@@ -650,6 +672,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched summary")
     ap.add_argument("--no-served", action="store_true", help="skip the served summary")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the plain per-table loop of the batched run (profiling)")
     ap.add_argument("--serve-rates", type=lambda x: [float(v) for v in x.split(",")],
                     default=[100.0, 500.0])
     ap.add_argument("--serve-seconds", type=float, default=4.0)

@@ -383,9 +383,11 @@ RINGO_API void ringo_result_free(ringo_result* r);
 
 /*
  * Kernel timing.  While profiling is on, every kernel the library launches is
- * bracketed by CUDA events on its own stream.  ringo_profile_stop()
- * synchronises those events and returns, per kernel name, the number of
- * launches and their summed device time.
+ * bracketed by CUDA events on its own stream (kernels recorded into a CUDA
+ * graph are timed together, as "batch_wave"), and a few host steps are timed
+ * by the wall clock (names starting "host:").  ringo_profile_stop()
+ * synchronises the events and returns, per name, the number of launches and
+ * their summed time in milliseconds.
  */
 typedef struct {
   char name[48];

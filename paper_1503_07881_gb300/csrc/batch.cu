@@ -264,23 +264,34 @@ __global__ void k_select(const int32_t* __restrict__ tag_c, const int64_t* __res
 }
 
 // Copy the selected ranges into one input array: pair i's rows go to
-// [out_off[i], out_off[i] + cnt[i]).  Each thread copies eight consecutive
-// output rows (one binary search for the first).
-__global__ void k_gather(const int32_t* __restrict__ src_c, const int32_t* __restrict__ dst_c,
-                         const uint32_t* __restrict__ lo, const uint32_t* __restrict__ cnt,
-                         const uint64_t* __restrict__ out_off, uint32_t npairs, uint64_t total,
-                         int32_t* __restrict__ src, int32_t* __restrict__ dst) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * 8;
-  for (uint64_t r0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; r0 < total;
-       r0 += stride) {
-    uint32_t a = 0, b = npairs;  // last pair with out_off <= r0
-    while (b - a > 1) {
-      const uint32_t mid = (a + b) >> 1;
-      if (out_off[mid] <= r0) a = mid;
-      else b = mid;
+// [out_off[i], out_off[i] + cnt[i]).  A block copies 2048 consecutive output
+// rows (row r0 + t + 256 k by thread t): one thread finds the pair of the
+// block's first row by binary search, and each thread steps forward from it
+// (a block spans few pairs), so the copies are coalesced on both sides.
+constexpr uint32_t kGatherRows = 2048;
+
+__global__ void __launch_bounds__(256)
+    k_gather(const int32_t* __restrict__ src_c, const int32_t* __restrict__ dst_c,
+             const uint32_t* __restrict__ lo, const uint32_t* __restrict__ cnt,
+             const uint64_t* __restrict__ out_off, uint32_t npairs, uint64_t total,
+             int32_t* __restrict__ src, int32_t* __restrict__ dst) {
+  __shared__ uint32_t s_pair;
+  for (uint64_t r0 = (uint64_t)blockIdx.x * kGatherRows; r0 < total;
+       r0 += (uint64_t)gridDim.x * kGatherRows) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t a = 0, b = npairs;  // last pair with out_off <= r0
+      while (b - a > 1) {
+        const uint32_t mid = (a + b) >> 1;
+        if (out_off[mid] <= r0) a = mid;
+        else b = mid;
+      }
+      s_pair = a;
     }
-    uint32_t pi = a;
-    for (uint64_t r = r0; r < r0 + 8 && r < total; ++r) {
+    __syncthreads();
+    uint32_t pi = s_pair;
+    const uint64_t r1 = min(r0 + kGatherRows, total);
+    for (uint64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
       while (pi + 1 < npairs && out_off[pi + 1] <= r) ++pi;
       const uint64_t k = r - out_off[pi];
       if (k >= cnt[pi]) continue;  // alignment gap after a segment
@@ -567,9 +578,11 @@ std::vector<Pair> make_pairs(const ringo_select* preds, int32_t npred) {
   return pairs;
 }
 
-int select_ranges(const ringo_base* b, const std::vector<Pair>& pairs, cudaStream_t s, Ranges* r) {
+int select_ranges(const ringo_base* b, const std::vector<Pair>& pairs, cudaStream_t s, Ranges* r,
+                  bool host_lo) {
   const uint32_t np = (uint32_t)pairs.size();
   r->h_cnt.assign(np, 0);
+  if (host_lo) r->h_lo.assign(np, 0);
   if (np == 0) return RINGO_OK;
   const size_t bytes = al(sizeof(Pair) * np) + 2 * al(4ull * np);
   char* d = (char*)pool_alloc(bytes, s);
@@ -585,6 +598,8 @@ int select_ranges(const ringo_base* b, const std::vector<Pair>& pairs, cudaStrea
     RINGO_CUDA_TRY(cudaMemsetAsync(r->cnt, 0, 4ull * np, s));
   }
   RINGO_CUDA_TRY(cudaMemcpyAsync(r->h_cnt.data(), r->cnt, 4ull * np, cudaMemcpyDeviceToHost, s));
+  if (host_lo && b->n)
+    RINGO_CUDA_TRY(cudaMemcpyAsync(r->h_lo.data(), r->lo, 4ull * np, cudaMemcpyDeviceToHost, s));
   RINGO_CUDA_TRY(cudaStreamSynchronize(s));
   return RINGO_OK;
 }
@@ -594,8 +609,8 @@ int select_ranges(const ringo_base* b, const std::vector<Pair>& pairs, cudaStrea
 // gather, the whole pipeline and (topk > 0) the segmented top-k of both
 // directions are recorded as one CUDA graph and launched once on s.
 int run_wave(const ringo_base* b, const uint32_t* d_lo, const uint32_t* d_cnt,
-             const uint32_t* h_cnt, const std::vector<size_t>& first, uint32_t nseg, uint32_t topk,
-             cudaStream_t s, WaveResult* out) {
+             const uint32_t* h_lo, const uint32_t* h_cnt, const std::vector<size_t>& first,
+             uint32_t nseg, uint32_t topk, cudaStream_t s, WaveResult* out) {
   out->seg.assign(nseg, WaveSeg{});
   if (nseg == 0) return RINGO_OK;
   prepare_launches();
@@ -624,8 +639,10 @@ int run_wave(const ringo_base* b, const uint32_t* d_lo, const uint32_t* d_cnt,
   const uint64_t meta = zmeta + al(4ull * (nseg + 1)) * 4 + al(sizeof(SegResult) * nseg);
   const uint64_t tk_bytes = (uint64_t)ntasks * topk;
   char* zr = (char*)pool_alloc(zb + meta, s);
+  const bool up_ranges = d_lo == nullptr;  // ranges come from the host
   char* sr = (char*)pool_alloc(sb + al(sizeof(Ctl) * nseg) + al(sizeof(SegDesc) * nseg) +
-                                   al(8 * (npw + 1)) + al(8 * in_rows) + al(8 * tk_bytes),
+                                   al(8 * (npw + 1)) + al(8 * in_rows) + al(8 * tk_bytes) +
+                                   (up_ranges ? 2 * al(4 * (npw + 1)) : 0),
                                s);
   char* orr = (char*)pool_alloc(ob + al(4 * tk_bytes) + al(8 * tk_bytes), s);
   const size_t hbytes = sizeof(SegResult) * nseg + 12 * tk_bytes + 16;
@@ -653,6 +670,11 @@ int run_wave(const ringo_base* b, const uint32_t* d_lo, const uint32_t* d_cnt,
   int32_t* in_src = (int32_t*)((char*)d_pairoff + al(8 * (npw + 1)));
   int32_t* in_dst = in_src + in_rows;  // two int32 halves of the 8 * in_rows bytes
   uint64_t* d_cand = (uint64_t*)((char*)in_src + al(8 * in_rows));
+  if (up_ranges) {
+    char* rp = (char*)d_cand + al(8 * tk_bytes);
+    d_lo = (const uint32_t*)rp;
+    d_cnt = (const uint32_t*)(rp + al(4 * (npw + 1)));
+  }
   int32_t* d_tk_ids = (int32_t*)(orr + ob);
   int64_t* d_tk_degs = (int64_t*)(orr + ob + al(4 * tk_bytes));
   // per-pair output offsets inside the wave's input columns
@@ -677,14 +699,23 @@ int run_wave(const ringo_base* b, const uint32_t* d_lo, const uint32_t* d_cnt,
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
-  // small host data goes up first, outside the graph
-  ok = ok && cudaMemcpyAsync(d_desc, desc.data(), sizeof(SegDesc) * nseg,
-                             cudaMemcpyHostToDevice, s) == cudaSuccess;
-  ok = ok && cudaMemcpyAsync(d_rows, row_start.data(), 4ull * (nseg + 1),
-                             cudaMemcpyHostToDevice, s) == cudaSuccess;
-  ok = ok && cudaMemcpyAsync(d_pairoff, pair_off.data(), 8 * (npw + 1), cudaMemcpyHostToDevice,
-                             s) == cudaSuccess;
-  ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+  {
+    // small host data goes up first, outside the graph
+    HostScope hs("host:wave_upload");
+    ok = ok && cudaMemcpyAsync(d_desc, desc.data(), sizeof(SegDesc) * nseg,
+                               cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(d_rows, row_start.data(), 4ull * (nseg + 1),
+                               cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(d_pairoff, pair_off.data(), 8 * (npw + 1),
+                               cudaMemcpyHostToDevice, s) == cudaSuccess;
+    if (up_ranges && npw) {
+      ok = ok && cudaMemcpyAsync(const_cast<uint32_t*>(d_lo), h_lo, 4 * npw,
+                                 cudaMemcpyHostToDevice, s) == cudaSuccess;
+      ok = ok && cudaMemcpyAsync(const_cast<uint32_t*>(d_cnt), h_cnt, 4 * npw,
+                                 cudaMemcpyHostToDevice, s) == cudaSuccess;
+    }
+    ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+  }
   Launch L;
   L.ctls = d_ctls;
   L.nseg = nseg;
@@ -694,11 +725,12 @@ int run_wave(const ringo_base* b, const uint32_t* d_lo, const uint32_t* d_cnt,
   L.row_slots = row_start[nseg];
   L.counters = d_counters;
   int prc = RINGO_OK;
+  HostScope* cap_scope = new HostScope("host:wave_capture");
   if (ok) ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   if (ok) {
     cudaMemsetAsync(zr, 0, zb + zmeta, cs);
     if (npw)
-      k_gather<<<grid_for(in_rows, 256 * 8), 256, 0, cs>>>(b->src_c, b->dst_c, d_lo, d_cnt,
+      k_gather<<<grid_for(in_rows, kGatherRows), 256, 0, cs>>>(b->src_c, b->dst_c, d_lo, d_cnt,
                                                            d_pairoff, (uint32_t)npw, in_rows,
                                                            in_src, in_dst);
     k_init_ctls<<<nseg, 256, 0, cs>>>(d_ctls, d_desc);
@@ -723,7 +755,12 @@ int run_wave(const ringo_base* b, const uint32_t* d_lo, const uint32_t* d_cnt,
     const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     ok = prc == RINGO_OK && ce == cudaSuccess;
   }
-  ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  delete cap_scope;
+  {
+    HostScope hs("host:wave_instantiate");
+    ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  }
+  HostScope* run_scope = new HostScope("host:wave_run");
   {
     ProfScope ps("batch_wave", s);
     ok = ok && cudaGraphLaunch(exec, s) == cudaSuccess;
@@ -739,6 +776,7 @@ int run_wave(const ringo_base* b, const uint32_t* d_lo, const uint32_t* d_cnt,
                    cudaSuccess;
   }
   ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+  delete run_scope;
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
   if (cs) cudaStreamDestroy(cs);
@@ -967,7 +1005,7 @@ int ringo_select_gather(const ringo_base* b, const ringo_select* pred, int32_t* 
       return RINGO_ENOMEM;
     }
     cudaMemcpyAsync(doff, off.data(), 8 * off.size(), cudaMemcpyHostToDevice, s);
-    k_gather<<<grid_for(total, 256 * 8), 256, 0, s>>>(b->src_c, b->dst_c, rg.lo, rg.cnt, doff,
+    k_gather<<<grid_for(total, kGatherRows), 256, 0, s>>>(b->src_c, b->dst_c, rg.lo, rg.cnt, doff,
                                                       (uint32_t)pairs.size(), total, d_src, d_dst);
     const cudaError_t e1 = cudaGetLastError();
     const cudaError_t e2 = cudaStreamSynchronize(s);
@@ -1028,7 +1066,7 @@ int ringo_convert_batch(const ringo_base* b, const ringo_select* preds, int32_t 
     std::vector<size_t> wf(z - a + 1);
     for (int32_t k = a; k <= z; ++k) wf[k - a] = first[k] - first[a];
     WaveResult w;
-    rc = run_wave(b, rg.lo + first[a], rg.cnt + first[a], rg.h_cnt.data() + first[a], wf,
+    rc = run_wave(b, rg.lo + first[a], rg.cnt + first[a], nullptr, rg.h_cnt.data() + first[a], wf,
                   (uint32_t)(z - a), 0, s, &w);
     if (w.block) bt->blocks.push_back(w.block);
     if (rc != RINGO_OK) break;

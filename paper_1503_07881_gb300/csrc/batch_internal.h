@@ -41,6 +41,7 @@ struct Ranges {
   uint32_t* lo = nullptr;
   uint32_t* cnt = nullptr;
   std::vector<uint32_t> h_cnt;
+  std::vector<uint32_t> h_lo;  // filled when asked for
 };
 
 // One converted segment of a wave: its sizes and its arrays inside the
@@ -65,14 +66,17 @@ struct WaveResult {
 int check_preds(const ringo_select* preds, int32_t npred);
 // One pair per distinct tag of each predicate, in predicate order.
 std::vector<Pair> make_pairs(const ringo_select* preds, int32_t npred);
-// Binary searches of all pairs on s; blocks until h_cnt is on the host.  The
-// caller frees r->block (also on error).
-int select_ranges(const ringo_base* b, const std::vector<Pair>& pairs, cudaStream_t s, Ranges* r);
+// Binary searches of all pairs on s; blocks until h_cnt (and, if host_lo,
+// h_lo) is on the host.  The caller frees r->block (also on error).
+int select_ranges(const ringo_base* b, const std::vector<Pair>& pairs, cudaStream_t s, Ranges* r,
+                  bool host_lo = false);
 // Converts one wave: segment j holds pairs [first[j], first[j + 1]) of the
-// range arrays.  topk > 0 adds the top-k of both directions of every graph.
+// range arrays (device d_lo/d_cnt, or, with d_lo == nullptr, host h_lo/h_cnt
+// uploaded with the wave's other small tables).  topk > 0 adds the top-k of
+// both directions of every graph.
 int run_wave(const ringo_base* b, const uint32_t* d_lo, const uint32_t* d_cnt,
-             const uint32_t* h_cnt, const std::vector<size_t>& first, uint32_t nseg, uint32_t topk,
-             cudaStream_t s, WaveResult* out);
+             const uint32_t* h_lo, const uint32_t* h_cnt, const std::vector<size_t>& first,
+             uint32_t nseg, uint32_t topk, cudaStream_t s, WaveResult* out);
 // Device bytes one segment of n rows takes in a wave (scratch and outputs),
 // an upper bound used for admission by memory budget.
 uint64_t wave_seg_bytes(uint32_t n, uint32_t topk);

@@ -33,7 +33,7 @@ __device__ __forceinline__ ScanChunks chunks_of(const Ctl* ctl, int i) {
 //   out_nbr[e]               = dst-run index (turned into a node index later)
 //   usrc[s], usrc_start[s]   = src ID and its first edge; usrc_start[Vs] = E
 //   in_sort.hist             = digit histograms of the in-sort passes
-__global__ void __launch_bounds__(kScanThreads)
+__global__ void __launch_bounds__(kScanThreads, 4)
     k_dedup(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
   __shared__ uint32_t s_hist[kInPasses][kRadix];
   __shared__ uint32_t s_we[kWarps], s_ws[kWarps];
@@ -51,6 +51,10 @@ __global__ void __launch_bounds__(kScanThreads)
   if (tile >= ntiles) return;
   const uint64_t* __restrict__ keys = ctl->out_sort.result;
   const uint32_t wbase = tile * (uint32_t)kScanTile + warp * (kScanItems * 32);
+  // in-sort digit positions that can vary: dst-run indices are below Vd
+  const uint32_t Vd = ctl->Vd;
+  int npos = 1;
+  while (npos < kInPasses && ((Vd - 1) >> (8 * npos)) != 0) ++npos;
 
   uint64_t key[kScanItems];
   uint32_t valid = 0;
@@ -65,7 +69,6 @@ __global__ void __launch_bounds__(kScanThreads)
 
   const uint32_t lt = lanemask_lt();
   uint32_t he = 0, hs = 0, ce = 0, cs = 0;
-  uint16_t eloc[kScanItems], sloc[kScanItems];
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, key[i], 1);
@@ -76,12 +79,8 @@ __global__ void __launch_bounds__(kScanThreads)
     const bool first = pos == 0;
     const bool h_e = ok && (first || key[i] != prev);
     const bool h_s = ok && (first || (key[i] >> 32) != (prev >> 32));
-    const uint32_t be = __ballot_sync(0xFFFFFFFFu, h_e);
-    const uint32_t bs = __ballot_sync(0xFFFFFFFFu, h_s);
-    eloc[i] = (uint16_t)(ce + __popc(be & lt));
-    sloc[i] = (uint16_t)(cs + __popc(bs & lt));
-    ce += __popc(be);
-    cs += __popc(bs);
+    ce += __popc(__ballot_sync(0xFFFFFFFFu, h_e));
+    cs += __popc(__ballot_sync(0xFFFFFFFFu, h_s));
     he |= (uint32_t)h_e << i;
     hs |= (uint32_t)h_s << i;
   }
@@ -109,6 +108,8 @@ __global__ void __launch_bounds__(kScanThreads)
         ctl->E = E;
         ctl->Vs = Vs;
         ctl->usrc_start[Vs] = (int32_t)E;
+        // positions that cannot vary hold every edge in digit 0
+        for (int p = npos; p < kInPasses; ++p) ctl->in_sort.hist[p][0] = E;
       }
     }
   }
@@ -119,20 +120,31 @@ __global__ void __launch_bounds__(kScanThreads)
   int32_t* __restrict__ out_nbr = ctl->out_nbr;
   int32_t* __restrict__ usrc = ctl->usrc;
   int32_t* __restrict__ usrc_start = ctl->usrc_start;
+  const int top = npos - 1;
+  uint32_t ce2 = 0, cs2 = 0;  // heads of earlier items of this warp (positions recomputed)
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    if (!((he >> i) & 1u)) continue;
-    const uint32_t e = e0 + eloc[i];
-    const uint32_t s = s0 + sloc[i];
+    const bool h = (he >> i) & 1u;
     const bool head_s = (hs >> i) & 1u;
-    const uint32_t sidx = head_s ? s : s - 1;
     const uint32_t db = (uint32_t)key[i];
+    const uint32_t emask = __ballot_sync(0xFFFFFFFFu, h);
+    const uint32_t smask = __ballot_sync(0xFFFFFFFFu, head_s);
+    const uint32_t e = e0 + ce2 + __popc(emask & lt);
+    const uint32_t s = s0 + cs2 + __popc(smask & lt);
+    ce2 += __popc(emask);
+    cs2 += __popc(smask);
+    // the highest varying position takes few values: one add per value per
+    // warp instead of up to 32 colliding adds on one counter
+    if (h) {
+      const uint32_t td = (db >> (8 * top)) & 0xFFu;
+      const uint32_t peers = __match_any_sync(emask, td);
+      if (lane == 31 - __clz(peers)) atomicAdd(&s_hist[top][td], (uint32_t)__popc(peers));
+    }
+    if (!h) continue;
+    const uint32_t sidx = head_s ? s : s - 1;
     ekeys[e] = ((uint64_t)db << 32) | sidx;
     out_nbr[e] = (int32_t)db;
-    atomicAdd(&s_hist[0][db & 0xFF], 1u);
-    atomicAdd(&s_hist[1][(db >> 8) & 0xFF], 1u);
-    atomicAdd(&s_hist[2][(db >> 16) & 0xFF], 1u);
-    atomicAdd(&s_hist[3][db >> 24], 1u);
+    for (int p = 0; p < top; ++p) atomicAdd(&s_hist[p][(db >> (8 * p)) & 0xFFu], 1u);
     if (head_s) {
       usrc[s] = unbias((uint32_t)(key[i] >> 32));
       usrc_start[s] = (int32_t)e;
@@ -157,7 +169,7 @@ void launch_dedup(const Launch& L, uint32_t* counter, cudaStream_t s) {
 // Reads rank_step.in (or packs from the columns when every dst pass was
 // trivial) and writes rank_step.out.  Single-pass compaction count with
 // decoupled look-back.
-__global__ void __launch_bounds__(kScanThreads)
+__global__ void __launch_bounds__(kScanThreads, 4)
     k_dst_rank(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
   __shared__ uint32_t s_w[kWarps];
   __shared__ uint64_t s_prefix;
@@ -196,7 +208,6 @@ __global__ void __launch_bounds__(kScanThreads)
   if (wbase > 0 && wbase <= n) before = key_at(wbase - 1);
   const uint32_t lt = lanemask_lt();
   uint32_t hd = 0, cd = 0;
-  uint16_t dloc[kScanItems];
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, key[i], 1);
@@ -205,9 +216,7 @@ __global__ void __launch_bounds__(kScanThreads)
     const uint32_t pos = wbase + i * 32 + lane;
     const bool ok = (valid >> i) & 1u;
     const bool h = ok && (pos == 0 || (uint32_t)key[i] != (uint32_t)prev);
-    const uint32_t b = __ballot_sync(0xFFFFFFFFu, h);
-    dloc[i] = (uint16_t)(cd + __popc(b & lt));
-    cd += __popc(b);
+    cd += __popc(__ballot_sync(0xFFFFFFFFu, h));
     hd |= (uint32_t)h << i;
   }
   if (lane == 0) s_w[warp] = cd;
@@ -228,11 +237,15 @@ __global__ void __launch_bounds__(kScanThreads)
   __syncthreads();
   const uint32_t d0 = unpackB(s_prefix) + s_w[warp];
   int32_t* __restrict__ udst = ctl->udst;
+  uint32_t cd2 = 0;  // heads of earlier items of this warp
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    if (!((valid >> i) & 1u)) continue;
     const bool h = (hd >> i) & 1u;
-    const uint32_t r = d0 + dloc[i] + (h ? 0u : 0xFFFFFFFFu);  // inclusive count - 1
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, h);
+    const uint32_t dl = cd2 + __popc(b & lt);
+    cd2 += __popc(b);
+    if (!((valid >> i) & 1u)) continue;
+    const uint32_t r = d0 + dl + (h ? 0u : 0xFFFFFFFFu);  // inclusive count - 1
     __stcs(out + wbase + i * 32 + lane, (key[i] & 0xFFFFFFFF00000000ull) | r);
     if (h) udst[r] = unbias((uint32_t)key[i]);
   }
@@ -287,9 +300,8 @@ void launch_dst_runs(const Launch& L, uint32_t* counter, cudaStream_t s) {
 //   out_off[r] = usrc_start[i]   and   in_off[r] = udst_start[j],
 // which holds for nodes in both lists and for nodes in only one of them.
 // Also src_rank[i] and dst_rank[j]: the node index of each list entry.
-__device__ __forceinline__ uint32_t merge_path(const int32_t* __restrict__ a, uint32_t na,
-                                               const int32_t* __restrict__ b, uint32_t nb,
-                                               uint32_t diag) {
+__device__ __forceinline__ uint32_t merge_path(const int32_t* a, uint32_t na, const int32_t* b,
+                                               uint32_t nb, uint32_t diag) {
   uint32_t lo = diag > nb ? diag - nb : 0;
   uint32_t hi = diag < na ? diag : na;
   while (lo < hi) {
@@ -300,48 +312,100 @@ __device__ __forceinline__ uint32_t merge_path(const int32_t* __restrict__ a, ui
   return lo;
 }
 
-__device__ __forceinline__ void merge_tile(Ctl* __restrict__ ctl, uint32_t tile, uint32_t* s_sw,
-                                           uint64_t* s_prefix) {
+// One merge tile: kMergeTile consecutive items of the merged order, between
+// the splits found by k_merge_split.
+// The tile's slices of usrc / udst and of their run starts are loaded into
+// shared memory (coalesced), each thread merges kMergeItems items from there,
+// and the outputs are staged so that node_ids, both offset arrays and both
+// rank maps are written coalesced.
+struct MergeSmem {
+  int32_t val[kMergeTile];        // usrc[i0, i1) then udst[j0, j1)
+  int32_t start[kMergeTile + 2];  // usrc_start[i0, i1] then udst_start[j0, j1]
+  int32_t rank[kMergeTile];       // tile-local node index of each input item
+  uint32_t node[kMergeTile];      // emitted nodes: i | j << 12 | from_src << 24 (local)
+  uint32_t sw[kWarps + 1];
+  int32_t prev;                   // usrc[i0 - 1]
+  uint32_t has_prev;
+  uint64_t prefix;
+};
+
+// The merge path splits of every merge tile of every table, before the
+// merge: one binary search per tile start, all of them in parallel.  The
+// splits go to the radix key buffer, which phase 2 no longer uses.
+__global__ void __launch_bounds__(256)
+    k_merge_split(Ctl* __restrict__ ctls, SegMap m) {
+  const uint32_t total = __ldg(m.start + m.nseg);
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += gridDim.x * blockDim.x) {
+    const uint32_t sidx = seg_of(m, g);
+    Ctl* __restrict__ ctl = ctls + sidx;
+    const uint32_t t = g - __ldg(m.start + sidx);
+    const uint32_t Vs = ctl->Vs, Vd = ctl->Vd;
+    const uint32_t diag = t * (uint32_t)kMergeTile;
+    if (diag >= Vs + Vd) continue;
+    merge_splits(ctl)[t] = merge_path(ctl->usrc, Vs, ctl->udst, Vd, diag);
+  }
+}
+
+__device__ __forceinline__ void merge_tile(Ctl* __restrict__ ctl, uint32_t tile, MergeSmem& S) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t Vs = ctl->Vs, Vd = ctl->Vd, M = Vs + Vd;
   const uint32_t ntiles = (M + kMergeTile - 1) / kMergeTile;
   if (tile >= ntiles) return;
   const int32_t* __restrict__ usrc = ctl->usrc;
   const int32_t* __restrict__ udst = ctl->udst;
-  const uint32_t k0 = tile * (uint32_t)kMergeTile + tid * kMergeItems;
-  int32_t x[kMergeItems];
-  uint32_t ci[kMergeItems], cj[kMergeItems];
-  uint32_t emit = 0, from_src = 0, cnt = 0, used = 0;
-  if (k0 < M) {
-    uint32_t i = merge_path(usrc, Vs, udst, Vd, k0);
-    uint32_t j = k0 - i;
+  const uint32_t k0 = tile * (uint32_t)kMergeTile;
+  const uint32_t k1 = min(k0 + (uint32_t)kMergeTile, M);
+  const uint32_t* __restrict__ split = merge_splits(ctl);
+  const uint32_t i0 = split[tile];
+  const uint32_t i1 = tile + 1 < ntiles ? split[tile + 1] : Vs;
+  const uint32_t j0 = k0 - i0, j1 = k1 - i1;
+  const uint32_t na = i1 - i0, nb = j1 - j0;
+  const int32_t* __restrict__ us = ctl->usrc_start;
+  const int32_t* __restrict__ ud = ctl->udst_start;
+  for (uint32_t t = tid; t < na; t += kScanThreads) S.val[t] = usrc[i0 + t];
+  for (uint32_t t = tid; t < nb; t += kScanThreads) S.val[na + t] = udst[j0 + t];
+  for (uint32_t t = tid; t <= na; t += kScanThreads) S.start[t] = us[i0 + t];
+  for (uint32_t t = tid; t <= nb; t += kScanThreads) S.start[na + 1 + t] = ud[j0 + t];
+  if (tid == 0) {
+    S.has_prev = i0 > 0 ? 1u : 0u;
+    S.prev = i0 > 0 ? usrc[i0 - 1] : 0;
+  }
+  __syncthreads();
+  const int32_t* sa = S.val;
+  const int32_t* sb = S.val + na;
+  const uint32_t nloc = na + nb;
+  const uint32_t d0 = tid * kMergeItems;
+  uint32_t lij[kMergeItems];  // local cursors i | j << 16 (each at most 2048)
+  uint32_t emit = 0, from_src = 0, used = 0;
+  if (d0 < nloc) {
+    uint32_t i = merge_path(sa, na, sb, nb, d0);
+    uint32_t j = d0 - i;
 #pragma unroll
     for (int q = 0; q < kMergeItems; ++q) {
-      if (k0 + q >= M) break;
+      if (d0 + q >= nloc) break;
       used |= 1u << q;
-      const bool take_s = i < Vs && (j >= Vd || usrc[i] <= udst[j]);
-      ci[q] = i;
-      cj[q] = j;
-      if (take_s) {
-        x[q] = usrc[i];
+      lij[q] = i | (j << 16);
+      if (i < na && (j >= nb || sa[i] <= sb[j])) {
         emit |= 1u << q;
         from_src |= 1u << q;
         ++i;
       } else {
-        x[q] = udst[j];
-        if (i == 0 || usrc[i - 1] != x[q]) emit |= 1u << q;
+        // a dst item equal to the src item before it is the same node
+        const bool has = i > 0 || S.has_prev;
+        const int32_t before = i > 0 ? sa[i - 1] : S.prev;
+        if (!(has && before == sb[j])) emit |= 1u << q;
         ++j;
       }
     }
-    cnt = __popc(emit);
   }
   uint32_t total;
-  const uint32_t local = block_exclusive_sum<kScanThreads>(cnt, s_sw, total);
+  const uint32_t local = block_exclusive_sum<kScanThreads>((uint32_t)__popc(emit), S.sw, total);
   if (warp == 0) {
     const uint64_t excl = scan_prefix(ctl->scan_status[2], chunks_of(ctl, 2), tile, ntiles,
                                       pack2(0, total), &ctl->err);
     if (lane == 0) {
-      *s_prefix = excl;
+      S.prefix = excl;
       if (tile == ntiles - 1) {
         const uint32_t V = unpackB(excl) + total;
         ctl->V = V;
@@ -350,40 +414,51 @@ __device__ __forceinline__ void merge_tile(Ctl* __restrict__ ctl, uint32_t tile,
       }
     }
   }
-  __syncthreads();
-  uint32_t r = unpackB(*s_prefix) + local;  // nodes emitted before this item
-  const int32_t* __restrict__ us = ctl->usrc_start;
-  const int32_t* __restrict__ ud = ctl->udst_start;
+  // stage: tile-local node index of every input item, and the emitted nodes
+  int32_t r = (int32_t)local;
 #pragma unroll
   for (int q = 0; q < kMergeItems; ++q) {
     if (!((used >> q) & 1u)) continue;
     const bool e = (emit >> q) & 1u;
+    const uint32_t li = lij[q] & 0xFFFFu, lj = lij[q] >> 16;
     if ((from_src >> q) & 1u) {
-      ctl->src_rank[ci[q]] = (int32_t)r;
+      S.rank[li] = r;
     } else {
-      // a dropped dst item is the node emitted just before it
-      ctl->dst_rank[cj[q]] = (int32_t)(e ? r : r - 1);
+      S.rank[na + lj] = e ? r : r - 1;  // a dropped dst item: the node just before
     }
     if (e) {
-      ctl->node_ids[r] = x[q];
-      ctl->out_off[r] = us[ci[q]];
-      ctl->in_off[r] = ud[cj[q]];
+      S.node[r] = li | (lj << 12) | (((from_src >> q) & 1u) << 24);
       ++r;
     }
   }
+  __syncthreads();
+  const uint32_t r0 = unpackB(S.prefix);
+  int32_t* __restrict__ node_ids = ctl->node_ids;
+  int64_t* __restrict__ out_off = ctl->out_off;
+  int64_t* __restrict__ in_off = ctl->in_off;
+  for (uint32_t t = tid; t < total; t += kScanThreads) {
+    const uint32_t p = S.node[t];
+    const uint32_t i = p & 0xFFFu, j = (p >> 12) & 0xFFFu;
+    node_ids[r0 + t] = (p >> 24) ? sa[i] : sb[j];
+    out_off[r0 + t] = S.start[i];
+    in_off[r0 + t] = S.start[na + 1 + j];
+  }
+  int32_t* __restrict__ src_rank = ctl->src_rank;
+  int32_t* __restrict__ dst_rank = ctl->dst_rank;
+  for (uint32_t t = tid; t < na; t += kScanThreads) src_rank[i0 + t] = (int32_t)r0 + S.rank[t];
+  for (uint32_t t = tid; t < nb; t += kScanThreads) dst_rank[j0 + t] = (int32_t)r0 + S.rank[na + t];
 }
 
 // Persistent: blocks claim merge slots in order until none is left.
-__global__ void __launch_bounds__(kScanThreads)
+__global__ void __launch_bounds__(kScanThreads, 6)
     k_merge(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
-  __shared__ uint32_t s_sw[kWarps + 1];
-  __shared__ uint64_t s_prefix;
+  __shared__ MergeSmem S;
   __shared__ Claim s_cl;
   while (true) {
     if (threadIdx.x == 0) claim_slot(m, counter, &s_cl);
     __syncthreads();
     if (!s_cl.valid) return;
-    merge_tile(ctls + s_cl.seg, s_cl.tile, s_sw, &s_prefix);
+    merge_tile(ctls + s_cl.seg, s_cl.tile, S);
     __syncthreads();
   }
 }
@@ -441,8 +516,12 @@ static uint32_t persistent_grid(uint32_t per_sm) {
   return (uint32_t)sms * per_sm;
 }
 
+void launch_merge_split(const Launch& L, cudaStream_t s) {
+  k_merge_split<<<persistent_grid(8), 256, 0, s>>>(L.ctls, L.merge);
+}
+
 void launch_merge(const Launch& L, uint32_t* counter, cudaStream_t s) {
-  k_merge<<<persistent_grid(8), kScanThreads, 0, s>>>(L.ctls, L.merge, counter);
+  k_merge<<<persistent_grid(6), kScanThreads, 0, s>>>(L.ctls, L.merge, counter);
 }
 
 // ---------------------------------------------------------- block tables --
@@ -497,24 +576,47 @@ __device__ __forceinline__ int32_t map_index(const uint32_t* __restrict__ blk,
   return __ldg(map + j);
 }
 
-// One direction of the remap over entries [base, end), in place.
+// One direction of the remap over the entries [base, end) of one tile, in
+// place.  A full tile is 16 entries per thread, taken as four coalesced
+// 128-bit loads; all block-table words are requested before any map word,
+// so each thread keeps 16 independent lookups in flight.
 __device__ __forceinline__ void remap_range(int32_t* __restrict__ a, uint32_t base, uint32_t end,
                                             const uint32_t* __restrict__ blk,
                                             const int32_t* __restrict__ map, uint32_t len,
                                             uint32_t* err) {
-  for (uint32_t e = base + threadIdx.x * 4; e < end; e += blockDim.x * 4) {
-    if (e + 4 <= end && (e & 3) == 0) {
-      int4 x = __ldcs(reinterpret_cast<const int4*>(a + e));
-      x.x = map_index(blk, map, len, (uint32_t)x.x, err);
-      x.y = map_index(blk, map, len, (uint32_t)x.y, err);
-      x.z = map_index(blk, map, len, (uint32_t)x.z, err);
-      x.w = map_index(blk, map, len, (uint32_t)x.w, err);
-      __stcs(reinterpret_cast<int4*>(a + e), x);
-    } else {
-      for (uint32_t q = e; q < min(e + 4, end); ++q)
-        a[q] = map_index(blk, map, len, (uint32_t)a[q], err);
+  constexpr int kVec = kScanTile / (4 * 256);  // 128-bit words per thread
+  if (end - base == (uint32_t)kScanTile && blockDim.x == 256) {
+    uint32_t v[4 * kVec];
+#pragma unroll
+    for (int k = 0; k < kVec; ++k) {
+      const int4 x = __ldcs(reinterpret_cast<const int4*>(a + base + k * 1024) + threadIdx.x);
+      v[4 * k] = (uint32_t)x.x;
+      v[4 * k + 1] = (uint32_t)x.y;
+      v[4 * k + 2] = (uint32_t)x.z;
+      v[4 * k + 3] = (uint32_t)x.w;
     }
+    uint32_t w[4 * kVec];
+#pragma unroll
+    for (int q = 0; q < 4 * kVec; ++q) w[q] = v[q] < len ? __ldg(blk + (v[q] >> kBlkShift)) : 0u;
+#pragma unroll
+    for (int q = 0; q < 4 * kVec; ++q) {
+      if (v[q] >= len) {  // never for a correct run index: recorded, not read
+        atomicOr(err, kErrRemap);
+        v[q] = 0;
+      } else if (w[q] & kBlkDense) {
+        v[q] = (w[q] & ~kBlkDense) + (v[q] & 31);
+      } else {
+        v[q] = (uint32_t)__ldg(map + v[q]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kVec; ++k)
+      __stcs(reinterpret_cast<int4*>(a + base + k * 1024) + threadIdx.x,
+             make_int4((int)v[4 * k], (int)v[4 * k + 1], (int)v[4 * k + 2], (int)v[4 * k + 3]));
+    return;
   }
+  for (uint32_t e = base + threadIdx.x; e < end; e += blockDim.x)
+    a[e] = map_index(blk, map, len, (uint32_t)a[e], err);
 }
 
 // When every node is a source (Vs == V) the source-run index already is the

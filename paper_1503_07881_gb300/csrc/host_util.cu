@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <chrono>
 #include <map>
 #include <mutex>
 #include <string>
@@ -125,7 +126,8 @@ void pinned_put(void* p) {
 // ------------------------------------------------------------ profiling ---
 struct ProfRecord {
   std::string name;
-  cudaEvent_t a, b;
+  cudaEvent_t a, b;   // device interval (null for host records)
+  double host_ms;     // host interval
 };
 static std::mutex g_prof_mu;
 static bool g_prof_on = false;
@@ -162,7 +164,19 @@ ProfScope::~ProfScope() {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   cudaEvent_t end = get_event();
   cudaEventRecord(end, s_);
-  g_prof.push_back(ProfRecord{name_, start_, end});
+  g_prof.push_back(ProfRecord{name_, start_, end, 0.0});
+}
+
+HostScope::HostScope(const char* name) : name_(name) {
+  if (g_prof_on) t0_ = std::chrono::steady_clock::now(), on_ = true;
+}
+
+HostScope::~HostScope() {
+  if (!on_) return;
+  const double ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0_).count();
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.push_back(ProfRecord{name_, nullptr, nullptr, ms});
 }
 
 }  // namespace ringo
@@ -170,6 +184,7 @@ ProfScope::~ProfScope() {
 extern "C" int ringo_profile_start(void) {
   std::lock_guard<std::mutex> lk(ringo::g_prof_mu);
   for (auto& r : ringo::g_prof) {
+    if (!r.a) continue;
     ringo::g_event_cache.push_back(r.a);
     ringo::g_event_cache.push_back(r.b);
   }
@@ -184,9 +199,9 @@ extern "C" int ringo_profile_stop(ringo_kernel_stat* out, int32_t cap, int32_t* 
   std::vector<std::string> order;
   std::map<std::string, std::pair<int64_t, double>> agg;
   for (auto& r : ringo::g_prof) {
-    float ms = 0.f;
-    if (cudaEventSynchronize(r.b) != cudaSuccess ||
-        cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+    float ms = (float)r.host_ms;
+    if (r.a && (cudaEventSynchronize(r.b) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)) {
       ringo::set_error("profiling event failed");
       return RINGO_ECUDA;
     }
@@ -207,6 +222,7 @@ extern "C" int ringo_profile_stop(ringo_kernel_stat* out, int32_t cap, int32_t* 
   }
   if (n_out) *n_out = n;
   for (auto& r : ringo::g_prof) {
+    if (!r.a) continue;
     ringo::g_event_cache.push_back(r.a);
     ringo::g_event_cache.push_back(r.b);
   }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <chrono>
 #include <string>
 
 namespace ringo {
@@ -32,6 +33,14 @@ struct ProfScope {
   const char* name_;
   cudaStream_t s_;
   cudaEvent_t start_ = nullptr;
+};
+// Host wall time of a scope, reported beside the kernels (name "host:...").
+struct HostScope {
+  explicit HostScope(const char* name);
+  ~HostScope();
+  const char* name_;
+  std::chrono::steady_clock::time_point t0_;
+  bool on_ = false;
 };
 
 }  // namespace ringo

@@ -59,10 +59,11 @@ int enqueue_sort_only(const Launch& L, cudaStream_t s) {
   return RINGO_OK;
 }
 
-// merge into the node list, block tables of the two rank maps, remap.
+// merge splits, merge into the node list, block tables of the two rank maps, remap.
 int enqueue_phase2(const Launch& L, cudaStream_t s) {
   uint32_t* c = L.counters + 20;
   RINGO_ENQUEUE("phase2_maps", launch_phase2_maps(L, s));
+  RINGO_ENQUEUE("merge_split", launch_merge_split(L, s));
   RINGO_ENQUEUE("merge", launch_merge(L, c + 0, s));
   RINGO_ENQUEUE("rank_blocks", launch_rank_blocks(L, c + 1, s));
   RINGO_ENQUEUE("remap", launch_remap(L, c + 2, s));

@@ -141,6 +141,13 @@ struct alignas(16) Ctl {
   uint32_t solo_counters[32];
 };
 
+// Merge-path splits of the merge tiles (phase 2).  They live in the radix key
+// buffer, which no phase-2 kernel reads: at most (2n + 2047) / 2048 + 1
+// words, far below its 8 (n + 1) bytes.
+__host__ __device__ inline uint32_t* merge_splits(const Ctl* c) {
+  return reinterpret_cast<uint32_t*>(c->keysA);
+}
+
 constexpr uint32_t kBlkDense = 0x80000000u;
 
 constexpr int kBlkShift = 5;  // 32 map entries per block-table word
@@ -148,9 +155,10 @@ constexpr int kBlkShift = 5;  // 32 map entries per block-table word
 // ------------------------------------------------------- multi-segment map --
 // Every pipeline kernel runs over a table of segments at once (one segment
 // for a single table, thousands for a batch): segment s owns the global tile
-// slots [start[s], start[s+1]), a multiple of kChunkTiles, and blocks claim
-// slots in increasing order from a per-launch counter, so a tile only ever
-// waits on earlier tiles of its own segment, all claimed before it.
+// slots [start[s], start[s+1]) (look-back chunks count from the segment's own
+// first tile), and blocks claim slots in increasing order from a per-launch
+// counter, so a tile only ever waits on earlier tiles of its own segment, all
+// claimed before it.
 struct SegMap {
   const uint32_t* start;  // [nseg + 1], device
   uint32_t nseg;
@@ -198,6 +206,7 @@ void launch_dst_rank(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_dedup(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_dst_runs(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_phase2_maps(const Launch& L, cudaStream_t s);
+void launch_merge_split(const Launch& L, cudaStream_t s);
 void launch_merge(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_rank_blocks(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_remap(const Launch& L, uint32_t* counter, cudaStream_t s);

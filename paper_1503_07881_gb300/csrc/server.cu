@@ -84,6 +84,7 @@ struct Req {
   int32_t topk = 0;
   int32_t flags = 0;
   int64_t rows = -1;  // selected rows, once counted
+  std::vector<uint32_t> lo, cnt;  // its (tag, window) ranges of clustered rows
   bool counting = false;
   bool done = false;
   int64_t est = 0;  // bytes charged while in flight
@@ -124,7 +125,8 @@ void finish(ringo_server* S, Req* r, int status) {
   else S->stats.failed++;
 }
 
-// Counts the selected rows of `batch` (all uncounted, marked counting).
+// Counts the selected rows of `batch` (all uncounted, marked counting) and
+// keeps each request's ranges for its wave.
 int count_rows(ringo_server* S, const std::vector<Req*>& batch, cudaStream_t st,
                std::vector<int64_t>* rows) {
   std::vector<ringo_select> preds(batch.size());
@@ -133,33 +135,36 @@ int count_rows(ringo_server* S, const std::vector<Req*>& batch, cudaStream_t st,
                             batch[i]->t1};
   const std::vector<Pair> pairs = make_pairs(preds.data(), (int32_t)preds.size());
   Ranges rg;
-  const int rc = select_ranges(S->base, pairs, st, &rg);
+  HostScope hs("host:serve_count");
+  const int rc = select_ranges(S->base, pairs, st, &rg, true);
   pool_free(rg.block, st);
   rows->assign(batch.size(), 0);
   if (rc != RINGO_OK) return rc;
-  for (size_t i = 0; i < pairs.size(); ++i) (*rows)[pairs[i].seg] += rg.h_cnt[i];
+  for (size_t i = 0; i < pairs.size(); ++i) {
+    Req* r = batch[pairs[i].seg];
+    (*rows)[pairs[i].seg] += rg.h_cnt[i];
+    r->lo.push_back(rg.h_lo[i]);
+    r->cnt.push_back(rg.h_cnt[i]);
+  }
   return RINGO_OK;
 }
 
-// Runs one admitted batch as one wave; fills each request's result.
+// Runs one admitted batch as one wave, with the ranges its requests got
+// when they were counted; fills each request's result.
 int run_batch(ringo_server* S, const std::vector<Req*>& batch, cudaStream_t st) {
-  std::vector<ringo_select> preds(batch.size());
   uint32_t topk = 0;
-  for (size_t i = 0; i < batch.size(); ++i) {
-    preds[i] = ringo_select{batch[i]->tags.data(), (int32_t)batch[i]->tags.size(), batch[i]->t0,
-                            batch[i]->t1};
-    topk = std::max(topk, (uint32_t)batch[i]->topk);
-  }
-  const std::vector<Pair> pairs = make_pairs(preds.data(), (int32_t)preds.size());
-  Ranges rg;
-  int rc = select_ranges(S->base, pairs, st, &rg);
   const uint32_t nseg = (uint32_t)batch.size();
   std::vector<size_t> first(nseg + 1, 0);
-  for (size_t i = 0; i < pairs.size(); ++i) first[pairs[i].seg + 1] = i + 1;
-  for (uint32_t i = 0; i < nseg; ++i) first[i + 1] = std::max(first[i + 1], first[i]);
+  std::vector<uint32_t> h_lo, h_cnt;
+  for (uint32_t i = 0; i < nseg; ++i) {
+    topk = std::max(topk, (uint32_t)batch[i]->topk);
+    h_lo.insert(h_lo.end(), batch[i]->lo.begin(), batch[i]->lo.end());
+    h_cnt.insert(h_cnt.end(), batch[i]->cnt.begin(), batch[i]->cnt.end());
+    first[i + 1] = h_lo.size();
+  }
   WaveResult w;
-  if (rc == RINGO_OK)
-    rc = run_wave(S->base, rg.lo, rg.cnt, rg.h_cnt.data(), first, nseg, topk, st, &w);
+  int rc = run_wave(S->base, nullptr, nullptr, h_lo.data(), h_cnt.data(), first, nseg, topk, st,
+                    &w);
   int64_t batch_rows = 0;
   for (Req* r : batch) batch_rows += r->rows;
   for (uint32_t j = 0; j < nseg && rc == RINGO_OK; ++j) {
@@ -207,7 +212,6 @@ int run_batch(ringo_server* S, const std::vector<Req*>& batch, cudaStream_t st) 
   }
   if (cudaStreamSynchronize(st) != cudaSuccess && rc == RINGO_OK) rc = RINGO_ECUDA;
   pool_free(w.block, st);
-  pool_free(rg.block, st);
   return rc;
 }
 

@@ -399,10 +399,15 @@ __global__ void __launch_bounds__(kSortThreads, 4)
   uint32_t* cinc = ctl->chunk_inc[reg];
   uint32_t* ccnt = ctl->chunk_cnt[reg];
   if (bin_total) atomicAdd(cagg + (size_t)chunk * kRadix + tid, bin_total);
-  __threadfence();  // the counts above are visible before the chunk counter moves
   uint32_t tile_total;
   const uint32_t bin_start = block_exclusive_sum<kSortThreads>(bin_total, S.sw, tile_total);
-  if (tid == 0) atomicAdd(ccnt + chunk, 1u);
+  if (tid == 0) {
+    // the block barrier inside the sum orders every thread's chunk-aggregate
+    // add before this fence (fences are cumulative), so one release fence
+    // makes all of them visible before the chunk counter moves
+    __threadfence();
+    atomicAdd(ccnt + chunk, 1u);
+  }
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w) S.whist[w][tid] += bin_start;
   __syncthreads();
