@@ -180,7 +180,7 @@ def sort_source_digest() -> str:
 def ncu_traffic_per_key_pass() -> float | None:
     """DRAM bytes per key per radix pass from the committed ncu summary, if it
     was taken on the current onesweep source."""
-    path = os.path.join(ROOT, "profiles", "onesweep_pass_ncu.md")
+    path = os.path.join(ROOT, "profiles", "onesweep_pass_lj_ncu.md")
     try:
         text = open(path).read()
     except OSError:
@@ -373,10 +373,22 @@ BATCH_PREDS, BATCH_LO, BATCH_HI = 4096, 1_000, 4_000_000
 SERVE_LO, SERVE_HI, SERVE_TOPK, SERVE_BUDGET = 10_000, 50_000_000, 100, 120 << 30
 
 
-def load_base(seed: int):
-    """The 200M-row base table, generated on the device and loaded (clustered)."""
+def base_spec(scale: float = 1.0):
+    """The base table of configs 4-5 (200M rows, 16M IDs, 10K tags), or a
+    proportionally smaller one (profiling captures use scale 0.1)."""
+    from paper_1503_07881_gb300 import tablegen
+    full = tablegen.BaseSpec()
+    if scale == 1.0:
+        return full
+    return tablegen.BaseSpec(rows=max(1, int(full.rows * scale)),
+                             nodes=max(2, int(full.nodes * scale)),
+                             tags=max(10, int(full.tags * scale)))
+
+
+def load_base(seed: int, scale: float = 1.0):
+    """The base table, generated on the device and loaded (clustered)."""
     from paper_1503_07881_gb300 import ringo, tablegen
-    spec = tablegen.BaseSpec()
+    spec = base_spec(scale)
     cols = tablegen.make_base_table(spec, seed=seed, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -400,7 +412,8 @@ def plain_convert(ringo, base, pred, count: int, topk: int = 0):
 
 def run_batched(args, spec, base, steps: int, warmup: int) -> dict:
     from paper_1503_07881_gb300 import ringo, tablegen
-    preds = tablegen.make_predicates(spec, BATCH_PREDS, BATCH_LO, BATCH_HI, seed=args.seed)
+    hi = max(BATCH_LO + 1, int(BATCH_HI * args.base_scale))
+    preds = tablegen.make_predicates(spec, args.predicates, BATCH_LO, hi, seed=args.seed)
     counts = base.select_count(preds)
     R = int(counts.sum())
     peak, peak_kind = measured_peak_hbm()
@@ -545,7 +558,7 @@ def run_base_workloads(args) -> tuple[dict | None, dict | None]:
     only = args.workload in ("batched", "served")
     do_batched = args.workload == "batched" or (not only and not args.no_batched)
     do_served = args.workload == "served" or (not only and not args.no_served)
-    spec, base, load_ms = load_base(args.seed)
+    spec, base, load_ms = load_base(args.seed, args.base_scale)
     try:
         if do_batched:
             try:
@@ -674,6 +687,9 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the plain per-table loop of the batched run (profiling)")
+    ap.add_argument("--base-scale", type=float, default=1.0,
+                    help="scale of the base table and of the largest selection (profiling)")
+    ap.add_argument("--predicates", type=int, default=BATCH_PREDS)
     ap.add_argument("--serve-rates", type=lambda x: [float(v) for v in x.split(",")],
                     default=[100.0, 500.0])
     ap.add_argument("--serve-seconds", type=float, default=4.0)
