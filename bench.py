@@ -253,6 +253,11 @@ def run_ours(args, world, rank, local):
     model_bytes = 8 * N + 20 * V + 16 + 8 * E + 104 * N + 64 * E
     model_frac = model_bytes / (ms / 1e3) / 1e9 / peak
 
+    # graph -> table (Section 3.4) and PageRank (Table "paralg") on the same graph
+    to_table = pagerank = None
+    if not args.no_to_table:
+        to_table, pagerank = run_graph_ops(args, src, dst, stream, peak, peak_kind)
+
     # e2e: host columns -> graph -> host arrays, through the C ABI
     e2e = None
     if not args.no_e2e:
@@ -337,6 +342,8 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
         "batched": batched,
         "served": served,
+        "graph_to_table": to_table,
+        "pagerank": pagerank,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -366,6 +373,108 @@ def run_base_only(args):
         if served and "error" not in served:
             line["value"] = served["rates"][-1]["server"]["edges_per_s"]
     print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------- graph -> table --
+PAPER_TO_TABLE_RATE = {"twitter": 50.4e6, "lj": 46.0e6}  # Table 5, edges/s
+
+
+PAPER_PAGERANK_S = {"twitter": 60.5, "lj": 2.76}  # Table "paralg", ten iterations
+
+
+def run_graph_ops(args, src, dst, stream, peak, peak_kind) -> tuple[dict, dict]:
+    """Graph -> table and PageRank on the graph of the workload."""
+    from paper_1503_07881_gb300 import ringo
+    g = ringo.ringo_table_to_graph(src, dst)
+    try:
+        return run_to_table(args, g, stream, peak, peak_kind), run_pagerank(args, g, stream, peak,
+                                                                            peak_kind)
+    finally:
+        g.free()
+        torch.cuda.empty_cache()
+
+
+def run_pagerank(args, g, stream, peak, peak_kind) -> dict:
+    """Ten PageRank iterations (d = 0.85), timed with CUDA events over 3 runs
+    after one warm-up."""
+    from paper_1503_07881_gb300 import ringo
+    V, E = g.num_nodes, g.num_edges
+    out = torch.empty(max(V, 1), dtype=torch.float64, device="cuda")
+    iters, runs = 10, 3
+    g.pagerank(0.85, iters, out=out)
+    torch.cuda.synchronize()
+    ringo.ringo_profile_start()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(runs):
+        g.pagerank(0.85, iters, out=out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    prof = {p["name"]: p for p in ringo.ringo_profile_stop()}
+    ms = a.elapsed_time(b) / runs
+    total = float(out[:V].sum().item())
+    # edge pass per iteration: in-neighbour index (4 B) and its contribution
+    # (8 B) per edge, the in-offsets, one add per node
+    edge_ms = prof["pagerank_edges"]["total_ms"] / (runs * iters) if "pagerank_edges" in prof else None
+    algo = 12 * E + 8 * (V + 1) + 8 * V
+    paper = PAPER_PAGERANK_S.get(args.workload)
+    res = {"metric": "PageRank, 10 iterations", "ms": round(ms, 3), "unit": "ms",
+           "iterations": iters, "damping": 0.85, "edges": E, "nodes": V,
+           "edges_per_s": E * iters / (ms / 1e3), "rank_sum": total,
+           "paper_s": paper, "vs_paper": (paper * 1e3 / ms) if paper else None,
+           "dtype": "f64"}
+    if edge_ms:
+        res["roofline"] = {"bound": "hbm", "kernel": "k_pr_edges",
+                           "achieved": algo / (edge_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                           "frac": algo / (edge_ms / 1e3) / 1e9 / peak,
+                           "algorithmic_bytes": "12 B per edge + 16 B per node",
+                           "peak_source": peak_kind}
+    del out
+    return res
+
+
+def run_to_table(args, g, stream, peak, peak_kind) -> dict:
+    """Edge table (out-CSR order) and node table of the graph of the workload,
+    timed with CUDA events over 5 launches after 2 warm-ups."""
+    from paper_1503_07881_gb300 import ringo
+    V, E = g.num_nodes, g.num_edges
+    cols = (torch.empty(max(E, 1), dtype=torch.int32, device="cuda"),
+            torch.empty(max(E, 1), dtype=torch.int32, device="cuda"))
+    k = 5
+    for _ in range(2):
+        g.to_edge_table(ringo.RINGO_OUT, out=cols)
+        g.to_node_table()
+    torch.cuda.synchronize()
+    ringo.ringo_profile_start()
+    a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    a.record(stream)
+    for _ in range(k):
+        g.to_edge_table(ringo.RINGO_OUT, out=cols)
+    b.record(stream)
+    for _ in range(k):
+        g.to_node_table()
+    c.record(stream)
+    torch.cuda.synchronize()
+    prof = {p["name"]: p for p in ringo.ringo_profile_stop()}
+    edge_ms = a.elapsed_time(b) / k
+    node_ms = b.elapsed_time(c) / k
+    kern_ms = prof["edge_table"]["total_ms"] / k if "edge_table" in prof else edge_ms
+    # per launch: neighbours read, one node-ID read per row end, two columns
+    # written, the offsets and node IDs read once
+    algo = 4 * E + 4 * E + 8 * E + 8 * (V + 1) + 4 * V
+    del cols
+    torch.cuda.empty_cache()
+    rate = E / (edge_ms / 1e3)
+    paper = PAPER_TO_TABLE_RATE.get(args.workload)
+    return {"metric": "graph->table edges/s", "value": rate, "unit": "edges/s",
+            "edge_table_ms": round(edge_ms, 3), "node_table_ms": round(node_ms, 3),
+            "edges": E, "nodes": V, "paper_rate": paper,
+            "vs_paper": rate / paper if paper else None,
+            "roofline": {"bound": "hbm", "kernel": "k_expand", "achieved": algo / (kern_ms / 1e3) / 1e9,
+                         "peak": peak, "unit": "GB/s",
+                         "frac": algo / (kern_ms / 1e3) / 1e9 / peak,
+                         "algorithmic_bytes": "16 B per edge + 12 B per node",
+                         "peak_source": peak_kind}}
 
 
 # ------------------------------------------------------ batched / served --
@@ -683,6 +792,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched summary")
+    ap.add_argument("--no-to-table", action="store_true", help="skip the graph->table summary")
     ap.add_argument("--no-served", action="store_true", help="skip the served summary")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true",

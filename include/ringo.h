@@ -178,6 +178,46 @@ RINGO_API int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* ds
                                            int64_t node_capacity, int64_t edge_capacity,
                                            int64_t* num_nodes, int64_t* num_edges);
 
+/*
+ * ringo_graph_to_edge_table -- Section 3.4 "Conversion of graphs to tables":
+ * the graph's edge table, one row per edge, written to caller-owned device
+ * columns d_src[cap], d_dst[cap] (node IDs).  dir RINGO_OUT gives the rows in
+ * out-CSR order (sources ascending, each source's destinations ascending),
+ * RINGO_IN in in-CSR order (destinations ascending, then sources); either
+ * converts back to the same graph.  *n receives E.  Enqueued on `stream`
+ * (NULL: the graph's stream); the columns are complete when the stream
+ * reaches this point.  Errors: EINVAL (NULL g or n, bad dir, cap < 0, NULL
+ * column with E > 0), ERANGE (cap < E; nothing written), ECUDA.
+ */
+RINGO_API int ringo_graph_to_edge_table(const ringo_graph* g, int dir, int32_t* d_src,
+                                        int32_t* d_dst, int64_t cap, int64_t* n, void* stream);
+/*
+ * ringo_graph_to_node_table -- the node table: one row per node in ascending
+ * ID order, with its out- and in-degree, into caller-owned device columns
+ * d_ids[cap], d_outdeg[cap], d_indeg[cap].  *n receives V.  Stream and errors
+ * as ringo_graph_to_edge_table (ERANGE if cap < V).
+ */
+RINGO_API int ringo_graph_to_node_table(const ringo_graph* g, int32_t* d_ids, int64_t* d_outdeg,
+                                        int64_t* d_indeg, int64_t cap, int64_t* n, void* stream);
+
+/*
+ * ringo_graph_pagerank -- PageRank of the graph, the paper's second workload
+ * (Section 4, Table "paralg": ten iterations).  Power iteration from the
+ * uniform vector, in fp64:
+ *   PR'(v) = (1 - d) / V + d * (sum over in-neighbours u of PR(u) / outdeg(u)
+ *                               + sum of PR over nodes without out-edges / V),
+ * `iterations` steps (0 gives the uniform vector), d = damping in [0, 1].
+ * Writes PR in node-index order to caller-owned device d_rank[V].  Enqueued
+ * on `stream` (NULL: the graph's stream); scratch of 16 V bytes comes from
+ * the library's pool.  Sums are formed in a different order than a
+ * sequential loop, so results agree with one to within fp64 rounding (about
+ * max in-degree x 1e-16 relative per step), not bit for bit.
+ * Errors: EINVAL (NULL g, NULL d_rank with V > 0, iterations < 0, damping
+ * outside [0, 1]), ENOMEM, ECUDA.
+ */
+RINGO_API int ringo_graph_pagerank(const ringo_graph* g, double damping, int32_t iterations,
+                                   double* d_rank, void* stream);
+
 /* ------------------------------------------------------------------------
  * Base tables, selection and batched conversion.
  *
@@ -281,6 +321,11 @@ RINGO_API int ringo_batch_copy_graph_to_host(const ringo_batch* bt, int32_t i,
 /* Top-k degrees of graph i (same contract as ringo_graph_degree_topk). */
 RINGO_API int ringo_batch_degree_topk(const ringo_batch* bt, int32_t i, int dir, int32_t k,
                                       int32_t* h_ids, int64_t* h_degs, int32_t* n_out);
+/* Edge table of graph i (same contract as ringo_graph_to_edge_table; NULL
+ * stream: the batch's stream). */
+RINGO_API int ringo_batch_graph_to_edge_table(const ringo_batch* bt, int32_t i, int dir,
+                                              int32_t* d_src, int32_t* d_dst, int64_t cap,
+                                              int64_t* n, void* stream);
 /* Releases every graph of the batch; NULL is a no-op. */
 RINGO_API void ringo_batch_free(ringo_batch* bt);
 

@@ -74,6 +74,10 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
                 ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)),
                 ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)), ctypes.c_void_p]
             lib.oracle_free_lists.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+            lib.oracle_graph_to_edge_table.restype = ctypes.c_int
+            lib.oracle_graph_to_edge_table.argtypes = [
+                ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                ctypes.c_void_p, ctypes.c_void_p]
             lib.oracle_count_distinct.restype = ctypes.c_int
             lib.oracle_count_distinct.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                   ctypes.c_void_p, ctypes.c_void_p]
@@ -162,3 +166,60 @@ def count_distinct(src, dst) -> tuple[int, int]:
     _lib().oracle_count_distinct(s.ctypes.data, d.ctypes.data, s.size, e.ctypes.data,
                                  v.ctypes.data)
     return int(e[0]), int(v[0])
+
+
+def graph_to_edge_table(g: dict, direction: str = "out", mutant: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Edge table of a graph (paper Section 3.4, "Conversion of graphs to
+    tables"): (src, dst) ID columns, one row per edge, in the CSR order of
+    the chosen direction ("out": by source then destination, "in": by
+    destination then source)."""
+    V, E = int(g["num_nodes"]), int(g["num_edges"])
+    ids = _i32(g["node_ids"])
+    off = np.ascontiguousarray(g[f"{direction}_off"], np.int64)
+    nbr = _i32(g[f"{direction}_nbr"])
+    src = np.zeros(E, np.int32)
+    dst = np.zeros(E, np.int32)
+    if E:
+        rc = _lib(mutant).oracle_graph_to_edge_table(V, ids.ctypes.data, off.ctypes.data,
+                                                     nbr.ctypes.data, 1 if direction == "in" else 0,
+                                                     src.ctypes.data, dst.ctypes.data)
+        if rc != 0:
+            raise RuntimeError("oracle_graph_to_edge_table failed")
+    return src, dst
+
+
+def graph_to_node_table(g: dict) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Node table of a graph: node IDs ascending, out-degree, in-degree (the
+    lengths of the per-node neighbour vectors)."""
+    return (np.asarray(g["node_ids"], np.int32).copy(), np.diff(np.asarray(g["out_off"], np.int64)),
+            np.diff(np.asarray(g["in_off"], np.int64)))
+
+
+def pagerank(g: dict, damping: float = 0.85, iterations: int = 10, drop_dangling: bool = False) -> np.ndarray:
+    """PageRank of a built graph (the paper's second workload, Section 4,
+    Table "paralg": ten iterations), in fp64, node index order.
+
+    Readings (the paper names the algorithm but not its variant): the
+    standard power iteration from the uniform vector,
+        PR'(v) = (1 - d) / V + d * ( sum over in-neighbours u of PR(u) / outdeg(u)
+                                     + (sum of PR over nodes with no out-edges) / V ),
+    with d = damping, a fixed number of iterations and no convergence test.
+    ``drop_dangling`` plants a mistake for the pin tests (the mass of nodes
+    without out-edges is lost).
+    """
+    V = int(g["num_nodes"])
+    if V == 0:
+        return np.zeros(0, np.float64)
+    out_off = np.asarray(g["out_off"], np.int64)
+    in_off = np.asarray(g["in_off"], np.int64)
+    in_nbr = np.asarray(g["in_nbr"], np.int64)
+    outdeg = np.diff(out_off)
+    indeg = np.diff(in_off)
+    row_of_edge = np.repeat(np.arange(V), indeg)  # the node each in-edge enters
+    pr = np.full(V, 1.0 / V)
+    for _ in range(iterations):
+        contrib = np.where(outdeg > 0, pr / np.maximum(outdeg, 1), 0.0)
+        dangling = 0.0 if drop_dangling else float(pr[outdeg == 0].sum())
+        incoming = np.bincount(row_of_edge, weights=contrib[in_nbr], minlength=V)
+        pr = (1.0 - damping) / V + damping * (incoming + dangling / V)
+    return pr

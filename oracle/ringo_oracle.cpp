@@ -1,4 +1,4 @@
-// Ringo table->graph ORACLE.  TEST INFRASTRUCTURE ONLY.
+// Ringo table->graph (and graph->table) ORACLE.  TEST INFRASTRUCTURE ONLY.
 //
 // This file is the plain, slow, obviously-correct CPU statement of what the
 // table->graph conversion computes.  Only the tests, the smoke check and the
@@ -230,6 +230,28 @@ int oracle_count_distinct(const int32_t* src, const int32_t* dst, int64_t n,
   }
   *num_edges = (int64_t)rows.size();
   *num_nodes = (int64_t)nodes.size();
+  return 0;
+}
+
+// Graph -> edge table (paper, Section 3.4 "Conversion of graphs to tables"):
+// every node contributes one row per neighbour in one direction's CSR,
+// visited node by node, neighbour by neighbour.  Out-CSR rows are
+// (node, neighbour); in-CSR rows (swap != 0) are (neighbour, node), so both
+// give (src ID, dst ID) columns.
+int oracle_graph_to_edge_table(int64_t num_nodes, const int32_t* node_ids, const int64_t* off,
+                               const int32_t* nbr, int swap, int32_t* src_out, int32_t* dst_out) {
+  int64_t row = 0;
+  for (int64_t r = 0; r < num_nodes; ++r) {
+    const int64_t end = MUTANT(8) ? off[r + 1] - 1 : off[r + 1];  // drops each last neighbour
+    for (int64_t k = off[r]; k < end; ++k) {
+      const int32_t node = node_ids[r];
+      const int32_t other = node_ids[nbr[k]];
+      const bool sw = swap && !MUTANT(7);  // forgets to swap the in-CSR rows back
+      src_out[row] = sw ? other : node;
+      dst_out[row] = sw ? node : other;
+      ++row;
+    }
+  }
   return 0;
 }
 

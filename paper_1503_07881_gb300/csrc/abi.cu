@@ -468,6 +468,49 @@ int ringo_graph_copy_to_host(const ringo_graph* g, int32_t* h_node_ids, int64_t*
   return RINGO_OK;
 }
 
+int ringo_graph_to_edge_table(const ringo_graph* g, int dir, int32_t* d_src, int32_t* d_dst,
+                              int64_t cap, int64_t* n, void* stream) {
+  if (!g || !n || check_dir(dir) || cap < 0) return RINGO_EINVAL;
+  const int64_t E = g->info.num_edges;
+  *n = E;
+  if (E > cap) {
+    set_error("ringo_graph_to_edge_table: the graph has more edges than cap");
+    return RINGO_ERANGE;
+  }
+  if (E && (!d_src || !d_dst)) return RINGO_EINVAL;
+  cudaStream_t s = stream ? (cudaStream_t)stream : g->stream;
+  const uint32_t V = (uint32_t)g->info.num_nodes;
+  // out-CSR rows are (src, dst); in-CSR rows are (dst, src), swapped back
+  if (dir == RINGO_OUT)
+    return launch_edge_table(g->node_ids, g->out_off, g->out_nbr, V, (uint64_t)E, d_src, d_dst, s);
+  return launch_edge_table(g->node_ids, g->in_off, g->in_nbr, V, (uint64_t)E, d_dst, d_src, s);
+}
+
+int ringo_graph_to_node_table(const ringo_graph* g, int32_t* d_ids, int64_t* d_outdeg,
+                              int64_t* d_indeg, int64_t cap, int64_t* n, void* stream) {
+  if (!g || !n || cap < 0) return RINGO_EINVAL;
+  const int64_t V = g->info.num_nodes;
+  *n = V;
+  if (V > cap) {
+    set_error("ringo_graph_to_node_table: the graph has more nodes than cap");
+    return RINGO_ERANGE;
+  }
+  if (V && (!d_ids || !d_outdeg || !d_indeg)) return RINGO_EINVAL;
+  cudaStream_t s = stream ? (cudaStream_t)stream : g->stream;
+  return launch_node_table(g->node_ids, g->out_off, g->in_off, (uint32_t)V, d_ids, d_outdeg,
+                           d_indeg, s);
+}
+
+int ringo_graph_pagerank(const ringo_graph* g, double damping, int32_t iterations, double* d_rank,
+                         void* stream) {
+  if (!g || iterations < 0 || !(damping >= 0.0 && damping <= 1.0)) return RINGO_EINVAL;
+  const int64_t V = g->info.num_nodes, E = g->info.num_edges;
+  if (V && !d_rank) return RINGO_EINVAL;
+  cudaStream_t s = stream ? (cudaStream_t)stream : g->stream;
+  return run_pagerank(g->out_off, g->in_off, g->in_nbr, (uint32_t)V, (uint64_t)E, damping,
+                      iterations, d_rank, s);
+}
+
 void ringo_graph_free(ringo_graph* g) {
   if (!g) return;
   free_graph_arrays(g);

@@ -1208,6 +1208,24 @@ int ringo_batch_degree_topk(const ringo_batch* bt, int32_t i, int dir, int32_t k
   return rc;
 }
 
+int ringo_batch_graph_to_edge_table(const ringo_batch* bt, int32_t i, int dir, int32_t* d_src,
+                                    int32_t* d_dst, int64_t cap, int64_t* n, void* stream) {
+  if (!bt || !n || i < 0 || i >= (int32_t)bt->res.size() || cap < 0 ||
+      (dir != RINGO_OUT && dir != RINGO_IN))
+    return RINGO_EINVAL;
+  const int64_t E = bt->res[i].E;
+  *n = E;
+  if (E > cap) return RINGO_ERANGE;
+  if (E && (!d_src || !d_dst)) return RINGO_EINVAL;
+  cudaStream_t s = stream ? (cudaStream_t)stream : bt->stream;
+  const uint32_t V = bt->res[i].V;
+  if (dir == RINGO_OUT)
+    return launch_edge_table(bt->node_ids[i], bt->out_off[i], bt->out_nbr[i], V, (uint64_t)E,
+                             d_src, d_dst, s);
+  return launch_edge_table(bt->node_ids[i], bt->in_off[i], bt->in_nbr[i], V, (uint64_t)E, d_dst,
+                           d_src, s);
+}
+
 void ringo_batch_free(ringo_batch* bt) {
   if (!bt) return;
   for (void* p : bt->blocks) pool_free(p, bt->stream);

@@ -33,11 +33,12 @@ __device__ __forceinline__ ScanChunks chunks_of(const Ctl* ctl, int i) {
 //   out_nbr[e]               = dst-run index (turned into a node index later)
 //   usrc[s], usrc_start[s]   = src ID and its first edge; usrc_start[Vs] = E
 //   in_sort.hist             = digit histograms of the in-sort passes
-__global__ void __launch_bounds__(kScanThreads, 4)
+__global__ void __launch_bounds__(kScanThreads, 6)
     k_dedup(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
+  __shared__ uint64_t s_keys[kScanTile];  // the tile, read once, coalesced
   __shared__ uint32_t s_hist[kInPasses][kRadix];
   __shared__ uint32_t s_we[kWarps], s_ws[kWarps];
-  __shared__ uint64_t s_prefix;
+  __shared__ uint64_t s_prefix, s_before;
   __shared__ Claim s_cl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) claim_slot(m, counter, &s_cl);
@@ -50,35 +51,30 @@ __global__ void __launch_bounds__(kScanThreads, 4)
   const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
   if (tile >= ntiles) return;
   const uint64_t* __restrict__ keys = ctl->out_sort.result;
-  const uint32_t wbase = tile * (uint32_t)kScanTile + warp * (kScanItems * 32);
+  const uint32_t base = tile * (uint32_t)kScanTile;
+  const uint32_t cnt = min((uint32_t)kScanTile, n - base);
   // in-sort digit positions that can vary: dst-run indices are below Vd
   const uint32_t Vd = ctl->Vd;
   int npos = 1;
   while (npos < kInPasses && ((Vd - 1) >> (8 * npos)) != 0) ++npos;
+  for (uint32_t j = tid; j < cnt; j += kScanThreads) s_keys[j] = __ldcs(keys + base + j);
+  if (tid == 0) s_before = base > 0 ? keys[base - 1] : 0;
+  __syncthreads();
 
-  uint64_t key[kScanItems];
-  uint32_t valid = 0;
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const uint32_t pos = wbase + i * 32 + lane;
-    key[i] = pos < n ? __ldcs(keys + pos) : 0;
-    if (pos < n) valid |= 1u << i;
-  }
-  uint64_t before = 0;  // key just before this warp's first item
-  if (wbase > 0 && wbase <= n) before = keys[wbase - 1];
-
+  const uint32_t wl = warp * (kScanItems * 32);  // the warp's first item in the tile
   const uint32_t lt = lanemask_lt();
   uint32_t he = 0, hs = 0, ce = 0, cs = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, key[i], 1);
-    const uint64_t last_prev_item = __shfl_sync(0xFFFFFFFFu, i ? key[i - 1] : before, 31);
-    if (lane == 0) prev = i ? last_prev_item : before;
-    const uint32_t pos = wbase + i * 32 + lane;
-    const bool ok = (valid >> i) & 1u;
-    const bool first = pos == 0;
-    const bool h_e = ok && (first || key[i] != prev);
-    const bool h_s = ok && (first || (key[i] >> 32) != (prev >> 32));
+    const uint32_t j = wl + i * 32 + lane;
+    bool h_e = false, h_s = false;
+    if (j < cnt) {
+      const uint64_t k = s_keys[j];
+      const uint64_t p = j ? s_keys[j - 1] : s_before;
+      const bool first = base + j == 0;
+      h_e = first || k != p;
+      h_s = first || (k >> 32) != (p >> 32);
+    }
     ce += __popc(__ballot_sync(0xFFFFFFFFu, h_e));
     cs += __popc(__ballot_sync(0xFFFFFFFFu, h_s));
     he |= (uint32_t)h_e << i;
@@ -122,31 +118,30 @@ __global__ void __launch_bounds__(kScanThreads, 4)
   int32_t* __restrict__ usrc_start = ctl->usrc_start;
   const int top = npos - 1;
   uint32_t ce2 = 0, cs2 = 0;  // heads of earlier items of this warp (positions recomputed)
-#pragma unroll
+#pragma unroll 1
   for (int i = 0; i < kScanItems; ++i) {
     const bool h = (he >> i) & 1u;
     const bool head_s = (hs >> i) & 1u;
-    const uint32_t db = (uint32_t)key[i];
     const uint32_t emask = __ballot_sync(0xFFFFFFFFu, h);
     const uint32_t smask = __ballot_sync(0xFFFFFFFFu, head_s);
     const uint32_t e = e0 + ce2 + __popc(emask & lt);
     const uint32_t s = s0 + cs2 + __popc(smask & lt);
     ce2 += __popc(emask);
     cs2 += __popc(smask);
+    if (!h) continue;
+    const uint64_t k = s_keys[wl + i * 32 + lane];
+    const uint32_t db = (uint32_t)k;
     // the highest varying position takes few values: one add per value per
     // warp instead of up to 32 colliding adds on one counter
-    if (h) {
-      const uint32_t td = (db >> (8 * top)) & 0xFFu;
-      const uint32_t peers = __match_any_sync(emask, td);
-      if (lane == 31 - __clz(peers)) atomicAdd(&s_hist[top][td], (uint32_t)__popc(peers));
-    }
-    if (!h) continue;
+    const uint32_t td = (db >> (8 * top)) & 0xFFu;
+    const uint32_t peers = __match_any_sync(emask, td);
+    if (lane == 31 - __clz(peers)) atomicAdd(&s_hist[top][td], (uint32_t)__popc(peers));
     const uint32_t sidx = head_s ? s : s - 1;
     ekeys[e] = ((uint64_t)db << 32) | sidx;
     out_nbr[e] = (int32_t)db;
     for (int p = 0; p < top; ++p) atomicAdd(&s_hist[p][(db >> (8 * p)) & 0xFFu], 1u);
     if (head_s) {
-      usrc[s] = unbias((uint32_t)(key[i] >> 32));
+      usrc[s] = unbias((uint32_t)(k >> 32));
       usrc_start[s] = (int32_t)e;
     }
   }
@@ -169,8 +164,10 @@ void launch_dedup(const Launch& L, uint32_t* counter, cudaStream_t s) {
 // Reads rank_step.in (or packs from the columns when every dst pass was
 // trivial) and writes rank_step.out.  Single-pass compaction count with
 // decoupled look-back.
-__global__ void __launch_bounds__(kScanThreads, 4)
+__global__ void __launch_bounds__(kScanThreads, 6)
     k_dst_rank(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
+  __shared__ uint64_t s_keys[kScanTile];  // the tile, read once, coalesced
+  __shared__ uint64_t s_before;           // the key just before the tile
   __shared__ uint32_t s_w[kWarps];
   __shared__ uint64_t s_prefix;
   __shared__ Claim s_cl;
@@ -191,31 +188,27 @@ __global__ void __launch_bounds__(kScanThreads, 4)
     if (in) return in[pos];
     return ((uint64_t)((uint32_t)src[pos] ^ kBias) << 32) | ((uint32_t)dst[pos] ^ kBias);
   };
-  const uint32_t wbase = tile * (uint32_t)kScanTile + warp * (kScanItems * 32);
-  uint64_t key[kScanItems];
-  uint32_t valid = 0;
-#pragma unroll
-  for (int i = 0; i < kScanItems; ++i) {
-    const uint32_t pos = wbase + i * 32 + lane;
-    if (pos < n) {
-      key[i] = in ? __ldcs(in + pos) : key_at(pos);
-      valid |= 1u << i;
-    } else {
-      key[i] = 0;
-    }
+  const uint32_t base = tile * (uint32_t)kScanTile;
+  const uint32_t cnt = min((uint32_t)kScanTile, n - base);
+  if (in) {
+    for (uint32_t j = tid; j < cnt; j += kScanThreads) s_keys[j] = __ldcs(in + base + j);
+  } else {
+    for (uint32_t j = tid; j < cnt; j += kScanThreads) s_keys[j] = key_at(base + j);
   }
-  uint64_t before = 0;
-  if (wbase > 0 && wbase <= n) before = key_at(wbase - 1);
+  if (tid == 0) s_before = base > 0 ? key_at(base - 1) : 0;
+  __syncthreads();
+  const uint32_t wl = warp * (kScanItems * 32);  // the warp's first item in the tile
   const uint32_t lt = lanemask_lt();
   uint32_t hd = 0, cd = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, key[i], 1);
-    const uint64_t last_prev_item = __shfl_sync(0xFFFFFFFFu, i ? key[i - 1] : before, 31);
-    if (lane == 0) prev = i ? last_prev_item : before;
-    const uint32_t pos = wbase + i * 32 + lane;
-    const bool ok = (valid >> i) & 1u;
-    const bool h = ok && (pos == 0 || (uint32_t)key[i] != (uint32_t)prev);
+    const uint32_t j = wl + i * 32 + lane;
+    bool h = false;
+    if (j < cnt) {
+      const uint64_t k = s_keys[j];
+      const uint64_t p = j ? s_keys[j - 1] : s_before;
+      h = (base + j == 0) || (uint32_t)k != (uint32_t)p;
+    }
     cd += __popc(__ballot_sync(0xFFFFFFFFu, h));
     hd |= (uint32_t)h << i;
   }
@@ -244,10 +237,12 @@ __global__ void __launch_bounds__(kScanThreads, 4)
     const uint32_t b = __ballot_sync(0xFFFFFFFFu, h);
     const uint32_t dl = cd2 + __popc(b & lt);
     cd2 += __popc(b);
-    if (!((valid >> i) & 1u)) continue;
+    const uint32_t j = wl + i * 32 + lane;
+    if (j >= cnt) continue;
+    const uint64_t k = s_keys[j];
     const uint32_t r = d0 + dl + (h ? 0u : 0xFFFFFFFFu);  // inclusive count - 1
-    __stcs(out + wbase + i * 32 + lane, (key[i] & 0xFFFFFFFF00000000ull) | r);
-    if (h) udst[r] = unbias((uint32_t)key[i]);
+    __stcs(out + base + j, (k & 0xFFFFFFFF00000000ull) | r);
+    if (h) udst[r] = unbias((uint32_t)k);
   }
 }
 

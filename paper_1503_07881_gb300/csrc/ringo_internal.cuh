@@ -207,6 +207,14 @@ void launch_dedup(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_dst_runs(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_phase2_maps(const Launch& L, cudaStream_t s);
 void launch_merge_split(const Launch& L, cudaStream_t s);
+// graph -> table (to_table.cu); both return a ringo status
+int launch_edge_table(const int32_t* node_ids, const int64_t* off, const int32_t* nbr, uint32_t V,
+                      uint64_t E, int32_t* key, int32_t* val, cudaStream_t s);
+int launch_node_table(const int32_t* node_ids, const int64_t* out_off, const int64_t* in_off,
+                      uint32_t V, int32_t* ids, int64_t* outdeg, int64_t* indeg, cudaStream_t s);
+// PageRank (pagerank.cu); returns a ringo status
+int run_pagerank(const int64_t* out_off, const int64_t* in_off, const int32_t* in_nbr, uint32_t V,
+                 uint64_t E, double damping, int32_t iterations, double* rank, cudaStream_t s);
 void launch_merge(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_rank_blocks(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_remap(const Launch& L, uint32_t* counter, cudaStream_t s);

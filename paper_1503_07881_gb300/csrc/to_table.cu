@@ -1,0 +1,116 @@
+// Graph -> table conversion (ringo_graph_to_edge_table, ringo_graph_to_node_table
+// and their batch forms).
+//
+// Section 3.4, "Conversion of graphs to tables": a node table or an edge table
+// is built by splitting the graph's nodes or edges among workers, each
+// writing its part of a pre-allocated output.  Here the output columns are
+// pre-allocated by the caller and every edge is one work item: a 2048-edge
+// tile finds the source nodes it spans with one binary search over the
+// offsets, stages their offsets in shared memory, and each edge finds its
+// source there; rows are written coalesced, in CSR order.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ringo.h"
+#include "host_util.h"
+#include "ringo_internal.cuh"
+
+namespace ringo {
+
+namespace {
+
+constexpr uint32_t kExpandTile = 2048;   // edges per tile
+constexpr uint32_t kExpandWindow = 2048; // node offsets staged per tile
+
+// largest r in [0, V) with off[r] <= e (off[0] = 0 <= e < off[V] = E)
+__device__ __forceinline__ uint32_t owner(const int64_t* __restrict__ off, uint32_t V, uint64_t e) {
+  uint32_t lo = 0, hi = V;  // off[lo] <= e < off[hi]
+  while (hi - lo > 1) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    if ((uint64_t)off[mid] <= e) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Rows e of the edge table, in CSR order: key[e] = node_ids[row node],
+// val[e] = node_ids[nbr[e]].  For the out-CSR that is (src, dst); for the
+// in-CSR the caller swaps the columns.
+__global__ void __launch_bounds__(256)
+    k_expand(const int32_t* __restrict__ node_ids, const int64_t* __restrict__ off,
+             const int32_t* __restrict__ nbr, uint32_t V, uint64_t E, int32_t* __restrict__ key,
+             int32_t* __restrict__ val) {
+  __shared__ int64_t s_off[kExpandWindow + 1];
+  __shared__ uint32_t s_r0, s_r1;
+  for (uint64_t e0 = (uint64_t)blockIdx.x * kExpandTile; e0 < E;
+       e0 += (uint64_t)gridDim.x * kExpandTile) {
+    const uint64_t e1 = min(e0 + kExpandTile, E);
+    __syncthreads();
+    if (threadIdx.x == 0) s_r0 = owner(off, V, e0);
+    if (threadIdx.x == 32) s_r1 = owner(off, V, e1 - 1);
+    __syncthreads();
+    const uint32_t r0 = s_r0, r1 = s_r1;
+    const uint32_t w = r1 - r0 + 1;  // nodes spanned by the tile
+    const bool staged = w <= kExpandWindow;
+    if (staged)
+      for (uint32_t t = threadIdx.x; t <= w; t += blockDim.x) s_off[t] = off[r0 + t];
+    __syncthreads();
+    for (uint64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      uint32_t r;
+      if (staged) {  // largest t in [0, w) with s_off[t] <= e
+        uint32_t lo = 0, hi = w;
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if ((uint64_t)s_off[mid] <= e) lo = mid;
+          else hi = mid;
+        }
+        r = r0 + lo;
+      } else {
+        r = owner(off, V, e);
+      }
+      const int32_t m = __ldcs(nbr + e);
+      key[e] = node_ids[r];
+      val[e] = (uint32_t)m < V ? __ldg(node_ids + m) : 0;
+    }
+  }
+}
+
+__global__ void k_node_table(const int32_t* __restrict__ node_ids, const int64_t* __restrict__ out_off,
+                             const int64_t* __restrict__ in_off, uint32_t V, int32_t* __restrict__ ids,
+                             int64_t* __restrict__ outdeg, int64_t* __restrict__ indeg) {
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < V; r += gridDim.x * blockDim.x) {
+    ids[r] = node_ids[r];
+    outdeg[r] = out_off[r + 1] - out_off[r];
+    indeg[r] = in_off[r + 1] - in_off[r];
+  }
+}
+
+}  // namespace
+
+int launch_edge_table(const int32_t* node_ids, const int64_t* off, const int32_t* nbr, uint32_t V,
+                      uint64_t E, int32_t* key, int32_t* val, cudaStream_t s) {
+  if (E == 0) return RINGO_OK;
+  uint64_t grid = (E + kExpandTile - 1) / kExpandTile;
+  if (grid > 65535) grid = 65535;
+  {
+    ProfScope ps("edge_table", s);
+    k_expand<<<(uint32_t)grid, 256, 0, s>>>(node_ids, off, nbr, V, E, key, val);
+  }
+  RINGO_LAUNCH_CHECK("k_expand");
+  return RINGO_OK;
+}
+
+int launch_node_table(const int32_t* node_ids, const int64_t* out_off, const int64_t* in_off,
+                      uint32_t V, int32_t* ids, int64_t* outdeg, int64_t* indeg, cudaStream_t s) {
+  if (V == 0) return RINGO_OK;
+  uint32_t grid = (V + 255) / 256;
+  if (grid > 8192) grid = 8192;
+  {
+    ProfScope ps("node_table", s);
+    k_node_table<<<grid, 256, 0, s>>>(node_ids, out_off, in_off, V, ids, outdeg, indeg);
+  }
+  RINGO_LAUNCH_CHECK("k_node_table");
+  return RINGO_OK;
+}
+
+}  // namespace ringo

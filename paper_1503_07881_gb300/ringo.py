@@ -93,6 +93,11 @@ SIGNATURES = {
     "ringo_result_topk": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _I32, _P]),
     "ringo_result_copy_graph_to_host": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "ringo_result_free": (None, [_P]),
+    "ringo_graph_to_edge_table": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _I64, _P, _P]),
+    "ringo_graph_to_node_table": (ctypes.c_int, [_P, _P, _P, _P, _I64, _P, _P]),
+    "ringo_batch_graph_to_edge_table": (ctypes.c_int, [_P, _I32, ctypes.c_int, _P, _P, _I64, _P,
+                                                       _P]),
+    "ringo_graph_pagerank": (ctypes.c_int, [_P, ctypes.c_double, _I32, _P, _P]),
     "ringo_profile_start": (ctypes.c_int, []),
     "ringo_profile_stop": (ctypes.c_int, [ctypes.POINTER(KernelStat), _I32, _P]),
 }
@@ -226,6 +231,47 @@ class Graph:
                                               degs.ctypes.data, ctypes.byref(n)),
                "ringo_graph_degree_topk")
         return ids[:n.value].copy(), degs[:n.value].copy()
+
+    def to_edge_table(self, direction: int = RINGO_OUT, out=None,
+                      stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+        """Section 3.4 graph -> table: (src, dst) ID columns, one row per edge,
+        in the CSR order of `direction`.  `out` may give two int32 CUDA tensors
+        of at least E entries."""
+        E = self.num_edges
+        if out is None:
+            out = (torch.empty(max(E, 1), dtype=torch.int32, device="cuda"),
+                   torch.empty(max(E, 1), dtype=torch.int32, device="cuda"))
+        src, dst = out
+        n = ctypes.c_int64()
+        _check(load().ringo_graph_to_edge_table(self.handle, direction, src.data_ptr(),
+                                                dst.data_ptr(), min(src.numel(), dst.numel()),
+                                                ctypes.byref(n), _stream_ptr(stream)),
+               "ringo_graph_to_edge_table")
+        return src[:n.value], dst[:n.value]
+
+    def pagerank(self, damping: float = 0.85, iterations: int = 10, out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+        """PageRank (fp64, node index order) as a CUDA tensor."""
+        V = self.num_nodes
+        if out is None:
+            out = torch.empty(max(V, 1), dtype=torch.float64, device="cuda")
+        _check(load().ringo_graph_pagerank(self.handle, float(damping), int(iterations),
+                                           out.data_ptr(), _stream_ptr(stream)),
+               "ringo_graph_pagerank")
+        return out[:V]
+
+    def to_node_table(self, stream=None) -> tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
+        """(node IDs ascending, out-degree, in-degree) as CUDA tensors."""
+        V = self.num_nodes
+        ids = torch.empty(max(V, 1), dtype=torch.int32, device="cuda")
+        od = torch.empty(max(V, 1), dtype=torch.int64, device="cuda")
+        idg = torch.empty(max(V, 1), dtype=torch.int64, device="cuda")
+        n = ctypes.c_int64()
+        _check(load().ringo_graph_to_node_table(self.handle, ids.data_ptr(), od.data_ptr(),
+                                                idg.data_ptr(), V, ctypes.byref(n),
+                                                _stream_ptr(stream)),
+               "ringo_graph_to_node_table")
+        return ids[:V], od[:V], idg[:V]
 
     def copy_to_host(self, out: dict | None = None) -> dict:
         """All five arrays into host memory (numpy, or caller-given buffers)."""
@@ -457,6 +503,19 @@ class Batch:
             "ringo_batch_copy_graph_to_host")
         out["num_nodes"], out["num_edges"] = V, E
         return out
+
+    def to_edge_table(self, i: int, direction: int = RINGO_OUT,
+                      stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+        """Edge table of graph i (as Graph.to_edge_table)."""
+        E = self.info(i)["num_edges"]
+        src = torch.empty(max(E, 1), dtype=torch.int32, device="cuda")
+        dst = torch.empty(max(E, 1), dtype=torch.int32, device="cuda")
+        n = ctypes.c_int64()
+        _check(load().ringo_batch_graph_to_edge_table(self._h, i, direction, src.data_ptr(),
+                                                      dst.data_ptr(), E, ctypes.byref(n),
+                                                      _stream_ptr(stream)),
+               "ringo_batch_graph_to_edge_table")
+        return src[:n.value], dst[:n.value]
 
     def degree_topk(self, i: int, direction: int, k: int) -> tuple[np.ndarray, np.ndarray]:
         ids = np.zeros(max(k, 1), np.int32)

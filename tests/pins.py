@@ -227,3 +227,51 @@ def check_row_order_and_duplicates(convert, src, dst, seed: int = 3) -> None:
         s2 = np.concatenate([src, np.asarray(src)[extra]])
         d2 = np.concatenate([dst, np.asarray(dst)[extra]])
         assert_same_graph(convert(s2, d2), base, "with duplicates")
+
+
+# ------------------------------------------------------------ graph -> table
+def expected_tables(src, dst) -> dict:
+    """Section 3.4, "Conversion of graphs to tables", on the graph of a table:
+    one edge-table row per distinct row of the table (set semantics), in
+    (src, dst) order for the out-CSR and (dst, src) order for the in-CSR;
+    one node-table row per distinct ID, with the number of distinct rows that
+    leave and that enter it.  Plain Python sets and sorts."""
+    rows = sorted(set(zip((int(x) for x in src), (int(x) for x in dst))))
+    rows_in = sorted(rows, key=lambda r: (r[1], r[0]))
+    ids = sorted(set(int(x) for x in src) | set(int(x) for x in dst))
+    outdeg = {i: 0 for i in ids}
+    indeg = {i: 0 for i in ids}
+    for a, b in rows:
+        outdeg[a] += 1
+        indeg[b] += 1
+    col = lambda xs: np.array(xs, dtype=np.int32)
+    return {"out_src": col([r[0] for r in rows]), "out_dst": col([r[1] for r in rows]),
+            "in_src": col([r[0] for r in rows_in]), "in_dst": col([r[1] for r in rows_in]),
+            "ids": col(ids), "outdeg": np.array([outdeg[i] for i in ids], np.int64),
+            "indeg": np.array([indeg[i] for i in ids], np.int64)}
+
+
+def assert_same_tables(got: dict, want: dict, what: str = "") -> None:
+    for k in ("out_src", "out_dst", "in_src", "in_dst", "ids", "outdeg", "indeg"):
+        g, w = np.asarray(got[k]), np.asarray(want[k])
+        assert g.shape == w.shape and np.array_equal(g, w), f"{what}: {k} differs"
+
+
+def check_graph_to_table(tables, max_rows: int = 3, trials: int = 100, seed: int = 11) -> None:
+    """`tables(src, dst)` returns the edge tables (both directions) and the
+    node table of the graph of (src, dst); checked on the golden tables, every
+    table of up to max_rows rows over {-1, 0, 1, 2}, and random tables over
+    extreme IDs."""
+    for path in golden_files():
+        t = load_golden(path)
+        assert_same_tables(tables(t["src"], t["dst"]), expected_tables(t["src"], t["dst"]),
+                           os.path.basename(path))
+    for s, d in exhaustive_tables(max_rows=max_rows):
+        assert_same_tables(tables(s, d), expected_tables(s, d), f"{s.tolist()} {d.tolist()}")
+    rng = np.random.default_rng(seed)
+    pool = np.array([-2**31, -2**31 + 1, -7, -1, 0, 1, 5, 2**31 - 2, 2**31 - 1], np.int32)
+    for _ in range(trials):
+        n = int(rng.integers(0, 40))
+        s = pool[rng.integers(0, pool.size, n)]
+        d = pool[rng.integers(0, pool.size, n)]
+        assert_same_tables(tables(s, d), expected_tables(s, d), "random")

@@ -108,3 +108,97 @@ def test_pins_catch_planted_mistake(mutant):
         except (AssertionError, IndexError, ValueError):
             caught.append(name)
     assert caught, f"mutant {mutant} ({MUTANTS[mutant]}) passed every pin"
+
+
+def oracle_tables(src, dst, mutant: int = 0) -> dict:
+    g = oracle.table_to_graph(src, dst)
+    os_, od = oracle.graph_to_edge_table(g, "out", mutant=mutant)
+    is_, id_ = oracle.graph_to_edge_table(g, "in", mutant=mutant)
+    ids, outdeg, indeg = oracle.graph_to_node_table(g)
+    return {"out_src": os_, "out_dst": od, "in_src": is_, "in_dst": id_, "ids": ids,
+            "outdeg": outdeg, "indeg": indeg}
+
+
+def test_graph_to_table_pins():
+    pins.check_graph_to_table(oracle_tables)
+
+
+def test_graph_to_table_round_trip():
+    # the edge table converts back to the same graph, in either row order
+    rng = np.random.default_rng(4)
+    for n in (0, 1, 17, 500):
+        s = rng.integers(-50, 50, n).astype(np.int32)
+        d = rng.integers(-50, 50, n).astype(np.int32)
+        g = oracle.table_to_graph(s, d)
+        for direction in ("out", "in"):
+            pins.assert_same_graph(oracle.table_to_graph(*oracle.graph_to_edge_table(g, direction)),
+                                   g, f"round trip {direction} n={n}")
+
+
+@pytest.mark.parametrize("mutant", [7, 8])
+def test_graph_to_table_pins_catch_planted_mistake(mutant):
+    with pytest.raises(AssertionError):
+        pins.check_graph_to_table(lambda s, d: oracle_tables(s, d, mutant=mutant))
+
+
+# ------------------------------------------------------------- PageRank ---
+def dense_pagerank(src, dst, damping=0.85, iterations=10):
+    """Power iteration with the explicit V x V transition matrix (a route
+    independent of the CSR): column-stochastic over out-edges, uniform
+    columns for nodes without out-edges, then teleportation."""
+    ids = sorted(set(int(x) for x in src) | set(int(x) for x in dst))
+    idx = {x: i for i, x in enumerate(ids)}
+    V = len(ids)
+    A = np.zeros((V, V))
+    for a, b in set(zip((int(x) for x in src), (int(x) for x in dst))):
+        A[idx[b], idx[a]] = 1.0
+    colsum = A.sum(axis=0)
+    M = np.where(colsum > 0, A / np.maximum(colsum, 1), 1.0 / V)
+    G = damping * M + (1 - damping) / V
+    pr = np.full(V, 1.0 / V)
+    for _ in range(iterations):
+        pr = G @ pr
+    return pr
+
+
+def test_pagerank_matches_dense_power_iteration():
+    rng = np.random.default_rng(9)
+    for n in (1, 3, 20, 200):
+        for _ in range(5):
+            s = rng.integers(-8, 8, n).astype(np.int32)
+            d = rng.integers(-8, 8, n).astype(np.int32)
+            g = oracle.table_to_graph(s, d)
+            for iters in (0, 1, 10, 30):
+                got = oracle.pagerank(g, 0.85, iters)
+                want = dense_pagerank(s, d, 0.85, iters)
+                assert np.allclose(got, want, rtol=1e-12, atol=1e-15)
+    for t in (pins.load_golden(p) for p in pins.golden_files()):
+        if len(t["src"]):
+            g = oracle.table_to_graph(t["src"], t["dst"])
+            assert np.allclose(oracle.pagerank(g), dense_pagerank(t["src"], t["dst"]), rtol=1e-12)
+
+
+def test_pagerank_closed_forms_and_conservation():
+    # a directed cycle stays uniform; one self-loop holds all the rank
+    n = 7
+    s = np.arange(n, dtype=np.int32)
+    g = oracle.table_to_graph(s, (s + 1) % n)
+    assert np.allclose(oracle.pagerank(g, 0.85, 10), 1.0 / n, rtol=0, atol=1e-15)
+    g = oracle.table_to_graph(np.array([4], np.int32), np.array([4], np.int32))
+    assert np.allclose(oracle.pagerank(g), [1.0])
+    # two nodes a -> b: b is dangling; after one step
+    # PR(a) = (1-d)/2 + d*(0.5/2), PR(b) = (1-d)/2 + d*(0.5 + 0.5/2)
+    g = oracle.table_to_graph(np.array([1], np.int32), np.array([2], np.int32))
+    d = 0.85
+    assert np.allclose(oracle.pagerank(g, d, 1), [(1 - d) / 2 + d * 0.25, (1 - d) / 2 + d * 0.75])
+    # the total rank stays 1
+    s, dd = tg.make_table(tg.SPECS["lj"].scaled(20_000), seed=3)
+    g = oracle.table_to_graph(s.numpy(), dd.numpy())
+    assert abs(oracle.pagerank(g).sum() - 1.0) < 1e-12
+
+
+def test_pagerank_pins_catch_dropped_dangling_mass():
+    g = oracle.table_to_graph(np.array([1, 1, 3], np.int32), np.array([2, 3, 1], np.int32))
+    bad = oracle.pagerank(g, drop_dangling=True)
+    assert abs(bad.sum() - 1.0) > 1e-3
+    assert not np.allclose(bad, dense_pagerank([1, 1, 3], [2, 3, 1]), rtol=1e-6)
