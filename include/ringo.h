@@ -208,10 +208,12 @@ RINGO_API int ringo_graph_to_node_table(const ringo_graph* g, int32_t* d_ids, in
  *                               + sum of PR over nodes without out-edges / V),
  * `iterations` steps (0 gives the uniform vector), d = damping in [0, 1].
  * Writes PR in node-index order to caller-owned device d_rank[V].  Enqueued
- * on `stream` (NULL: the graph's stream); scratch of 16 V bytes comes from
- * the library's pool.  Sums are formed in a different order than a
- * sequential loop, so results agree with one to within fp64 rounding (about
- * max in-degree x 1e-16 relative per step), not bit for bit.
+ * on `stream` (NULL: the graph's stream); scratch of about 16 V + E / 1024
+ * bytes comes from the library's pool.  Each node's sum is formed in a fixed
+ * order (per-warp lanes, or fixed chunks for nodes of more than 8192
+ * in-edges), so runs agree bit for bit; a sequential loop sums in another
+ * order and agrees to within fp64 rounding (about max in-degree x 1e-16
+ * relative per step).
  * Errors: EINVAL (NULL g, NULL d_rank with V > 0, iterations < 0, damping
  * outside [0, 1]), ENOMEM, ECUDA.
  */

@@ -5,21 +5,24 @@
 //   PR'(v) = (1 - d) / V + d * ( sum over in-neighbours u of PR(u) / outdeg(u)
 //                                + (sum of PR over nodes without out-edges) / V ).
 //
-// One iteration is three launches:
-//   edges: in-CSR tiles of 2048 edges; each thread sums the contributions of
-//          its 8 consecutive in-edges per target node, the block adds its
-//          threads' sums per node in shared memory, and one global add per
-//          (tile, node) gives sum[v] (so a node with millions of in-edges gets
-//          one add per tile, not per edge);
-//   nodes: PR(v), the next contributions PR(v) / outdeg(v), sum[v] cleared,
-//          and per-block sums of PR over nodes without out-edges;
-//   reduce: those block sums in a fixed order (one block).
+// Each node's sum over its in-edges is formed in a fixed order, so the
+// result is the same on every run:
+//   light nodes (in-degree up to kBig): one warp per node, lanes striding over
+//          its in-edges (coalesced index loads, independent gathers), a
+//          fixed-order warp reduction, one plain store;
+//   heavy nodes: split into kBig-edge chunks, one block per chunk with a
+//          fixed-order block reduction, then the chunks of each node added in
+//          order;
+//   nodes: PR(v), the next contributions PR(v) / outdeg(v), and per-block
+//          sums of PR over nodes without out-edges, reduced in a fixed order.
+// The heavy-node list and its chunk offsets are built once per call.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <string>
 
 #include "../../include/ringo.h"
+#include "device_util.cuh"
 #include "host_util.h"
 #include "ringo_internal.cuh"
 
@@ -27,89 +30,128 @@ namespace ringo {
 
 namespace {
 
-constexpr uint32_t kPrTile = 2048;    // in-edges per tile
-constexpr uint32_t kPrItems = 8;      // per thread
-constexpr uint32_t kPrWindow = 2048;  // target nodes staged per tile
-constexpr uint32_t kNodeGrid = 1024;  // blocks of the node pass (fixed: partial sums)
+constexpr uint32_t kBig = 8192;        // in-edges above which a node is split into chunks
+constexpr uint32_t kNodeGrid = 1024;   // blocks of the node pass (fixed: partial sums)
 
 struct PrState {
   double dangling;  // sum of PR over nodes without out-edges, for this iteration
 };
 
-__device__ __forceinline__ uint32_t pr_owner(const int64_t* __restrict__ off, uint32_t V, uint64_t e) {
-  uint32_t lo = 0, hi = V;  // off[lo] <= e < off[hi]
-  while (hi - lo > 1) {
-    const uint32_t mid = lo + ((hi - lo) >> 1);
-    if ((uint64_t)off[mid] <= e) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
+// Light nodes: one warp per node (grid-stride over warps).  sum[v] is
+// written for every node of in-degree at most kBig, 0 when it has none.
 __global__ void __launch_bounds__(256)
-    k_pr_edges(const int64_t* __restrict__ in_off, const int32_t* __restrict__ in_nbr, uint32_t V,
-               uint64_t E, const double* __restrict__ contrib, double* __restrict__ sum) {
-  __shared__ int64_t s_off[kPrWindow + 1];
-  __shared__ double s_acc[kPrWindow];
-  __shared__ uint32_t s_r0, s_r1;
-  for (uint64_t e0 = (uint64_t)blockIdx.x * kPrTile; e0 < E; e0 += (uint64_t)gridDim.x * kPrTile) {
-    const uint64_t e1 = min(e0 + kPrTile, E);
-    __syncthreads();
-    if (threadIdx.x == 0) s_r0 = pr_owner(in_off, V, e0);
-    if (threadIdx.x == 32) s_r1 = pr_owner(in_off, V, e1 - 1);
-    __syncthreads();
-    const uint32_t r0 = s_r0, r1 = s_r1;
-    const uint32_t w = r1 - r0 + 1;
-    const bool staged = w <= kPrWindow;
-    if (staged) {
-      for (uint32_t t = threadIdx.x; t <= w; t += blockDim.x) s_off[t] = in_off[r0 + t];
-      for (uint32_t t = threadIdx.x; t < w; t += blockDim.x) s_acc[t] = 0.0;
+    k_pr_light(const int64_t* __restrict__ in_off, const int32_t* __restrict__ in_nbr, uint32_t V,
+               const double* __restrict__ contrib, double* __restrict__ sum) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t v = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < V;
+       v += warps) {
+    const int64_t a = in_off[v], b = in_off[v + 1];
+    if (b - a > (int64_t)kBig) continue;  // heavy: summed by chunks
+    double acc = 0.0;
+    int64_t e = a + lane;
+    for (; e + 96 < b; e += 128) {  // four independent gathers in flight per lane
+      const uint32_t u0 = (uint32_t)__ldcs(in_nbr + e), u1 = (uint32_t)__ldcs(in_nbr + e + 32);
+      const uint32_t u2 = (uint32_t)__ldcs(in_nbr + e + 64), u3 = (uint32_t)__ldcs(in_nbr + e + 96);
+      const double c0 = u0 < V ? __ldg(contrib + u0) : 0.0, c1 = u1 < V ? __ldg(contrib + u1) : 0.0;
+      const double c2 = u2 < V ? __ldg(contrib + u2) : 0.0, c3 = u3 < V ? __ldg(contrib + u3) : 0.0;
+      acc += (c0 + c1) + (c2 + c3);
     }
-    __syncthreads();
-    const uint64_t a = e0 + (uint64_t)threadIdx.x * kPrItems;
-    if (a < e1) {
-      const uint64_t b = min(a + kPrItems, e1);
-      // the target node of edge a
-      uint32_t r;
-      if (staged) {
-        uint32_t lo = 0, hi = w;
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if ((uint64_t)s_off[mid] <= a) lo = mid;
-          else hi = mid;
-        }
-        r = r0 + lo;
-      } else {
-        r = pr_owner(in_off, V, a);
-      }
-      uint64_t next = staged ? (uint64_t)s_off[r - r0 + 1] : (uint64_t)in_off[r + 1];
-      double acc = 0.0;
-      for (uint64_t e = a; e < b; ++e) {
-        while (e >= next) {  // the next target node (skipping nodes without in-edges)
-          if (acc != 0.0) {
-            if (staged) atomicAdd(&s_acc[r - r0], acc);
-            else atomicAdd(&sum[r], acc);
-          }
-          acc = 0.0;
-          ++r;
-          next = staged ? (uint64_t)s_off[r - r0 + 1] : (uint64_t)in_off[r + 1];
-        }
-        const uint32_t u = (uint32_t)__ldcs(in_nbr + e);
-        acc += u < V ? __ldg(contrib + u) : 0.0;
-      }
-      if (acc != 0.0) {
-        if (staged) atomicAdd(&s_acc[r - r0], acc);
-        else atomicAdd(&sum[r], acc);
-      }
+    for (; e < b; e += 32) {
+      const uint32_t u = (uint32_t)__ldcs(in_nbr + e);
+      acc += u < V ? __ldg(contrib + u) : 0.0;
     }
-    __syncthreads();
-    if (staged)
-      for (uint32_t t = threadIdx.x; t < w; t += blockDim.x)
-        if (s_acc[t] != 0.0) atomicAdd(&sum[r0 + t], s_acc[t]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if (lane == 0) sum[v] = acc;
   }
 }
 
-// New ranks; next contributions; sum cleared; block sums of dangling rank.
+// The heavy nodes (in-degree above kBig), in any order, and their count.
+__global__ void k_pr_heavy_list(const int64_t* __restrict__ in_off, uint32_t V, uint32_t* heavy,
+                                uint32_t* nheavy) {
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
+    if (in_off[v + 1] - in_off[v] > (int64_t)kBig) heavy[atomicAdd(nheavy, 1u)] = v;
+}
+
+// chunk_start[i] = chunks of heavy nodes before heavy[i]; chunk_start[n] = all.  One block.
+__global__ void k_pr_chunk_starts(const int64_t* __restrict__ in_off, const uint32_t* __restrict__ heavy,
+                                  const uint32_t* __restrict__ nheavy, uint32_t* chunk_start) {
+  __shared__ uint32_t s_sw[33];
+  __shared__ uint32_t carry;
+  const uint32_t n = *nheavy;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t b0 = 0; b0 < n; b0 += blockDim.x) {
+    const uint32_t i = b0 + threadIdx.x;
+    uint32_t c = 0;
+    if (i < n) {
+      const uint32_t v = heavy[i];
+      c = (uint32_t)((in_off[v + 1] - in_off[v] + kBig - 1) / kBig);
+    }
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_sum<1024>(c, s_sw, tot);
+    if (i < n) chunk_start[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) chunk_start[n] = carry;
+}
+
+// One block per chunk of kBig in-edges of a heavy node: a fixed-order sum.
+__global__ void __launch_bounds__(256)
+    k_pr_heavy_chunks(const int64_t* __restrict__ in_off, const int32_t* __restrict__ in_nbr,
+                      uint32_t V, const double* __restrict__ contrib,
+                      const uint32_t* __restrict__ heavy, const uint32_t* __restrict__ nheavy,
+                      const uint32_t* __restrict__ chunk_start, double* __restrict__ partial) {
+  __shared__ double s[256];
+  __shared__ uint32_t s_i;
+  const uint32_t n = *nheavy;
+  const uint32_t total = chunk_start[n];
+  for (uint32_t g = blockIdx.x; g < total; g += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x == 0) {  // heavy node owning chunk g: last i with chunk_start[i] <= g
+      uint32_t lo = 0, hi = n;
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (chunk_start[mid] <= g) lo = mid;
+        else hi = mid;
+      }
+      s_i = lo;
+    }
+    __syncthreads();
+    const uint32_t i = s_i, v = heavy[i];
+    const int64_t a = in_off[v] + (int64_t)(g - chunk_start[i]) * kBig;
+    const int64_t b = min(a + (int64_t)kBig, in_off[v + 1]);
+    double acc = 0.0;
+    for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
+      const uint32_t u = (uint32_t)__ldcs(in_nbr + e);
+      acc += u < V ? __ldg(contrib + u) : 0.0;
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (uint32_t k = blockDim.x / 2; k > 0; k >>= 1) {
+      if (threadIdx.x < k) s[threadIdx.x] += s[threadIdx.x + k];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[g] = s[0];
+  }
+}
+
+// sum[heavy node] = its chunks' sums, in chunk order.
+__global__ void k_pr_heavy_sum(const uint32_t* __restrict__ heavy, const uint32_t* __restrict__ nheavy,
+                               const uint32_t* __restrict__ chunk_start,
+                               const double* __restrict__ partial, double* __restrict__ sum) {
+  const uint32_t n = *nheavy;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (uint32_t g = chunk_start[i]; g < chunk_start[i + 1]; ++g) t += partial[g];
+    sum[heavy[i]] = t;
+  }
+}
+
+// New ranks; next contributions; block sums of dangling rank.
 __global__ void __launch_bounds__(256)
     k_pr_nodes(const int64_t* __restrict__ out_off, uint32_t V, double damping, int first,
                const PrState* __restrict__ st, double* __restrict__ pr, double* __restrict__ sum,
@@ -121,7 +163,6 @@ __global__ void __launch_bounds__(256)
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
     const double p = first ? inv_v : base + damping * sum[v];
     pr[v] = p;
-    sum[v] = 0.0;
     const int64_t od = out_off[v + 1] - out_off[v];
     contrib[v] = od > 0 ? p / (double)od : 0.0;
     if (od == 0) dang += p;
@@ -155,20 +196,33 @@ __global__ void k_pr_reduce(const double* __restrict__ partial, uint32_t n, PrSt
 int run_pagerank(const int64_t* out_off, const int64_t* in_off, const int32_t* in_nbr, uint32_t V,
                  uint64_t E, double damping, int32_t iterations, double* rank, cudaStream_t s) {
   if (V == 0) return RINGO_OK;
-  // scratch: contrib[V], sum[V], partial[kNodeGrid], state
-  const size_t bytes = 16 * (size_t)V + 8 * kNodeGrid + 256;
+  // scratch: contrib[V], sum[V], node partials[kNodeGrid], state, heavy list
+  // [V/kBig + 1], chunk starts [V/kBig + 2], chunk partials [E/kBig + V/kBig + 1]
+  const uint64_t max_heavy = E / kBig + 1;
+  const uint64_t max_chunks = E / kBig + max_heavy + 1;
+  const size_t bytes = 16 * (size_t)V + 8 * kNodeGrid + 256 + 4 * (max_heavy + 1) +
+                       4 * (max_heavy + 2) + 8 * max_chunks + 64;
   char* buf = (char*)pool_alloc(bytes, s);
   if (!buf) return RINGO_ENOMEM;
   double* contrib = (double*)buf;
   double* sum = contrib + V;
   double* partial = sum + V;
-  PrState* st = (PrState*)(partial + kNodeGrid);
+  double* cpartial = partial + kNodeGrid;
+  PrState* st = (PrState*)(cpartial + max_chunks);
+  uint32_t* nheavy = (uint32_t*)(st + 1);
+  uint32_t* heavy = nheavy + 4;
+  uint32_t* chunk_start = heavy + max_heavy + 1;
   const uint32_t node_blocks = (V + 255) / 256;
   const uint32_t node_grid = node_blocks < kNodeGrid ? node_blocks : kNodeGrid;
-  uint64_t eg = (E + kPrTile - 1) / kPrTile;
-  const uint32_t edge_grid = (uint32_t)(eg == 0 ? 1 : (eg > 65535 ? 65535 : eg));
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t lw = ((uint64_t)V + 7) / 8;  // 8 warps per block, one node each
+  const uint32_t light_grid = (uint32_t)(lw < (uint64_t)sms * 64 ? lw : (uint64_t)sms * 64);
   int rc = RINGO_OK;
   cudaError_t e = cudaMemsetAsync(buf, 0, bytes, s);
+  k_pr_heavy_list<<<node_grid, 256, 0, s>>>(in_off, V, heavy, nheavy);
+  k_pr_chunk_starts<<<1, 1024, 0, s>>>(in_off, heavy, nheavy, chunk_start);
   // iteration 0 sets the uniform vector and its contributions
   {
     ProfScope ps("pagerank_nodes", s);
@@ -176,9 +230,14 @@ int run_pagerank(const int64_t* out_off, const int64_t* in_off, const int32_t* i
   }
   k_pr_reduce<<<1, 256, 0, s>>>(partial, node_grid, st);
   for (int32_t it = 0; it < iterations; ++it) {
-    if (E) {
+    {
       ProfScope ps("pagerank_edges", s);
-      k_pr_edges<<<edge_grid, 256, 0, s>>>(in_off, in_nbr, V, E, contrib, sum);
+      k_pr_light<<<light_grid, 256, 0, s>>>(in_off, in_nbr, V, contrib, sum);
+      if (E > kBig) {
+        k_pr_heavy_chunks<<<(uint32_t)sms * 4, 256, 0, s>>>(in_off, in_nbr, V, contrib, heavy, nheavy,
+                                                            chunk_start, cpartial);
+        k_pr_heavy_sum<<<64, 256, 0, s>>>(heavy, nheavy, chunk_start, cpartial, sum);
+      }
     }
     {
       ProfScope ps("pagerank_nodes", s);

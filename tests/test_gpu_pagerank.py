@@ -99,3 +99,18 @@ def test_argument_errors():
             g.pagerank(damping, it)
         assert e.value.status == ringo.RINGO_EINVAL
     g.free()
+
+
+def test_same_bits_on_every_run():
+    # each node's sum is formed in a fixed order: two runs agree bit for bit,
+    # also with a hub node split into chunks
+    n = 40_000
+    s = np.concatenate([np.arange(n, dtype=np.int32) + 100,
+                        np.random.default_rng(1).integers(0, 5000, 200_000).astype(np.int32)])
+    d = np.concatenate([np.full(n, 7, np.int32),
+                        np.random.default_rng(2).integers(0, 5000, 200_000).astype(np.int32)])
+    g = ringo.ringo_table_to_graph(torch.as_tensor(s).cuda(), torch.as_tensor(d).cuda())
+    a = g.pagerank(0.85, 10).clone()
+    b = g.pagerank(0.85, 10)
+    assert torch.equal(a, b)
+    g.free()
