@@ -220,6 +220,29 @@ RINGO_API int ringo_graph_to_node_table(const ringo_graph* g, int32_t* d_ids, in
 RINGO_API int ringo_graph_pagerank(const ringo_graph* g, double damping, int32_t iterations,
                                    double* d_rank, void* stream);
 
+/*
+ * ringo_table_to_undirected_graph -- the undirected graph of an edge table,
+ * for the paper's undirected workload (Section 4, triangle counting): each
+ * row (s, d) is the edge {s, d}; every distinct pair is one edge; a node's
+ * list holds each neighbour once, sorted (node indices); a self-loop puts the
+ * node once in its own list.  Both CSR directions hold the same symmetric
+ * lists (num_edges counts each non-loop edge twice, once per endpoint).  The
+ * table with each row also reversed goes through ringo_table_to_graph's
+ * conversion, so nrows is at most 2^30 - 1 (ERANGE above).  Arguments and
+ * other errors as ringo_table_to_graph.
+ */
+RINGO_API int ringo_table_to_undirected_graph(const int32_t* src, const int32_t* dst,
+                                              int64_t nrows, void* stream, ringo_graph** out);
+/*
+ * ringo_graph_count_triangles -- the number of triangles (three distinct
+ * nodes, each pair joined) of the undirected graph held in g's out-CSR, which
+ * must be symmetric (as built by ringo_table_to_undirected_graph); self-loops
+ * are ignored.  Exact (64-bit integer).  Scratch of about 16 V + 2 E bytes
+ * from the library's pool; blocks until *count is on the host.
+ * Errors: EINVAL (NULL g or count), ENOMEM, ECUDA.
+ */
+RINGO_API int ringo_graph_count_triangles(const ringo_graph* g, void* stream, uint64_t* count);
+
 /* ------------------------------------------------------------------------
  * Base tables, selection and batched conversion.
  *

@@ -78,6 +78,9 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
             lib.oracle_graph_to_edge_table.argtypes = [
                 ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                 ctypes.c_void_p, ctypes.c_void_p]
+            lib.oracle_count_triangles.restype = ctypes.c_int
+            lib.oracle_count_triangles.argtypes = [ctypes.c_int64, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_void_p]
             lib.oracle_count_distinct.restype = ctypes.c_int
             lib.oracle_count_distinct.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                                   ctypes.c_void_p, ctypes.c_void_p]
@@ -223,3 +226,24 @@ def pagerank(g: dict, damping: float = 0.85, iterations: int = 10, drop_dangling
         incoming = np.bincount(row_of_edge, weights=contrib[in_nbr], minlength=V)
         pr = (1.0 - damping) / V + damping * (incoming + dangling / V)
     return pr
+
+
+def undirected_graph(src, dst) -> dict:
+    """The undirected graph of an edge table (the paper's undirected workload,
+    Section 4): every row (s, d) is the edge {s, d}, i.e. the directed graph
+    of the table with each row also reversed; both CSR directions then hold
+    the same symmetric neighbour lists."""
+    s, d = _i32(src), _i32(dst)
+    return table_to_graph(np.concatenate([s, d]), np.concatenate([d, s]))
+
+
+def count_triangles(g: dict, mutant: int = 0) -> int:
+    """Triangles of the undirected graph in g's (symmetric) out-CSR."""
+    off = np.ascontiguousarray(g["out_off"], np.int64)
+    nbr = _i32(g["out_nbr"])
+    c = np.zeros(1, np.uint64)
+    rc = _lib(mutant).oracle_count_triangles(int(g["num_nodes"]), off.ctypes.data, nbr.ctypes.data,
+                                             c.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("oracle_count_triangles failed")
+    return int(c[0])

@@ -255,4 +255,26 @@ int oracle_graph_to_edge_table(int64_t num_nodes, const int32_t* node_ids, const
   return 0;
 }
 
+// Triangles of an undirected graph given by a symmetric CSR (sorted lists of
+// node indices): unordered triples {u, v, w} of distinct nodes with all three
+// edges, each counted once as u < v < w: for every u, every neighbour v > u,
+// every neighbour w > v of u that is also a neighbour of v.
+int oracle_count_triangles(int64_t num_nodes, const int64_t* off, const int32_t* nbr,
+                           uint64_t* count) {
+  uint64_t c = 0;
+  for (int64_t u = 0; u < num_nodes; ++u) {
+    for (int64_t i = off[u]; i < off[u + 1]; ++i) {
+      const int64_t v = nbr[i];
+      if (v <= u) continue;
+      for (int64_t j = off[u]; j < off[u + 1]; ++j) {
+        const int64_t w = nbr[j];
+        if (MUTANT(9) ? (w == v || w <= u) : (w <= v)) continue;  // mutant: each triangle twice
+        if (std::binary_search(nbr + off[v], nbr + off[v + 1], (int32_t)w)) ++c;
+      }
+    }
+  }
+  *count = c;
+  return 0;
+}
+
 }  // extern "C"

@@ -325,6 +325,55 @@ int ringo_table_to_graph_host(const int32_t* h_src, const int32_t* h_dst, int64_
   return table_to_graph_impl(h_src, h_dst, nrows, stream, out, true);
 }
 
+int ringo_table_to_undirected_graph(const int32_t* src, const int32_t* dst, int64_t nrows,
+                                    void* stream, ringo_graph** out) {
+  if (!out) return RINGO_EINVAL;
+  *out = nullptr;
+  if (nrows < 0 || (nrows > 0 && (!src || !dst))) {
+    set_error("nrows < 0 or NULL column");
+    return RINGO_EINVAL;
+  }
+  if (nrows > 0x3FFFFFFF) {
+    set_error("nrows exceeds 2^30 - 1 (the doubled table must fit 2^31 - 1 rows)");
+    return RINGO_ERANGE;
+  }
+  ringo_graph* g = new (std::nothrow) ringo_graph();
+  if (!g) return RINGO_ENOMEM;
+  g->stream = (cudaStream_t)stream;
+  cudaGetDevice(&g->device);
+  int rc;
+  if (nrows == 0) {
+    rc = make_empty(g);
+  } else {
+    const uint32_t n = (uint32_t)nrows;
+    const size_t bytes = sizeof(int32_t) * 2 * (size_t)n;
+    int32_t* s2 = (int32_t*)pool_alloc(bytes, g->stream);
+    int32_t* d2 = (int32_t*)pool_alloc(bytes, g->stream);
+    if (!s2 || !d2) {
+      rc = RINGO_ENOMEM;
+    } else {
+      rc = launch_double_table(src, dst, n, s2, d2, g->stream);
+      if (rc == RINGO_OK) rc = convert(s2, d2, 2 * n, g);
+    }
+    pool_free(s2, g->stream);
+    pool_free(d2, g->stream);
+  }
+  if (rc != RINGO_OK) {
+    free_graph_arrays(g);
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return RINGO_OK;
+}
+
+int ringo_graph_count_triangles(const ringo_graph* g, void* stream, uint64_t* count) {
+  if (!g || !count) return RINGO_EINVAL;
+  cudaStream_t s = stream ? (cudaStream_t)stream : g->stream;
+  return run_triangles(g->out_off, g->out_nbr, (uint32_t)g->info.num_nodes,
+                       (uint64_t)g->info.num_edges, s, count);
+}
+
 int ringo_graph_num_nodes(const ringo_graph* g, int64_t* v) {
   if (!g || !v) return RINGO_EINVAL;
   *v = g->info.num_nodes;

@@ -212,6 +212,11 @@ int launch_edge_table(const int32_t* node_ids, const int64_t* off, const int32_t
                       uint64_t E, int32_t* key, int32_t* val, cudaStream_t s);
 int launch_node_table(const int32_t* node_ids, const int64_t* out_off, const int64_t* in_off,
                       uint32_t V, int32_t* ids, int64_t* outdeg, int64_t* indeg, cudaStream_t s);
+// undirected conversion and triangles (undirected.cu); ringo statuses
+int launch_double_table(const int32_t* src, const int32_t* dst, uint32_t n, int32_t* s2, int32_t* d2,
+                        cudaStream_t s);
+int run_triangles(const int64_t* off, const int32_t* nbr, uint32_t V, uint64_t E, cudaStream_t s,
+                  uint64_t* count);
 // PageRank (pagerank.cu); returns a ringo status
 int run_pagerank(const int64_t* out_off, const int64_t* in_off, const int32_t* in_nbr, uint32_t V,
                  uint64_t E, double damping, int32_t iterations, double* rank, cudaStream_t s);

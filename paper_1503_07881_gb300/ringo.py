@@ -98,6 +98,8 @@ SIGNATURES = {
     "ringo_batch_graph_to_edge_table": (ctypes.c_int, [_P, _I32, ctypes.c_int, _P, _P, _I64, _P,
                                                        _P]),
     "ringo_graph_pagerank": (ctypes.c_int, [_P, ctypes.c_double, _I32, _P, _P]),
+    "ringo_table_to_undirected_graph": (ctypes.c_int, [_P, _P, _I64, _P, _PP]),
+    "ringo_graph_count_triangles": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "ringo_profile_start": (ctypes.c_int, []),
     "ringo_profile_stop": (ctypes.c_int, [ctypes.POINTER(KernelStat), _I32, _P]),
 }
@@ -260,6 +262,14 @@ class Graph:
                "ringo_graph_pagerank")
         return out[:V]
 
+    def count_triangles(self, stream=None) -> int:
+        """Triangles of the undirected graph in the out-CSR (see
+        ringo_table_to_undirected_graph)."""
+        c = ctypes.c_uint64()
+        _check(load().ringo_graph_count_triangles(self.handle, _stream_ptr(stream), ctypes.byref(c)),
+               "ringo_graph_count_triangles")
+        return c.value
+
     def to_node_table(self, stream=None) -> tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
         """(node IDs ascending, out-degree, in-degree) as CUDA tensors."""
         V = self.num_nodes
@@ -314,6 +324,21 @@ def ringo_table_to_graph(src: torch.Tensor, dst: torch.Tensor, stream=None) -> G
     _check(lib.ringo_table_to_graph(_col_ptr(src, "src") if src.numel() else None,
                                     _col_ptr(dst, "dst") if dst.numel() else None,
                                     src.numel(), sp, ctypes.byref(h)), "ringo_table_to_graph")
+    return Graph(h.value, sp)
+
+
+def ringo_table_to_undirected_graph(src: torch.Tensor, dst: torch.Tensor, stream=None) -> Graph:
+    """Undirected graph of device columns: each row is the edge {src, dst}."""
+    if src.numel() != dst.numel():
+        raise ValueError("src and dst differ in length")
+    if src.numel() and (not src.is_cuda or not dst.is_cuda):
+        raise ValueError("columns must be CUDA tensors")
+    sp = _stream_ptr(stream)
+    h = ctypes.c_void_p()
+    _check(load().ringo_table_to_undirected_graph(_col_ptr(src, "src") if src.numel() else None,
+                                                  _col_ptr(dst, "dst") if dst.numel() else None,
+                                                  src.numel(), sp, ctypes.byref(h)),
+           "ringo_table_to_undirected_graph")
     return Graph(h.value, sp)
 
 

@@ -53,3 +53,11 @@ def test_argument_validation_before_any_device_work():
     v = ctypes.c_int64()
     assert lib.ringo_graph_num_nodes(None, ctypes.byref(v)) == ringo.RINGO_EINVAL
     lib.ringo_graph_free(None)  # no-op
+
+
+def test_undirected_row_limit_checked_before_any_device_work():
+    lib = ringo.load()
+    fake = ctypes.c_void_p(4096)  # never dereferenced: the size check comes first
+    h = ctypes.c_void_p()
+    rc = lib.ringo_table_to_undirected_graph(fake, fake, 1 << 30, None, ctypes.byref(h))
+    assert rc == ringo.RINGO_ERANGE and not h.value

@@ -202,3 +202,70 @@ def test_pagerank_pins_catch_dropped_dangling_mass():
     bad = oracle.pagerank(g, drop_dangling=True)
     assert abs(bad.sum() - 1.0) > 1e-3
     assert not np.allclose(bad, dense_pagerank([1, 1, 3], [2, 3, 1]), rtol=1e-6)
+
+
+# ------------------------------------------------- undirected + triangles ---
+def dense_triangles(src, dst) -> int:
+    """trace(A^3) / 6 with the symmetric 0/1 adjacency matrix of the distinct
+    unordered pairs, loops removed: a route independent of the CSR."""
+    ids = sorted(set(int(x) for x in src) | set(int(x) for x in dst))
+    idx = {x: i for i, x in enumerate(ids)}
+    A = np.zeros((len(ids), len(ids)), dtype=np.int64)
+    for a, b in zip(src, dst):
+        if a != b:
+            A[idx[int(a)], idx[int(b)]] = A[idx[int(b)], idx[int(a)]] = 1
+    return int(np.trace(A @ A @ A)) // 6
+
+
+def test_undirected_graph_is_symmetric_set_of_pairs():
+    rng = np.random.default_rng(12)
+    for n in (0, 1, 5, 60):
+        s = rng.integers(-6, 6, n).astype(np.int32)
+        d = rng.integers(-6, 6, n).astype(np.int32)
+        g = oracle.undirected_graph(s, d)
+        ids = g["node_ids"]
+        adj = {int(ids[r]): set(int(ids[k]) for k in g["out_nbr"][g["out_off"][r]:g["out_off"][r + 1]])
+               for r in range(g["num_nodes"])}
+        want = {}
+        for a, b in zip(s.tolist(), d.tolist()):
+            want.setdefault(a, set()).add(b)
+            want.setdefault(b, set()).add(a)
+        assert adj == want
+        for d_ in ("off", "nbr"):
+            assert np.array_equal(g[f"out_{d_}"], g[f"in_{d_}"])
+
+
+def test_triangles_match_dense_count():
+    rng = np.random.default_rng(13)
+    for n in (0, 3, 20, 120, 400):
+        for _ in range(4):
+            s = rng.integers(0, 25, n).astype(np.int32)
+            d = rng.integers(0, 25, n).astype(np.int32)
+            assert oracle.count_triangles(oracle.undirected_graph(s, d)) == dense_triangles(s, d)
+
+
+def test_triangles_closed_forms():
+    import itertools
+    from math import comb
+    for n in (3, 4, 7, 12):  # complete graph
+        p = list(itertools.combinations(range(n), 2))
+        g = oracle.undirected_graph([a for a, _ in p], [b for _, b in p])
+        assert oracle.count_triangles(g) == comb(n, 3)
+    for n in (3, 4, 9):  # cycle
+        v = np.arange(n, dtype=np.int32)
+        assert oracle.count_triangles(oracle.undirected_graph(v, (v + 1) % n)) == (1 if n == 3 else 0)
+    for n in (4, 8):  # wheel: a hub joined to every node of an n-cycle
+        v = np.arange(n, dtype=np.int32)
+        s = np.concatenate([v, np.full(n, 100, np.int32)])
+        d = np.concatenate([(v + 1) % n, v])
+        assert oracle.count_triangles(oracle.undirected_graph(s, d)) == n
+    # loops, duplicates and reversed rows change nothing
+    s = np.array([1, 2, 3, 1, 2, 3, 3, 2], np.int32)
+    d = np.array([2, 3, 1, 1, 1, 3, 2, 2], np.int32)
+    assert oracle.count_triangles(oracle.undirected_graph(s, d)) == 1
+
+
+def test_triangle_pins_catch_planted_mistake():
+    p = [(0, 1), (1, 2), (0, 2), (2, 3)]
+    g = oracle.undirected_graph([a for a, _ in p], [b for _, b in p])
+    assert oracle.count_triangles(g, mutant=9) != dense_triangles([a for a, _ in p], [b for _, b in p])
