@@ -254,8 +254,9 @@ def run_ours(args, world, rank, local):
     model_frac = model_bytes / (ms / 1e3) / 1e9 / peak
 
     # graph -> table (Section 3.4) and PageRank (Table "paralg") on the same graph
-    to_table = pagerank = triangles = None
+    to_table = pagerank = triangles = table_ops = None
     if not args.no_to_table:
+        table_ops = run_select_join(args, src, dst, stream)
         to_table, pagerank = run_graph_ops(args, src, dst, stream, peak, peak_kind)
         if world == 1:
             triangles = run_triangles(args, stream)
@@ -347,6 +348,7 @@ def run_ours(args, world, rank, local):
         "graph_to_table": to_table,
         "pagerank": pagerank,
         "triangles": triangles,
+        "select_join": table_ops,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -471,6 +473,80 @@ def run_triangles(args, stream) -> dict:
             "undirected_conversion_ms": round(conv_ms, 3), "count_ms": round(count_ms, 3),
             "paper_s": PAPER_TRIANGLES_S["lj"], "vs_paper": PAPER_TRIANGLES_S["lj"] * 1e3 / count_ms,
             "twitter": "not run: the doubled Twitter-shaped table exceeds 2^31 - 1 rows"}
+
+
+PAPER_TABLE_OPS_S = {"twitter": {"select_10k": 1.6, "select_all_but_10k": 1.6, "join_10k": 4.2,
+                                   "join_all_but_10k": 29.7},
+                     "lj": {"select_10k": 0.2, "select_all_but_10k": 0.1, "join_10k": 0.6,
+                            "join_all_but_10k": 3.1}}  # Table "table_ringo"
+
+
+def run_select_join(args, src, dst, stream) -> dict:
+    """Section 4's table benchmark on the workload's edge table: select by
+    comparison with a constant keeping 10K rows or all but 10K (in place), and
+    join on src with a single-column table chosen so the output is about 10K
+    rows or all but about 10K."""
+    from paper_1503_07881_gb300 import ringo
+    N = src.numel()
+    k = 10_000
+    srt = torch.sort(src).values
+    lo_val = int(srt[k].item())  # src < lo_val keeps the k smallest rows (ties aside),
+    #                              src >= lo_val all the others
+    del srt
+    # join keys: source IDs of a random node subset whose rows total about k
+    ids, counts = torch.unique(src, return_counts=True)
+    perm = torch.randperm(ids.numel(), device=ids.device, generator=torch.Generator(device=ids.device).manual_seed(5))
+    csum = torch.cumsum(counts[perm], 0)
+    take = int(torch.searchsorted(csum, torch.tensor(k, device=csum.device)).item()) + 1
+    keys_small = ids[perm[:take]].contiguous()
+    keys_large = ids[perm[take:]].contiguous()
+    del ids, counts, perm, csum
+    ws, wd = torch.empty_like(src), torch.empty_like(dst)
+    out = {}
+
+    def timed(fn, runs=3):
+        ms = []
+        for r in range(runs + 1):
+            ws.copy_(src)
+            wd.copy_(dst)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            if r:
+                ms.append(a.elapsed_time(b))
+        return res, statistics.median(ms)
+
+    paper = PAPER_TABLE_OPS_S.get(args.workload, {})
+    n1, ms1 = timed(lambda: ringo.ringo_table_select(ws, wd, 0, "<", lo_val))
+    n2, ms2 = timed(lambda: ringo.ringo_table_select(ws, wd, 0, ">=", lo_val))
+    cap = N
+    js, jd = torch.empty_like(src), torch.empty_like(dst)
+
+    def join(keys):
+        import ctypes
+        n = ctypes.c_int64()
+        rc = ringo.load().ringo_table_join(src.data_ptr(), dst.data_ptr(), N, 0, keys.data_ptr(),
+                                           keys.numel(), js.data_ptr(), jd.data_ptr(), cap,
+                                           ctypes.byref(n), torch.cuda.current_stream().cuda_stream)
+        assert rc == 0, rc
+        return n.value
+
+    n3, ms3 = timed(lambda: join(keys_small))
+    n4, ms4 = timed(lambda: join(keys_large))
+    for name, rows, ms, in_rows in (("select_10k", n1, ms1, N), ("select_all_but_10k", n2, ms2, N),
+                                    ("join_10k", n3, ms3, N + keys_small.numel()),
+                                    ("join_all_but_10k", n4, ms4, N + keys_large.numel())):
+        p = paper.get(name)
+        out[name] = {"ms": round(ms, 3), "output_rows": rows, "rows_per_s": in_rows / (ms / 1e3),
+                     "paper_s": p, "vs_paper": (p * 1e3 / ms) if p else None}
+    del ws, wd, js, jd
+    torch.cuda.empty_cache()
+    out["note"] = ("median of 3 runs; select runs in place on a fresh copy each time; join rows/s "
+                   "counts both input tables, as the paper does")
+    return out
 
 
 def run_to_table(args, g, stream, peak, peak_kind) -> dict:

@@ -244,6 +244,40 @@ RINGO_API int ringo_table_to_undirected_graph(const int32_t* src, const int32_t*
 RINGO_API int ringo_graph_count_triangles(const ringo_graph* g, void* stream, uint64_t* count);
 
 /* ------------------------------------------------------------------------
+ * Select and join on edge tables: the relational operations that build the
+ * edge table before conversion (Section 3.3, "Tables in Ringo"; Section 4,
+ * Table "table_ringo").  Both keep row order and are enqueued on `stream`;
+ * they block until the output row count is on the host.
+ * ---------------------------------------------------------------------- */
+typedef enum {
+  RINGO_CMP_LT = 0, RINGO_CMP_LE = 1, RINGO_CMP_EQ = 2,
+  RINGO_CMP_NE = 3, RINGO_CMP_GE = 4, RINGO_CMP_GT = 5
+} ringo_cmp;
+
+/*
+ * ringo_table_select -- select in place: keeps the rows of the edge table
+ * (device columns src, dst of nrows entries, caller-owned) whose column
+ * `col` (0: src, 1: dst) compares with `value` by `op`, in their order, in
+ * the first *n_out rows of both columns (the rest is left unspecified).
+ * Errors: EINVAL (NULL n_out, NULL column with nrows > 0, nrows < 0, bad col
+ * or op), ERANGE (nrows >= 2^31), ENOMEM, ETIMEOUT, ECUDA.
+ */
+RINGO_API int ringo_table_select(int32_t* src, int32_t* dst, int64_t nrows, int col, int op,
+                                 int32_t value, int64_t* n_out, void* stream);
+/*
+ * ringo_table_join -- equi-join of the edge table with a single-column table
+ * keys[nkeys] (device) on column `col`: every row whose key occurs in keys,
+ * once per occurrence, in row order, written to caller-owned device columns
+ * out_src[cap], out_dst[cap].  *n_out receives the join's row count; if it
+ * exceeds cap (or 2^31 - 1) nothing is written and ERANGE is returned.
+ * Errors: EINVAL (bad pointers, sizes or col), ERANGE (nrows >= 2^31,
+ * nkeys >= 2^30, output above cap), ENOMEM, ETIMEOUT, ECUDA.
+ */
+RINGO_API int ringo_table_join(const int32_t* src, const int32_t* dst, int64_t nrows, int col,
+                               const int32_t* keys, int64_t nkeys, int32_t* out_src,
+                               int32_t* out_dst, int64_t cap, int64_t* n_out, void* stream);
+
+/* ------------------------------------------------------------------------
  * Base tables, selection and batched conversion.
  *
  * The paper builds graphs from tables after relational operations such as

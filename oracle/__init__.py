@@ -247,3 +247,30 @@ def count_triangles(g: dict, mutant: int = 0) -> int:
     if rc != 0:
         raise RuntimeError("oracle_count_triangles failed")
     return int(c[0])
+
+
+_OPS = {"<": np.less, "<=": np.less_equal, "==": np.equal, "!=": np.not_equal,
+        ">=": np.greater_equal, ">": np.greater}
+
+
+def table_select(src, dst, col: int, op: str, value: int) -> tuple[np.ndarray, np.ndarray]:
+    """Select (Section 3.3; Section 4's select benchmark compares a column with
+    a constant): the rows whose column `col` (0: src, 1: dst) compares with
+    `value` by `op`, in their order."""
+    s, d = _i32(src), _i32(dst)
+    keep = _OPS[op](d if col else s, np.int32(value))
+    return s[keep], d[keep]
+
+
+def table_join(src, dst, col: int, keys) -> tuple[np.ndarray, np.ndarray]:
+    """Equi-join with a single-column table (Section 4's join benchmark): every
+    row whose column `col` value occurs in `keys`, once per occurrence, in row
+    order."""
+    s, d = _i32(src), _i32(dst)
+    key = d if col else s
+    uk, cnt = np.unique(_i32(keys), return_counts=True)
+    if uk.size == 0 or key.size == 0:
+        return s[:0].copy(), d[:0].copy()
+    pos = np.minimum(np.searchsorted(uk, key), uk.size - 1)
+    mult = np.where(uk[pos] == key, cnt[pos], 0)
+    return np.repeat(s, mult), np.repeat(d, mult)

@@ -100,6 +100,9 @@ SIGNATURES = {
     "ringo_graph_pagerank": (ctypes.c_int, [_P, ctypes.c_double, _I32, _P, _P]),
     "ringo_table_to_undirected_graph": (ctypes.c_int, [_P, _P, _I64, _P, _PP]),
     "ringo_graph_count_triangles": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "ringo_table_select": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int, ctypes.c_int, _I32, _P, _P]),
+    "ringo_table_join": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I64, _P, _P, _I64, _P,
+                                        _P]),
     "ringo_profile_start": (ctypes.c_int, []),
     "ringo_profile_stop": (ctypes.c_int, [ctypes.POINTER(KernelStat), _I32, _P]),
 }
@@ -653,3 +656,46 @@ class Server:
         st = ServerStats()
         _check(load().ringo_server_get_stats(self._h, ctypes.byref(st)), "ringo_server_get_stats")
         return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+
+# ---------------------------------------------------------- select / join --
+RINGO_CMP_LT, RINGO_CMP_LE, RINGO_CMP_EQ, RINGO_CMP_NE, RINGO_CMP_GE, RINGO_CMP_GT = range(6)
+_CMP = {"<": RINGO_CMP_LT, "<=": RINGO_CMP_LE, "==": RINGO_CMP_EQ, "!=": RINGO_CMP_NE,
+        ">=": RINGO_CMP_GE, ">": RINGO_CMP_GT}
+
+
+def ringo_table_select(src: torch.Tensor, dst: torch.Tensor, col: int, op: str, value: int,
+                       stream=None) -> int:
+    """Select in place on device columns; returns the number of rows kept
+    (the first n rows of src and dst)."""
+    n = ctypes.c_int64()
+    _check(load().ringo_table_select(_col_ptr(src, "src") if src.numel() else None,
+                                     _col_ptr(dst, "dst") if dst.numel() else None, src.numel(),
+                                     int(col), _CMP[op], int(value), ctypes.byref(n),
+                                     _stream_ptr(stream)), "ringo_table_select")
+    return n.value
+
+
+def ringo_table_join(src: torch.Tensor, dst: torch.Tensor, col: int, keys: torch.Tensor,
+                     cap: int | None = None, stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+    """Join on column col with a single-column table of keys (device int32);
+    returns the output columns."""
+    if cap is None:
+        cap = src.numel() * max(1, keys.numel())
+        cap = min(cap, 2**31 - 1)
+    # size first with a zero-capacity call, then write
+    n = ctypes.c_int64()
+    lib = load()
+    sp = _stream_ptr(stream)
+    args = (_col_ptr(src, "src") if src.numel() else None, _col_ptr(dst, "dst") if dst.numel() else None,
+            src.numel(), int(col), _col_ptr(keys, "keys") if keys.numel() else None, keys.numel())
+    rc = lib.ringo_table_join(*args, None, None, 0, ctypes.byref(n), sp)
+    if rc not in (RINGO_OK, RINGO_ERANGE):
+        _check(rc, "ringo_table_join")
+    rows = n.value
+    out_s = torch.empty(max(rows, 1), dtype=torch.int32, device="cuda")
+    out_d = torch.empty(max(rows, 1), dtype=torch.int32, device="cuda")
+    if rows:
+        _check(lib.ringo_table_join(*args, out_s.data_ptr(), out_d.data_ptr(), rows,
+                                    ctypes.byref(n), sp), "ringo_table_join")
+    return out_s[:rows], out_d[:rows]

@@ -269,3 +269,43 @@ def test_triangle_pins_catch_planted_mistake():
     p = [(0, 1), (1, 2), (0, 2), (2, 3)]
     g = oracle.undirected_graph([a for a, _ in p], [b for _, b in p])
     assert oracle.count_triangles(g, mutant=9) != dense_triangles([a for a, _ in p], [b for _, b in p])
+
+
+# ----------------------------------------------------------- select / join ---
+def test_select_is_the_ordered_filter():
+    import operator
+    ops = {"<": operator.lt, "<=": operator.le, "==": operator.eq, "!=": operator.ne,
+           ">=": operator.ge, ">": operator.gt}
+    rng = np.random.default_rng(14)
+    for n in (0, 1, 7, 300):
+        s = rng.integers(-5, 5, n).astype(np.int32)
+        d = rng.integers(-5, 5, n).astype(np.int32)
+        for col in (0, 1):
+            for op, fn in ops.items():
+                for v in (-6, -1, 0, 3, 6):
+                    got = oracle.table_select(s, d, col, op, v)
+                    want = [(a, b) for a, b in zip(s.tolist(), d.tolist()) if fn((b if col else a), v)]
+                    assert list(zip(got[0].tolist(), got[1].tolist())) == want
+        # complementary comparisons split the table
+        for v in (-2, 0, 4):
+            assert oracle.table_select(s, d, 0, "<", v)[0].size + \
+                oracle.table_select(s, d, 0, ">=", v)[0].size == n
+
+
+def test_join_is_the_nested_loop():
+    rng = np.random.default_rng(15)
+    for n in (0, 1, 9, 200):
+        s = rng.integers(-4, 4, n).astype(np.int32)
+        d = rng.integers(-4, 4, n).astype(np.int32)
+        for nk in (0, 1, 5, 30):
+            keys = rng.integers(-5, 5, nk).astype(np.int32)
+            for col in (0, 1):
+                got = oracle.table_join(s, d, col, keys)
+                want = [(a, b) for a, b in zip(s.tolist(), d.tolist())
+                        for k in keys.tolist() if (b if col else a) == k]
+                assert list(zip(got[0].tolist(), got[1].tolist())) == want
+    # every key once: the join keeps the whole table
+    s = rng.integers(0, 50, 400).astype(np.int32)
+    d = rng.integers(0, 50, 400).astype(np.int32)
+    out = oracle.table_join(s, d, 0, np.unique(s))
+    assert np.array_equal(out[0], s) and np.array_equal(out[1], d)
