@@ -5,9 +5,9 @@
 // is built by splitting the graph's nodes or edges among workers, each
 // writing its part of a pre-allocated output.  Here the output columns are
 // pre-allocated by the caller and every edge is one work item: a 2048-edge
-// tile finds the source nodes it spans with one binary search over the
-// offsets, stages their offsets in shared memory, and each edge finds its
-// source there; rows are written coalesced, in CSR order.
+// tile finds the nodes it spans with one binary search per end, marks where
+// each of them starts inside the tile, and a max-scan gives every edge its
+// row node; rows are written coalesced, in CSR order.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,7 +20,7 @@ namespace ringo {
 namespace {
 
 constexpr uint32_t kExpandTile = 2048;   // edges per tile
-constexpr uint32_t kExpandWindow = 2048; // node offsets staged per tile
+constexpr uint32_t kExpandWindow = 2048; // most nodes a tile resolves by the max-scan
 
 // largest r in [0, V) with off[r] <= e (off[0] = 0 <= e < off[V] = E)
 __device__ __forceinline__ uint32_t owner(const int64_t* __restrict__ off, uint32_t V, uint64_t e) {
@@ -35,42 +35,75 @@ __device__ __forceinline__ uint32_t owner(const int64_t* __restrict__ off, uint3
 
 // Rows e of the edge table, in CSR order: key[e] = node_ids[row node],
 // val[e] = node_ids[nbr[e]].  For the out-CSR that is (src, dst); for the
-// in-CSR the caller swaps the columns.
+// in-CSR the caller swaps the columns.  Each node whose edges start inside
+// the tile marks its start position with its index (the largest index wins,
+// so a node with no edges yields to the next one starting at the same
+// place), and an inclusive max-scan over the tile gives every edge its row
+// node.
 __global__ void __launch_bounds__(256)
     k_expand(const int32_t* __restrict__ node_ids, const int64_t* __restrict__ off,
              const int32_t* __restrict__ nbr, uint32_t V, uint64_t E, int32_t* __restrict__ key,
              int32_t* __restrict__ val) {
-  __shared__ int64_t s_off[kExpandWindow + 1];
+  constexpr uint32_t kPer = kExpandTile / 256;  // positions per thread in the scan
+  __shared__ int32_t s_own[kExpandTile];
+  __shared__ int32_t s_w[8];
   __shared__ uint32_t s_r0, s_r1;
   for (uint64_t e0 = (uint64_t)blockIdx.x * kExpandTile; e0 < E;
        e0 += (uint64_t)gridDim.x * kExpandTile) {
     const uint64_t e1 = min(e0 + kExpandTile, E);
+    const uint32_t len = (uint32_t)(e1 - e0);
     __syncthreads();
     if (threadIdx.x == 0) s_r0 = owner(off, V, e0);
     if (threadIdx.x == 32) s_r1 = owner(off, V, e1 - 1);
+    for (uint32_t t = threadIdx.x; t < kExpandTile; t += blockDim.x) s_own[t] = 0;
     __syncthreads();
     const uint32_t r0 = s_r0, r1 = s_r1;
-    const uint32_t w = r1 - r0 + 1;  // nodes spanned by the tile
-    const bool staged = w <= kExpandWindow;
-    if (staged)
-      for (uint32_t t = threadIdx.x; t <= w; t += blockDim.x) s_off[t] = off[r0 + t];
-    __syncthreads();
-    for (uint64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      uint32_t r;
-      if (staged) {  // largest t in [0, w) with s_off[t] <= e
-        uint32_t lo = 0, hi = w;
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if ((uint64_t)s_off[mid] <= e) lo = mid;
-          else hi = mid;
-        }
-        r = r0 + lo;
-      } else {
-        r = owner(off, V, e);
+    if (r1 - r0 + 1 <= kExpandWindow) {
+      // nodes r0+1 .. r1 start inside the tile
+      for (uint32_t r = r0 + 1 + threadIdx.x; r <= r1; r += blockDim.x) {
+        const uint64_t p = (uint64_t)off[r] - e0;
+        if (p < len) atomicMax(&s_own[p], (int32_t)(r - r0));
       }
-      const int32_t m = __ldcs(nbr + e);
-      key[e] = node_ids[r];
-      val[e] = (uint32_t)m < V ? __ldg(node_ids + m) : 0;
+      __syncthreads();
+      // inclusive max-scan of s_own (each thread 8 consecutive positions)
+      const uint32_t base = threadIdx.x * kPer;
+      int32_t run = 0;
+#pragma unroll
+      for (uint32_t q = 0; q < kPer; ++q) run = max(run, s_own[base + q]);
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      int32_t incl = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl = max(incl, y);
+      }
+      if (lane == 31) s_w[warp] = incl;
+      __syncthreads();
+      int32_t carry = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+      if (lane == 0) carry = 0;
+      for (int k = 0; k < warp; ++k) carry = max(carry, s_w[k]);
+      __syncthreads();  // every thread has its carry before the positions are overwritten
+      int32_t m = carry;
+#pragma unroll
+      for (uint32_t q = 0; q < kPer; ++q) {
+        m = max(m, s_own[base + q]);
+        s_own[base + q] = m;
+      }
+      __syncthreads();
+      for (uint32_t t = threadIdx.x; t < len; t += blockDim.x) {
+        const uint64_t e = e0 + t;
+        const uint32_t r = r0 + (uint32_t)s_own[t];
+        const int32_t mm = __ldcs(nbr + e);
+        key[e] = node_ids[r];
+        val[e] = (uint32_t)mm < V ? __ldg(node_ids + mm) : 0;
+      }
+    } else {  // the tile spans more nodes than the window: search per edge
+      for (uint64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const uint32_t r = owner(off, V, e);
+        const int32_t mm = __ldcs(nbr + e);
+        key[e] = node_ids[r];
+        val[e] = (uint32_t)mm < V ? __ldg(node_ids + mm) : 0;
+      }
     }
   }
 }
