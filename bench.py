@@ -541,7 +541,7 @@ def run_select_join(args, src, dst, stream) -> dict:
                                     ("join_all_but_10k", n4, ms4, N + keys_large.numel())):
         p = paper.get(name)
         out[name] = {"ms": round(ms, 3), "output_rows": rows, "rows_per_s": in_rows / (ms / 1e3),
-                     "paper_s": p, "vs_paper": (p * 1e3 / ms) if p else None}
+                     "input_rows": in_rows, "paper_s": p, "vs_paper": (p * 1e3 / ms) if p else None}
     del ws, wd, js, jd
     torch.cuda.empty_cache()
     out["note"] = ("median of 3 runs; select runs in place on a fresh copy each time; join rows/s "
