@@ -767,11 +767,14 @@ def run_served(args, spec, base, rates, duration: float) -> dict:
         for p in warm:
             srv.wait(srv.submit(p, topk=SERVE_TOPK))
         srv.close()
-        server = serve_with_server(ringo, base, preds, arr, workers=2)
-        plain = serve_plain(ringo, base, preds, arr)
-        out.append({"rate_per_s": rate, "duration_s": duration, "requests": len(preds),
-                    "server": server, "plain_loop": plain,
-                    "p99_speedup_vs_plain": plain["p99_ms"] / server["p99_ms"]})
+        server = serve_with_server(ringo, base, preds, arr, workers=args.serve_workers)
+        row = {"rate_per_s": rate, "duration_s": duration, "requests": len(preds),
+               "workers": args.serve_workers, "server": server}
+        if not args.no_plain:
+            plain = serve_plain(ringo, base, preds, arr)
+            row["plain_loop"] = plain
+            row["p99_speedup_vs_plain"] = plain["p99_ms"] / server["p99_ms"]
+        out.append(row)
     return {"workload": WORKLOADS["served"], "budget_bytes": SERVE_BUDGET, "topk": SERVE_TOPK,
             "latency": "scheduled arrival to result ready (no coordinated omission)",
             "rates": out}
@@ -912,13 +915,14 @@ def main():
     ap.add_argument("--no-served", action="store_true", help="skip the served summary")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true",
-                    help="skip the plain per-table loop of the batched run (profiling)")
+                    help="skip the plain per-table / per-request loops (profiling, sweeps)")
     ap.add_argument("--base-scale", type=float, default=1.0,
                     help="scale of the base table and of the largest selection (profiling)")
     ap.add_argument("--predicates", type=int, default=BATCH_PREDS)
     ap.add_argument("--serve-rates", type=lambda x: [float(v) for v in x.split(",")],
                     default=[100.0, 500.0])
     ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-workers", type=int, default=1, help="server worker threads (streams)")
     args = ap.parse_args()
     if args.warmup < 3:
         log("note: fewer than 3 warm-up steps requested; using 3")

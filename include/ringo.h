@@ -405,7 +405,7 @@ typedef struct ringo_server ringo_server;
 typedef struct ringo_result ringo_result;
 
 typedef struct {
-  int32_t workers;         /* concurrent batches (threads and streams); 0: 2, at most 16 */
+  int32_t workers;         /* concurrent batches (threads and streams); 0: 1, at most 16 */
   int32_t max_batch;       /* requests per batch; 0: 1024 */
   int64_t max_batch_rows;  /* selected rows per batch (a larger single request
                               runs alone); 0: 2^28 */

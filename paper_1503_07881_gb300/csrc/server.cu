@@ -372,7 +372,7 @@ int ringo_server_create(const ringo_base* b, int64_t hbm_budget_bytes,
   ringo_server_config c{};
   if (cfg) c = *cfg;
   if (c.workers < 0 || c.max_batch < 0 || c.max_batch_rows < 0) return RINGO_EINVAL;
-  if (c.workers == 0) c.workers = 2;
+  if (c.workers == 0) c.workers = 1;
   if (c.max_batch == 0) c.max_batch = 1024;
   if (c.max_batch_rows == 0) c.max_batch_rows = 256ll << 20;
   if (c.workers > 16) return RINGO_ERANGE;
