@@ -118,6 +118,26 @@ __device__ __forceinline__ T warp_sum(T x) {
 // Exclusive sum over the block of one value per thread.  `sw` needs
 // THREADS/32 + 1 entries.  Ends with __syncthreads(); `sw` may be reused after
 // the caller's next barrier.
+// Largest r in [0, V) with off[r] <= e, for a non-decreasing off with
+// off[0] <= e < off[V], found by one warp (all lanes call it): each round
+// splits [lo, hi) into 32 parts and the lanes test the part starts together,
+// so the search takes log32(V) dependent loads instead of log2(V).
+__device__ __forceinline__ uint32_t warp_owner(const int64_t* __restrict__ off, uint32_t V, uint64_t e,
+                                               int lane) {
+  uint32_t lo = 0, hi = V;  // off[lo] <= e < off[hi]
+  while (hi - lo > 1) {
+    const uint32_t step = (hi - lo + 31) >> 5;
+    const uint32_t c = lo + (uint32_t)lane * step;
+    const bool le = lane > 0 && c < hi && (uint64_t)off[c] <= e;
+    // off is non-decreasing, so the lanes that pass are 1 .. k
+    const uint32_t k = __popc(__ballot_sync(0xFFFFFFFFu, le));
+    const uint32_t nhi = lo + (k + 1) * step;
+    lo += k * step;
+    hi = nhi < hi ? nhi : hi;
+  }
+  return lo;
+}
+
 template <int THREADS, typename T>
 __device__ __forceinline__ T block_exclusive_sum(T v, T* sw, T& total) {
   constexpr int NW = THREADS / 32;

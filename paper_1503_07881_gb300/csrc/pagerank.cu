@@ -6,16 +6,19 @@
 //                                + (sum of PR over nodes without out-edges) / V ).
 //
 // Each node's sum over its in-edges is formed in a fixed order, so the
-// result is the same on every run:
-//   light nodes (in-degree up to kBig): one warp per node, lanes striding over
-//          its in-edges (coalesced index loads, independent gathers), a
-//          fixed-order warp reduction, one plain store;
-//   heavy nodes: split into kBig-edge chunks, one block per chunk with a
-//          fixed-order block reduction, then the chunks of each node added in
-//          order;
+// result is the same on every run.  The in-edges are cut into 2048-edge
+// tiles (whatever the node boundaries):
+//   edges: a block gathers its tile's contributions into shared memory
+//          (coalesced index loads, independent gathers), finds each edge's
+//          node with a max-scan of node starts, and sums every node's run
+//          with a segmented scan over the threads' 8-edge runs; a node that
+//          lies inside the tile gets its sum written, a node cut by the tile
+//          edges leaves a partial sum in the tile's two slots;
+//   fix-up: one warp per node that ends in a tile it did not start in adds
+//          its partial sums in tile order;
 //   nodes: PR(v), the next contributions PR(v) / outdeg(v), and per-block
 //          sums of PR over nodes without out-edges, reduced in a fixed order.
-// The heavy-node list and its chunk offsets are built once per call.
+// The first and last node of every tile are found once per call.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,124 +33,193 @@ namespace ringo {
 
 namespace {
 
-constexpr uint32_t kBig = 8192;        // in-edges above which a node is split into chunks
+constexpr uint32_t kPrTile = 2048;      // in-edges per tile of the edge pass
+constexpr uint32_t kPrPer = kPrTile / 256;  // consecutive positions per thread
 constexpr uint32_t kNodeGrid = 1024;   // blocks of the node pass (fixed: partial sums)
 
 struct PrState {
   double dangling;  // sum of PR over nodes without out-edges, for this iteration
 };
 
-// Light nodes: one warp per node (grid-stride over warps).  sum[v] is
-// written for every node of in-degree at most kBig, 0 when it has none.
-__global__ void __launch_bounds__(256)
-    k_pr_light(const int64_t* __restrict__ in_off, const int32_t* __restrict__ in_nbr, uint32_t V,
-               const double* __restrict__ contrib, double* __restrict__ sum) {
+// shared-memory slot of tile position p: one pad slot after every 8, so each
+// thread's 8 consecutive positions fall in distinct banks across a warp
+__device__ __forceinline__ uint32_t pad8(uint32_t p) { return p + (p >> 3); }
+
+// tnode[2t], tnode[2t + 1]: the nodes owning the first and the last in-edge
+// of tile t.  One warp per tile.
+__global__ void k_pr_tile_nodes(const int64_t* __restrict__ in_off, uint32_t V, uint64_t E,
+                                uint32_t tiles, uint32_t* __restrict__ tnode) {
   const int lane = threadIdx.x & 31;
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t v = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < V;
-       v += warps) {
-    const int64_t a = in_off[v], b = in_off[v + 1];
-    if (b - a > (int64_t)kBig) continue;  // heavy: summed by chunks
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < tiles; t += warps) {
+    const uint64_t e0 = (uint64_t)t * kPrTile;
+    const uint64_t e1 = e0 + kPrTile < E ? e0 + kPrTile : E;
+    const uint32_t a = warp_owner(in_off, V, e0, lane);
+    const uint32_t b = warp_owner(in_off, V, e1 - 1, lane);
+    if (lane == 0) {
+      tnode[2 * t] = a;
+      tnode[2 * t + 1] = b;
+    }
+  }
+}
+
+// The run of one node at the end of a range of tile positions: the range's
+// first and last node (relative to the tile's first node) and the sum of the
+// positions that belong to its last node.  Keys do not decrease along the
+// tile, so the run of the concatenation AB is A's run plus B's when B holds
+// one node only and that node is A's last, else B's run.
+struct Run {
+  int32_t kf, kl;
+  double tail;
+};
+
+__device__ __forceinline__ Run run_cat(const Run& a, const Run& b) {
+  Run r;
+  r.kf = a.kf;
+  r.kl = b.kl;
+  r.tail = (b.kf == b.kl && a.kl == b.kf) ? a.tail + b.tail : b.tail;
+  return r;
+}
+
+// One block per tile of kPrTile in-edges.  sum[v] for every node whose
+// in-edges lie inside the tile; part[2t] = the tile's share of its first node
+// when that node starts in an earlier tile, part[2t + 1] = the share of its
+// last node when that node goes on past the tile.
+__global__ void __launch_bounds__(256)
+    k_pr_edges(const int64_t* __restrict__ in_off, const int32_t* __restrict__ in_nbr, uint32_t V,
+               uint64_t E, const uint32_t* __restrict__ tnode, const double* __restrict__ contrib,
+               double* __restrict__ sum, double* __restrict__ part) {
+  __shared__ double s_c[kPrTile + kPrTile / 8];
+  __shared__ int32_t s_own[kPrTile + kPrTile / 8];
+  __shared__ int32_t s_kf[256];
+  __shared__ int32_t s_wm[8];
+  __shared__ Run s_wr[8];
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t t = blockIdx.x;
+  const uint64_t e0 = (uint64_t)t * kPrTile;
+  const uint32_t len = (uint32_t)(E - e0 < kPrTile ? E - e0 : kPrTile);
+  const uint64_t e1 = e0 + len;
+  const uint32_t r0 = tnode[2 * t], r1 = tnode[2 * t + 1];
+  // contributions of the tile's edges (0 past its end), node-start marks cleared
+#pragma unroll
+  for (uint32_t q = 0; q < kPrPer; ++q) {
+    const uint32_t i = q * 256 + tid;
+    double c = 0.0;
+    if (i < len) {
+      const uint32_t u = (uint32_t)__ldcs(in_nbr + e0 + i);
+      c = u < V ? __ldg(contrib + u) : 0.0;
+    }
+    s_c[pad8(i)] = c;
+    s_own[pad8(i)] = 0;
+  }
+  __syncthreads();
+  // nodes r0+1 .. r1 start inside the tile; where several start at the same
+  // place (all but the last without in-edges) the last one wins
+  for (uint32_t r = r0 + 1 + tid; r <= r1; r += 256) {
+    const uint64_t p = (uint64_t)in_off[r] - e0;
+    if (p < len) atomicMax(&s_own[pad8((uint32_t)p)], (int32_t)(r - r0));
+  }
+  __syncthreads();
+  // inclusive max-scan of the marks: key[j] = node of position 8 tid + j
+  const uint32_t base = tid * kPrPer;
+  int32_t key[kPrPer];
+  int32_t mx = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kPrPer; ++j) {
+    key[j] = s_own[pad8(base + j)];
+    mx = max(mx, key[j]);
+  }
+  int32_t incl = mx;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if ((int)lane >= o) incl = max(incl, y);
+  }
+  if (lane == 31) s_wm[warp] = incl;
+  __syncthreads();
+  int32_t m = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+  if (lane == 0) m = 0;
+  for (uint32_t k = 0; k < warp; ++k) m = max(m, s_wm[k]);
+  double val[kPrPer];
+#pragma unroll
+  for (uint32_t j = 0; j < kPrPer; ++j) {
+    m = max(m, key[j]);
+    key[j] = m;
+    val[j] = s_c[pad8(base + j)];
+  }
+  // this thread's run of its last node, then a segmented scan over threads
+  Run mine;
+  mine.kf = key[0];
+  mine.kl = key[kPrPer - 1];
+  mine.tail = 0.0;
+#pragma unroll
+  for (uint32_t j = 0; j < kPrPer; ++j)
+    if (key[j] == mine.kl) mine.tail += val[j];
+  Run inc = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    Run y;
+    y.kf = __shfl_up_sync(0xFFFFFFFFu, inc.kf, o);
+    y.kl = __shfl_up_sync(0xFFFFFFFFu, inc.kl, o);
+    y.tail = __shfl_up_sync(0xFFFFFFFFu, inc.tail, o);
+    if ((int)lane >= o) inc = run_cat(y, inc);
+  }
+  s_kf[tid] = mine.kf;
+  if (lane == 31) s_wr[warp] = inc;
+  __syncthreads();
+  // the run that ends just before this thread: earlier warps in order, then
+  // the earlier lanes of this warp
+  Run before;
+  before.kf = -1;
+  before.kl = -1;
+  before.tail = 0.0;
+  for (uint32_t k = 0; k < warp; ++k) before = k == 0 ? s_wr[0] : run_cat(before, s_wr[k]);
+  Run prev;
+  prev.kf = __shfl_up_sync(0xFFFFFFFFu, inc.kf, 1);
+  prev.kl = __shfl_up_sync(0xFFFFFFFFu, inc.kl, 1);
+  prev.tail = __shfl_up_sync(0xFFFFFFFFu, inc.tail, 1);
+  if (lane > 0) before = warp == 0 ? prev : run_cat(before, prev);
+  const int32_t next = tid + 1 < 256 ? s_kf[tid + 1] : 0x7FFFFFFF;  // node after this thread
+  // every run that ends in this thread's positions gives one node's share
+  double acc = before.kl == key[0] ? before.tail : 0.0;
+#pragma unroll
+  for (uint32_t j = 0; j < kPrPer; ++j) {
+    acc += val[j];
+    const int32_t kn = j + 1 < kPrPer ? key[j + 1] : next;
+    if (kn != key[j]) {
+      const uint32_t v = r0 + (uint32_t)key[j];
+      const uint64_t a = (uint64_t)in_off[v], b = (uint64_t)in_off[v + 1];
+      if (a >= e0 && b <= e1) {
+        sum[v] = acc;
+      } else {
+        if (a < e0) part[2 * t] = acc;
+        if (b > e1) part[2 * t + 1] = acc;
+      }
+      acc = 0.0;
+    }
+  }
+}
+
+// Nodes cut by tile edges: one warp per tile m whose first node started in
+// an earlier tile k and ends in m adds that node's shares, part[2k + 1] then
+// part[2(k+1)] .. part[2m], in a fixed order.
+__global__ void k_pr_fixup(const int64_t* __restrict__ in_off, uint64_t E,
+                           const uint32_t* __restrict__ tnode, uint32_t tiles,
+                           const double* __restrict__ part, double* __restrict__ sum) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t mt = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); mt < tiles; mt += warps) {
+    const uint32_t v = tnode[2 * mt];
+    const uint64_t e0 = (uint64_t)mt * kPrTile;
+    const uint64_t e1 = e0 + kPrTile < E ? e0 + kPrTile : E;
+    const uint64_t a = (uint64_t)in_off[v], b = (uint64_t)in_off[v + 1];
+    if (!(a < e0 && b <= e1)) continue;
+    const uint32_t k = (uint32_t)(a / kPrTile);
     double acc = 0.0;
-    int64_t e = a + lane;
-    for (; e + 96 < b; e += 128) {  // four independent gathers in flight per lane
-      const uint32_t u0 = (uint32_t)__ldcs(in_nbr + e), u1 = (uint32_t)__ldcs(in_nbr + e + 32);
-      const uint32_t u2 = (uint32_t)__ldcs(in_nbr + e + 64), u3 = (uint32_t)__ldcs(in_nbr + e + 96);
-      const double c0 = u0 < V ? __ldg(contrib + u0) : 0.0, c1 = u1 < V ? __ldg(contrib + u1) : 0.0;
-      const double c2 = u2 < V ? __ldg(contrib + u2) : 0.0, c3 = u3 < V ? __ldg(contrib + u3) : 0.0;
-      acc += (c0 + c1) + (c2 + c3);
-    }
-    for (; e < b; e += 32) {
-      const uint32_t u = (uint32_t)__ldcs(in_nbr + e);
-      acc += u < V ? __ldg(contrib + u) : 0.0;
-    }
+    for (uint32_t u = k + 1 + lane; u <= mt; u += 32) acc += part[2 * u];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-    if (lane == 0) sum[v] = acc;
-  }
-}
-
-// The heavy nodes (in-degree above kBig), in any order, and their count.
-__global__ void k_pr_heavy_list(const int64_t* __restrict__ in_off, uint32_t V, uint32_t* heavy,
-                                uint32_t* nheavy) {
-  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
-    if (in_off[v + 1] - in_off[v] > (int64_t)kBig) heavy[atomicAdd(nheavy, 1u)] = v;
-}
-
-// chunk_start[i] = chunks of heavy nodes before heavy[i]; chunk_start[n] = all.  One block.
-__global__ void k_pr_chunk_starts(const int64_t* __restrict__ in_off, const uint32_t* __restrict__ heavy,
-                                  const uint32_t* __restrict__ nheavy, uint32_t* chunk_start) {
-  __shared__ uint32_t s_sw[33];
-  __shared__ uint32_t carry;
-  const uint32_t n = *nheavy;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (uint32_t b0 = 0; b0 < n; b0 += blockDim.x) {
-    const uint32_t i = b0 + threadIdx.x;
-    uint32_t c = 0;
-    if (i < n) {
-      const uint32_t v = heavy[i];
-      c = (uint32_t)((in_off[v + 1] - in_off[v] + kBig - 1) / kBig);
-    }
-    uint32_t tot;
-    const uint32_t ex = block_exclusive_sum<1024>(c, s_sw, tot);
-    if (i < n) chunk_start[i] = carry + ex;
-    __syncthreads();
-    if (threadIdx.x == 0) carry += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) chunk_start[n] = carry;
-}
-
-// One block per chunk of kBig in-edges of a heavy node: a fixed-order sum.
-__global__ void __launch_bounds__(256)
-    k_pr_heavy_chunks(const int64_t* __restrict__ in_off, const int32_t* __restrict__ in_nbr,
-                      uint32_t V, const double* __restrict__ contrib,
-                      const uint32_t* __restrict__ heavy, const uint32_t* __restrict__ nheavy,
-                      const uint32_t* __restrict__ chunk_start, double* __restrict__ partial) {
-  __shared__ double s[256];
-  __shared__ uint32_t s_i;
-  const uint32_t n = *nheavy;
-  const uint32_t total = chunk_start[n];
-  for (uint32_t g = blockIdx.x; g < total; g += gridDim.x) {
-    __syncthreads();
-    if (threadIdx.x == 0) {  // heavy node owning chunk g: last i with chunk_start[i] <= g
-      uint32_t lo = 0, hi = n;
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (chunk_start[mid] <= g) lo = mid;
-        else hi = mid;
-      }
-      s_i = lo;
-    }
-    __syncthreads();
-    const uint32_t i = s_i, v = heavy[i];
-    const int64_t a = in_off[v] + (int64_t)(g - chunk_start[i]) * kBig;
-    const int64_t b = min(a + (int64_t)kBig, in_off[v + 1]);
-    double acc = 0.0;
-    for (int64_t e = a + threadIdx.x; e < b; e += blockDim.x) {
-      const uint32_t u = (uint32_t)__ldcs(in_nbr + e);
-      acc += u < V ? __ldg(contrib + u) : 0.0;
-    }
-    s[threadIdx.x] = acc;
-    __syncthreads();
-    for (uint32_t k = blockDim.x / 2; k > 0; k >>= 1) {
-      if (threadIdx.x < k) s[threadIdx.x] += s[threadIdx.x + k];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) partial[g] = s[0];
-  }
-}
-
-// sum[heavy node] = its chunks' sums, in chunk order.
-__global__ void k_pr_heavy_sum(const uint32_t* __restrict__ heavy, const uint32_t* __restrict__ nheavy,
-                               const uint32_t* __restrict__ chunk_start,
-                               const double* __restrict__ partial, double* __restrict__ sum) {
-  const uint32_t n = *nheavy;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double t = 0.0;
-    for (uint32_t g = chunk_start[i]; g < chunk_start[i + 1]; ++g) t += partial[g];
-    sum[heavy[i]] = t;
+    if (lane == 0) sum[v] = part[2 * k + 1] + acc;
   }
 }
 
@@ -196,33 +268,26 @@ __global__ void k_pr_reduce(const double* __restrict__ partial, uint32_t n, PrSt
 int run_pagerank(const int64_t* out_off, const int64_t* in_off, const int32_t* in_nbr, uint32_t V,
                  uint64_t E, double damping, int32_t iterations, double* rank, cudaStream_t s) {
   if (V == 0) return RINGO_OK;
-  // scratch: contrib[V], sum[V], node partials[kNodeGrid], state, heavy list
-  // [V/kBig + 1], chunk starts [V/kBig + 2], chunk partials [E/kBig + V/kBig + 1]
-  const uint64_t max_heavy = E / kBig + 1;
-  const uint64_t max_chunks = E / kBig + max_heavy + 1;
-  const size_t bytes = 16 * (size_t)V + 8 * kNodeGrid + 256 + 4 * (max_heavy + 1) +
-                       4 * (max_heavy + 2) + 8 * max_chunks + 64;
+  // scratch: contrib[V], sum[V] (zero: nodes without in-edges keep 0), node
+  // partials[kNodeGrid], state, tile shares[2 * tiles], tile nodes[2 * tiles]
+  const uint64_t tiles = (E + kPrTile - 1) / kPrTile;
+  if (tiles > 0x7FFFFFFFull) return RINGO_ERANGE;
+  const size_t bytes = 16 * (size_t)V + 8 * kNodeGrid + 256 + 16 * tiles + 8 * tiles + 64;
   char* buf = (char*)pool_alloc(bytes, s);
   if (!buf) return RINGO_ENOMEM;
   double* contrib = (double*)buf;
   double* sum = contrib + V;
   double* partial = sum + V;
-  double* cpartial = partial + kNodeGrid;
-  PrState* st = (PrState*)(cpartial + max_chunks);
-  uint32_t* nheavy = (uint32_t*)(st + 1);
-  uint32_t* heavy = nheavy + 4;
-  uint32_t* chunk_start = heavy + max_heavy + 1;
+  PrState* st = (PrState*)(partial + kNodeGrid);
+  double* part = (double*)(st + 1);
+  uint32_t* tnode = (uint32_t*)(part + 2 * tiles);
   const uint32_t node_blocks = (V + 255) / 256;
   const uint32_t node_grid = node_blocks < kNodeGrid ? node_blocks : kNodeGrid;
-  int dev = 0, sms = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t lw = ((uint64_t)V + 7) / 8;  // 8 warps per block, one node each
-  const uint32_t light_grid = (uint32_t)(lw < (uint64_t)sms * 64 ? lw : (uint64_t)sms * 64);
+  const uint64_t tw = (tiles + 7) / 8;  // 8 warps per block, one tile each
+  const uint32_t tile_grid = (uint32_t)(tw < 65535 ? (tw > 0 ? tw : 1) : 65535);
   int rc = RINGO_OK;
   cudaError_t e = cudaMemsetAsync(buf, 0, bytes, s);
-  k_pr_heavy_list<<<node_grid, 256, 0, s>>>(in_off, V, heavy, nheavy);
-  k_pr_chunk_starts<<<1, 1024, 0, s>>>(in_off, heavy, nheavy, chunk_start);
+  if (tiles) k_pr_tile_nodes<<<tile_grid, 256, 0, s>>>(in_off, V, E, (uint32_t)tiles, tnode);
   // iteration 0 sets the uniform vector and its contributions
   {
     ProfScope ps("pagerank_nodes", s);
@@ -230,14 +295,10 @@ int run_pagerank(const int64_t* out_off, const int64_t* in_off, const int32_t* i
   }
   k_pr_reduce<<<1, 256, 0, s>>>(partial, node_grid, st);
   for (int32_t it = 0; it < iterations; ++it) {
-    {
+    if (tiles) {
       ProfScope ps("pagerank_edges", s);
-      k_pr_light<<<light_grid, 256, 0, s>>>(in_off, in_nbr, V, contrib, sum);
-      if (E > kBig) {
-        k_pr_heavy_chunks<<<(uint32_t)sms * 4, 256, 0, s>>>(in_off, in_nbr, V, contrib, heavy, nheavy,
-                                                            chunk_start, cpartial);
-        k_pr_heavy_sum<<<64, 256, 0, s>>>(heavy, nheavy, chunk_start, cpartial, sum);
-      }
+      k_pr_edges<<<(uint32_t)tiles, 256, 0, s>>>(in_off, in_nbr, V, E, tnode, contrib, sum, part);
+      k_pr_fixup<<<tile_grid, 256, 0, s>>>(in_off, E, tnode, (uint32_t)tiles, part, sum);
     }
     {
       ProfScope ps("pagerank_nodes", s);

@@ -4,9 +4,9 @@
 // constant, in place; join with a single-column table, into a new table).
 //
 // Both are single-pass stable compactions over 4096-row tiles: a block loads
-// its rows (16 consecutive rows per thread), decides how many output rows
-// each gives (0/1 for select; the key's multiplicity in the second table for
-// join), and finds the tile's output offset with the two-level decoupled
+// its rows (each warp 512 consecutive rows, 32 per coalesced step), decides
+// how many output rows each gives (0/1 for select; the key's multiplicity in
+// the second table for join), and finds the tile's output offset with the two-level decoupled
 // look-back over tiles claimed in order.  Select writes in place: a kept row
 // moves to a position at or before its own, and a tile publishes its count
 // only after it has loaded all its rows, so no row is overwritten before it
@@ -98,14 +98,20 @@ __global__ void k_join_count(const int32_t* __restrict__ keycol, uint32_t n,
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(total, c);
 }
 
-// One tile of the compaction.  mode 0: select (in place, src/dst are both
-// input and output); mode 1: join (each row written mult times into out).
+// One tile of the compaction.  kMode 0: select (in place, src/dst are both
+// input and output); kMode 1: join (each row written mult times into out).
+// Warp w of the block owns rows [tile * 4096 + 512 w, + 512) and reads them
+// 32 consecutive rows per step, so every load is one coalesced 128-byte
+// line; a row's place among the warp's output rows comes from a ballot
+// (select) or a warp scan of multiplicities (join) per step.
+template <int kMode>
 __global__ void __launch_bounds__(kOpThreads)
-    k_compact(int32_t* src, int32_t* dst, uint32_t n, int mode, int col, int op, int32_t value,
+    k_compact(int32_t* src, int32_t* dst, uint32_t n, int col, int op, int32_t value,
               const unsigned long long* __restrict__ table, uint32_t mask,
               int32_t* __restrict__ out_src, int32_t* __restrict__ out_dst, OpScan sc,
               uint64_t* n_out) {
-  __shared__ uint32_t s_sw[kOpThreads / 32 + 1];
+  constexpr int kWarps = kOpThreads / 32;
+  __shared__ uint32_t s_sw[kWarps];
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_prefix;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -114,40 +120,66 @@ __global__ void __launch_bounds__(kOpThreads)
   const uint32_t tile = s_tile;
   const uint32_t ntiles = (n + kOpTile - 1) / kOpTile;
   if (tile >= ntiles) return;
-  const uint32_t r0 = tile * kOpTile + tid * kOpItems;  // this thread's 16 consecutive rows
+  const uint32_t base = tile * kOpTile + (uint32_t)warp * (32 * kOpItems) + (uint32_t)lane;
+  const uint32_t lt = lanemask_lt();
   int32_t s[kOpItems], d[kOpItems];
-  uint32_t m[kOpItems];
-  uint32_t mine = 0;
+  uint32_t m[kMode == 0 ? 1 : kOpItems];
 #pragma unroll
   for (int q = 0; q < kOpItems; ++q) {
-    const uint32_t r = r0 + q;
-    m[q] = 0;
-    if (r < n) {
-      s[q] = src[r];
-      d[q] = dst[r];
-      const int32_t key = col ? d[q] : s[q];
-      m[q] = mode == 0 ? (compare(key, op, value) ? 1u : 0u) : lookup(table, mask, key);
-    }
-    mine += m[q];
+    const uint32_t r = base + 32u * q;
+    s[q] = r < n ? src[r] : 0;
+    d[q] = r < n ? dst[r] : 0;
   }
-  uint32_t total;
-  const uint32_t before = block_exclusive_sum<kOpThreads>(mine, s_sw, total);
+  uint32_t wtotal = 0;  // output rows of this warp
+#pragma unroll
+  for (int q = 0; q < kOpItems; ++q) {
+    const uint32_t r = base + 32u * q;
+    const int32_t key = col ? d[q] : s[q];
+    if constexpr (kMode == 0) {
+      wtotal += __popc(__ballot_sync(0xFFFFFFFFu, r < n && compare(key, op, value)));
+    } else {
+      m[q] = r < n ? lookup(table, mask, key) : 0u;
+      wtotal += __reduce_add_sync(0xFFFFFFFFu, m[q]);
+    }
+  }
+  if (lane == 0) s_sw[warp] = wtotal;
+  __syncthreads();
   if (warp == 0) {
+    const uint32_t t = lane < kWarps ? s_sw[lane] : 0u;
+    const uint32_t inc = warp_inclusive_sum(t);
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
     const uint64_t excl = scan_prefix(sc.status, sc.ch, tile, ntiles, pack2(0, total), sc.err);
+    if (lane < kWarps) s_sw[lane] = inc - t;
     if (lane == 0) {
       s_prefix = excl;
       if (tile == ntiles - 1) *n_out = unpackB(excl) + (uint64_t)total;
     }
   }
   __syncthreads();
-  uint32_t w = unpackB(s_prefix) + before;
-  int32_t* os = mode == 0 ? src : out_src;
-  int32_t* od = mode == 0 ? dst : out_dst;
+  uint32_t w = (uint32_t)unpackB(s_prefix) + s_sw[warp];  // next output row of this warp
+  int32_t* os = kMode == 0 ? src : out_src;
+  int32_t* od = kMode == 0 ? dst : out_dst;
 #pragma unroll
   for (int q = 0; q < kOpItems; ++q) {
-    for (uint32_t t = 0; t < m[q]; ++t, ++w) {
-      os[w] = s[q];
-      od[w] = d[q];
+    const uint32_t r = base + 32u * q;
+    const int32_t key = col ? d[q] : s[q];
+    if constexpr (kMode == 0) {
+      const bool keep = r < n && compare(key, op, value);
+      const uint32_t b = __ballot_sync(0xFFFFFFFFu, keep);
+      if (keep) {
+        const uint32_t p = w + __popc(b & lt);
+        os[p] = s[q];
+        od[p] = d[q];
+      }
+      w += __popc(b);
+    } else {
+      const uint32_t inc = warp_inclusive_sum(m[q]);
+      uint32_t p = w + inc - m[q];
+      for (uint32_t t = 0; t < m[q]; ++t, ++p) {
+        os[p] = s[q];
+        od[p] = d[q];
+      }
+      w += __shfl_sync(0xFFFFFFFFu, inc, 31);
     }
   }
 }
@@ -193,8 +225,8 @@ int run_select(int32_t* src, int32_t* dst, uint32_t n, int col, int op, int32_t 
   const uint32_t tiles = (n + kOpTile - 1) / kOpTile;
   {
     ProfScope ps("select", s);
-    k_compact<<<tiles, kOpThreads, 0, s>>>(src, dst, n, 0, col, op, value, nullptr, 0, nullptr,
-                                           nullptr, cs.sc, cs.n_out);
+    k_compact<0><<<tiles, kOpThreads, 0, s>>>(src, dst, n, col, op, value, nullptr, 0, nullptr,
+                                              nullptr, cs.sc, cs.n_out);
   }
   uint64_t h[2] = {0, 0};
   cudaError_t e = cudaGetLastError();
@@ -260,9 +292,9 @@ int run_join(const int32_t* src, const int32_t* dst, uint32_t n, int col, const 
       const uint32_t tiles = (n + kOpTile - 1) / kOpTile;
       {
         ProfScope ps("join_write", s);
-        k_compact<<<tiles, kOpThreads, 0, s>>>(const_cast<int32_t*>(src), const_cast<int32_t*>(dst),
-                                               n, 1, col, 0, 0, table, mask, out_src, out_dst,
-                                               cs.sc, cs.n_out);
+        k_compact<1><<<tiles, kOpThreads, 0, s>>>(const_cast<int32_t*>(src),
+                                                  const_cast<int32_t*>(dst), n, col, 0, 0, table,
+                                                  mask, out_src, out_dst, cs.sc, cs.n_out);
       }
       uint32_t herr = 0;
       e = cudaGetLastError();

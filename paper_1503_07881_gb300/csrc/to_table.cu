@@ -12,6 +12,7 @@
 #include <stdint.h>
 
 #include "../../include/ringo.h"
+#include "device_util.cuh"
 #include "host_util.h"
 #include "ringo_internal.cuh"
 
@@ -21,6 +22,10 @@ namespace {
 
 constexpr uint32_t kExpandTile = 2048;   // edges per tile
 constexpr uint32_t kExpandWindow = 2048; // most nodes a tile resolves by the max-scan
+
+// shared-memory slot of tile position p: one pad word after every 8, so the
+// 8 consecutive positions of each thread fall in distinct banks across a warp
+__device__ __forceinline__ uint32_t pad8(uint32_t p) { return p + (p >> 3); }
 
 // largest r in [0, V) with off[r] <= e (off[0] = 0 <= e < off[V] = E)
 __device__ __forceinline__ uint32_t owner(const int64_t* __restrict__ off, uint32_t V, uint64_t e) {
@@ -45,7 +50,7 @@ __global__ void __launch_bounds__(256)
              const int32_t* __restrict__ nbr, uint32_t V, uint64_t E, int32_t* __restrict__ key,
              int32_t* __restrict__ val) {
   constexpr uint32_t kPer = kExpandTile / 256;  // positions per thread in the scan
-  __shared__ int32_t s_own[kExpandTile];
+  __shared__ int32_t s_own[kExpandTile + kExpandTile / 8];
   __shared__ int32_t s_w[8];
   __shared__ uint32_t s_r0, s_r1;
   for (uint64_t e0 = (uint64_t)blockIdx.x * kExpandTile; e0 < E;
@@ -53,23 +58,28 @@ __global__ void __launch_bounds__(256)
     const uint64_t e1 = min(e0 + kExpandTile, E);
     const uint32_t len = (uint32_t)(e1 - e0);
     __syncthreads();
-    if (threadIdx.x == 0) s_r0 = owner(off, V, e0);
-    if (threadIdx.x == 32) s_r1 = owner(off, V, e1 - 1);
-    for (uint32_t t = threadIdx.x; t < kExpandTile; t += blockDim.x) s_own[t] = 0;
+    if (threadIdx.x < 32) {
+      const uint32_t r = warp_owner(off, V, e0, threadIdx.x);
+      if (threadIdx.x == 0) s_r0 = r;
+    } else if (threadIdx.x < 64) {
+      const uint32_t r = warp_owner(off, V, e1 - 1, threadIdx.x - 32);
+      if (threadIdx.x == 32) s_r1 = r;
+    }
+    for (uint32_t t = threadIdx.x; t < kExpandTile + kExpandTile / 8; t += blockDim.x) s_own[t] = 0;
     __syncthreads();
     const uint32_t r0 = s_r0, r1 = s_r1;
     if (r1 - r0 + 1 <= kExpandWindow) {
       // nodes r0+1 .. r1 start inside the tile
       for (uint32_t r = r0 + 1 + threadIdx.x; r <= r1; r += blockDim.x) {
         const uint64_t p = (uint64_t)off[r] - e0;
-        if (p < len) atomicMax(&s_own[p], (int32_t)(r - r0));
+        if (p < len) atomicMax(&s_own[pad8((uint32_t)p)], (int32_t)(r - r0));
       }
       __syncthreads();
       // inclusive max-scan of s_own (each thread 8 consecutive positions)
       const uint32_t base = threadIdx.x * kPer;
       int32_t run = 0;
 #pragma unroll
-      for (uint32_t q = 0; q < kPer; ++q) run = max(run, s_own[base + q]);
+      for (uint32_t q = 0; q < kPer; ++q) run = max(run, s_own[pad8(base + q)]);
       const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
       int32_t incl = run;
 #pragma unroll
@@ -86,13 +96,13 @@ __global__ void __launch_bounds__(256)
       int32_t m = carry;
 #pragma unroll
       for (uint32_t q = 0; q < kPer; ++q) {
-        m = max(m, s_own[base + q]);
-        s_own[base + q] = m;
+        m = max(m, s_own[pad8(base + q)]);
+        s_own[pad8(base + q)] = m;
       }
       __syncthreads();
       for (uint32_t t = threadIdx.x; t < len; t += blockDim.x) {
         const uint64_t e = e0 + t;
-        const uint32_t r = r0 + (uint32_t)s_own[t];
+        const uint32_t r = r0 + (uint32_t)s_own[pad8(t)];
         const int32_t mm = __ldcs(nbr + e);
         key[e] = node_ids[r];
         val[e] = (uint32_t)mm < V ? __ldg(node_ids + mm) : 0;

@@ -2,7 +2,8 @@
 through the C ABI, against the oracle's fp64 power iteration.
 
 Tolerance: the GPU forms each node's sum over its in-edges in another order
-than the oracle (per-thread runs, then per-tile and global adds), and the
+than the oracle (8-edge runs, a scan over a tile's threads, then the shares of
+the 2048-edge tiles a node spans, in tile order), and the
 dangling mass by a tree of block sums.  Reordering an fp64 sum of k positive
 terms changes it by at most (k - 1) * 2^-53 relative; with in-degrees below
 3e6 and the dangling sum over at most 4.2e7 nodes that is below 5e-9 per
@@ -103,7 +104,7 @@ def test_argument_errors():
 
 def test_same_bits_on_every_run():
     # each node's sum is formed in a fixed order: two runs agree bit for bit,
-    # also with a hub node split into chunks
+    # also with a hub node cut across many edge tiles
     n = 40_000
     s = np.concatenate([np.arange(n, dtype=np.int32) + 100,
                         np.random.default_rng(1).integers(0, 5000, 200_000).astype(np.int32)])
