@@ -60,6 +60,15 @@ def test_closed_forms():
     assert tri == 0
 
 
+def test_clique_longer_than_staged_list():
+    # in a 1100-clique the lowest-ordered members have more than 1024 oriented
+    # neighbours (searched in global memory), the rest are staged in shared memory
+    n = 1100
+    a, b = np.triu_indices(n, 1)
+    _, tri = gpu_undirected(a.astype(np.int32) * 3, b.astype(np.int32) * 3)
+    assert tri == comb(n, 3)
+
+
 def test_hub_and_clique():
     # a hub joined to 50K nodes, and a 60-clique among some of them: the hub
     # is ordered last, the clique's triangles are found from its members
