@@ -60,9 +60,9 @@ def test_closed_forms():
     assert tri == 0
 
 
-def test_clique_longer_than_staged_list():
-    # in a 1100-clique the lowest-ordered members have more than 1024 oriented
-    # neighbours (searched in global memory), the rest are staged in shared memory
+def test_large_clique():
+    # a 1100-clique: oriented lists of every length from 0 to 1099, and
+    # C(1100, 3) = 221,228,700 triangles in one 64-bit total
     n = 1100
     a, b = np.triu_indices(n, 1)
     _, tri = gpu_undirected(a.astype(np.int32) * 3, b.astype(np.int32) * 3)
