@@ -171,26 +171,14 @@ void launch_plan(const Launch& L, int which, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- K2/K4 ---
-// One onesweep LSD pass.  The kernel is persistent (a few blocks per SM) and
-// walks tiles of kSortTile keys handed out in order by an atomic counter.
-// Each tile arrives in shared memory by bulk asynchronous copy
-// (cp.async.bulk + mbarrier) into one of two buffers, so the next tile's
-// load is in flight while the current one is ranked, looked back and
-// scattered.  Per tile:
-//   1. every warp ranks its 512 keys in position order: match.any finds the
-//      lanes holding the same digit, the highest of them bumps the warp's
-//      digit counter for the group;
-//   2. thread d owns digit d: it sums the warp counters, publishes the
-//      tile's digit count, and obtains the count of digit d in all earlier
-//      tiles by decoupled look-back (bounded waits);
-//   3. the tile is re-staged in digit order in the same buffer and written
-//      out with consecutive keys of a digit going to consecutive addresses.
-// which: 0 out-sort, 1 in-sort.  pass: index within that sort.  gpass: global
-// pass number; status region gpass&1 is used, and every processed tile clears
-// its row of region (gpass+1)&1 for the next pass.  Tiles are claimed in
-// increasing order and a tile waits only on smaller tiles, every one of which
-// is held by a running block that never waits on a larger tile, so the
-// waits always end.
+// One onesweep LSD pass: one block per tile of kSortTile keys, tiles claimed
+// in increasing order through an atomic counter (the kernel and its per-tile
+// steps are described at k_onesweep below).  which: 0 out-sort, 1 in-sort.
+// pass: index within that sort.  gpass: global pass number; status region
+// gpass&1 is used, and every processed tile clears its row of region
+// (gpass+1)&1 for the next pass.  A tile waits only on smaller tiles, every
+// one of which was claimed by a block that is resident or done and never
+// waits on a larger tile, so the waits always end.
 
 // Two-level decoupled look-back for digit d of `tile`: first over the
 // earlier tiles of the tile's own chunk (their aggregates or an inclusive
