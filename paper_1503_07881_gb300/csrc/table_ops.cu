@@ -10,12 +10,18 @@
 // look-back over tiles claimed in order.  Select writes in place: a kept row
 // moves to a position at or before its own, and a tile publishes its count
 // only after it has loaded all its rows, so no row is overwritten before it
-// is read.  Join builds an open-addressing hash table of the second table's
-// keys with their multiplicities first.
+// is read.  Join first builds the set of the second table's keys with their
+// multiplicities (an open-addressing hash table when that is small, else a
+// bitmap over the key range with a hash table for the keys that occur more
+// than once); a marking pass then records, per row, whether its key occurs
+// once or more often (two bits per row) and scans the tiles' output counts,
+// so the output size is known before anything is written; a writing pass
+// copies the matching rows, skipping tiles without any.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/ringo.h"
 #include "device_util.cuh"
@@ -29,6 +35,9 @@ namespace {
 constexpr uint32_t kOpThreads = 256;
 constexpr uint32_t kOpItems = 16;
 constexpr uint32_t kOpTile = kOpThreads * kOpItems;  // 4096 rows
+// a join's key hash table up to this size stays in cache; above it, a bitmap
+// over the key range is used when that is smaller
+constexpr uint64_t kJoinHashCacheBytes = 8ull << 20;
 
 struct OpScan {
   uint64_t* status;  // [tiles]
@@ -86,29 +95,202 @@ __global__ void k_hash_build(const int32_t* __restrict__ keys, uint32_t nkeys,
   }
 }
 
-// total output rows of the join (64-bit), to size and check it before writing
-__global__ void k_join_count(const int32_t* __restrict__ keycol, uint32_t n,
-                             const unsigned long long* __restrict__ table, uint32_t mask,
-                             unsigned long long* __restrict__ total) {
-  unsigned long long c = 0;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    c += lookup(table, mask, keycol[i]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-  if ((threadIdx.x & 31) == 0 && c) atomicAdd(total, c);
+// The second table's keys: multiplicity of a key, 0 if absent.  Either an
+// open-addressing hash table of (key, count) slots (bits == nullptr), or a
+// bitmap over [kmin, kmin + range) of the keys present, a bitmap of those
+// present more than once (dup, nullptr if none is) and a hash table of the
+// latter's counts.
+struct KeySet {
+  const unsigned long long* table;
+  uint32_t mask;
+  const uint32_t* bits;
+  const uint32_t* dup;
+  int64_t kmin;
+  uint64_t range;
+};
+
+__device__ __forceinline__ uint32_t multiplicity(const KeySet& ks, int32_t k) {
+  if (!ks.bits) return lookup(ks.table, ks.mask, k);
+  const uint64_t off = (uint64_t)((int64_t)k - ks.kmin);  // below kmin wraps past range
+  if (off >= ks.range) return 0u;
+  const uint32_t w = (uint32_t)(off >> 5), b = 1u << (off & 31);
+  if (!(__ldg(ks.bits + w) & b)) return 0u;
+  if (!ks.dup || !(__ldg(ks.dup + w) & b)) return 1u;
+  return lookup(ks.table, ks.mask, k);
 }
 
-// One tile of the compaction.  kMode 0: select (in place, src/dst are both
-// input and output); kMode 1: join (each row written mult times into out).
-// Warp w of the block owns rows [tile * 4096 + 512 w, + 512) and reads them
-// 32 consecutive rows per step, so every load is one coalesced 128-byte
-// line; a row's place among the warp's output rows comes from a ballot
-// (select) or a warp scan of multiplicities (join) per step.
-template <int kMode>
+// mm[0] = min, mm[1] = max of the keys (mm preset to INT32_MAX, INT32_MIN)
+__global__ void k_key_range(const int32_t* __restrict__ keys, uint32_t nkeys, int* __restrict__ mm) {
+  int lo = 0x7FFFFFFF, hi = (int)0x80000000;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nkeys; i += gridDim.x * blockDim.x) {
+    lo = min(lo, keys[i]);
+    hi = max(hi, keys[i]);
+  }
+  lo = __reduce_min_sync(0xFFFFFFFFu, lo);
+  hi = __reduce_max_sync(0xFFFFFFFFu, hi);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(mm, lo);
+    atomicMax(mm + 1, hi);
+  }
+}
+
+// bits: every key; dup: keys met again; extra: the number of repeats
+__global__ void k_bits_build(const int32_t* __restrict__ keys, uint32_t nkeys, int64_t kmin,
+                             uint32_t* __restrict__ bits, uint32_t* __restrict__ dup,
+                             unsigned long long* __restrict__ extra) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nkeys; i += gridDim.x * blockDim.x) {
+    const uint64_t off = (uint64_t)((int64_t)keys[i] - kmin);
+    const uint32_t w = (uint32_t)(off >> 5), b = 1u << (off & 31);
+    if (atomicOr(bits + w, b) & b) {
+      atomicOr(dup + w, b);
+      atomicAdd(extra, 1ull);
+    }
+  }
+}
+
+// (key, count) of every key that occurs more than once
+__global__ void k_hash_dup(const int32_t* __restrict__ keys, uint32_t nkeys, int64_t kmin,
+                           const uint32_t* __restrict__ dup, unsigned long long* __restrict__ table,
+                           uint32_t mask) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nkeys; i += gridDim.x * blockDim.x) {
+    const int32_t k = keys[i];
+    const uint64_t off = (uint64_t)((int64_t)k - kmin);
+    if (!(dup[off >> 5] & (1u << (off & 31)))) continue;
+    const unsigned long long mine = ((unsigned long long)(uint32_t)k << 32) | 1ull;
+    uint32_t h = hash_slot(k, mask);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+      unsigned long long slot = table[h];
+      if ((uint32_t)slot == 0u) {
+        slot = atomicCAS(table + h, 0ull, mine);
+        if (slot == 0ull) break;
+      }
+      if ((uint32_t)(slot >> 32) == (uint32_t)k) {
+        atomicAdd(table + h, 1ull);
+        break;
+      }
+      h = (h + 1) & mask;
+    }
+  }
+}
+
+// Join, marking pass: one 4096-row tile per block, claimed in order; warp w
+// reads rows [tile * 4096 + 512 w, + 512), 32 per step.  flags[(tile * 8 + w)
+// * 16 + step] = (rows whose key occurs, rows whose key occurs more than
+// once) as lane bitmasks; tile_off[tile] = output rows of all earlier tiles
+// (two-level decoupled look-back over 62-bit sums), *n_out the total.
 __global__ void __launch_bounds__(kOpThreads)
-    k_compact(int32_t* src, int32_t* dst, uint32_t n, int col, int op, int32_t value,
-              const unsigned long long* __restrict__ table, uint32_t mask,
-              int32_t* __restrict__ out_src, int32_t* __restrict__ out_dst, OpScan sc,
+    k_join_mark(const int32_t* __restrict__ keycol, uint32_t n, KeySet ks, uint2* __restrict__ flags,
+                uint64_t* __restrict__ tile_off, OpScan sc, uint64_t* n_out) {
+  constexpr int kWarps = kOpThreads / 32;
+  __shared__ unsigned long long s_w[kWarps];
+  __shared__ uint32_t s_tile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(sc.counter, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint32_t ntiles = (n + kOpTile - 1) / kOpTile;
+  if (tile >= ntiles) return;
+  const uint32_t base = tile * kOpTile + (uint32_t)warp * (32 * kOpItems) + (uint32_t)lane;
+  int32_t k[kOpItems];
+#pragma unroll
+  for (int q = 0; q < kOpItems; ++q) {
+    const uint32_t r = base + 32u * q;
+    k[q] = r < n ? keycol[r] : 0;
+  }
+  unsigned long long mine = 0;
+  uint2* wf = flags + ((size_t)tile * kWarps + warp) * kOpItems;
+#pragma unroll
+  for (int q = 0; q < kOpItems; ++q) {
+    const uint32_t r = base + 32u * q;
+    const uint32_t m = r < n ? multiplicity(ks, k[q]) : 0u;
+    const uint32_t once = __ballot_sync(0xFFFFFFFFu, m != 0u);
+    const uint32_t more = __ballot_sync(0xFFFFFFFFu, m > 1u);
+    if (lane == 0) wf[q] = make_uint2(once, more);
+    mine += m;
+  }
+  mine = warp_sum(mine);
+  if (lane == 0) s_w[warp] = mine;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long total = warp_sum(lane < kWarps ? s_w[lane] : 0ull);
+    const uint64_t excl = scan_prefix(sc.status, sc.ch, tile, ntiles, (uint64_t)total, sc.err);
+    if (lane == 0) {
+      tile_off[tile] = excl;
+      if (tile == ntiles - 1) *n_out = excl + total;
+    }
+  }
+}
+
+// Join, writing pass: one block per tile (any order); a tile without output
+// rows returns at once.  Rows are read only in the 32-row steps that have a
+// match; each matching row is written once per occurrence of its key.
+__global__ void __launch_bounds__(kOpThreads)
+    k_join_write(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, uint32_t n,
+                 int col, KeySet ks, const uint2* __restrict__ flags,
+                 const uint64_t* __restrict__ tile_off, uint64_t total, int32_t* __restrict__ out_src,
+                 int32_t* __restrict__ out_dst) {
+  constexpr int kWarps = kOpThreads / 32;
+  __shared__ uint32_t s_w[kWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t tile = blockIdx.x;
+  const uint32_t ntiles = (n + kOpTile - 1) / kOpTile;
+  const uint64_t t0 = tile_off[tile];
+  const uint64_t t1 = tile + 1 < ntiles ? tile_off[tile + 1] : total;
+  if (t0 == t1) return;
+  const uint32_t base = tile * kOpTile + (uint32_t)warp * (32 * kOpItems) + (uint32_t)lane;
+  const uint32_t lt = lanemask_lt();
+  const uint2 myf = lane < kOpItems ? flags[((size_t)tile * kWarps + warp) * kOpItems + lane]
+                                    : make_uint2(0u, 0u);
+  int32_t s[kOpItems], d[kOpItems];
+  uint32_t m[kOpItems];
+  uint32_t wtotal = 0;
+#pragma unroll
+  for (int q = 0; q < kOpItems; ++q) {
+    const uint32_t once = __shfl_sync(0xFFFFFFFFu, myf.x, q);
+    const uint32_t more = __shfl_sync(0xFFFFFFFFu, myf.y, q);
+    const uint32_t r = base + 32u * q;
+    m[q] = 0u;
+    s[q] = d[q] = 0;
+    if ((once >> lane) & 1u) {
+      s[q] = src[r];
+      d[q] = dst[r];
+      m[q] = ((more >> lane) & 1u) ? multiplicity(ks, col ? d[q] : s[q]) : 1u;
+    }
+    wtotal += more ? __reduce_add_sync(0xFFFFFFFFu, m[q]) : (uint32_t)__popc(once);
+  }
+  if (lane == 0) s_w[warp] = wtotal;
+  __syncthreads();
+  uint32_t w = (uint32_t)t0;  // the total fits 31 bits (checked before this pass)
+  for (int k2 = 0; k2 < warp; ++k2) w += s_w[k2];
+#pragma unroll
+  for (int q = 0; q < kOpItems; ++q) {
+    const uint32_t once = __shfl_sync(0xFFFFFFFFu, myf.x, q);
+    const uint32_t more = __shfl_sync(0xFFFFFFFFu, myf.y, q);
+    if (!more) {
+      if ((once >> lane) & 1u) {
+        const uint32_t p = w + __popc(once & lt);
+        out_src[p] = s[q];
+        out_dst[p] = d[q];
+      }
+      w += __popc(once);
+    } else {
+      const uint32_t inc = warp_inclusive_sum(m[q]);
+      uint32_t p = w + inc - m[q];
+      for (uint32_t t = 0; t < m[q]; ++t, ++p) {
+        out_src[p] = s[q];
+        out_dst[p] = d[q];
+      }
+      w += __shfl_sync(0xFFFFFFFFu, inc, 31);
+    }
+  }
+}
+
+// Select, in place: one tile per block, claimed in order.  Warp w of the
+// block owns rows [tile * 4096 + 512 w, + 512) and reads them 32 consecutive
+// rows per step, so every load is one coalesced 128-byte line; a kept row's
+// place among its warp's kept rows comes from a ballot per step.
+__global__ void __launch_bounds__(kOpThreads)
+    k_compact(int32_t* src, int32_t* dst, uint32_t n, int col, int op, int32_t value, OpScan sc,
               uint64_t* n_out) {
   constexpr int kWarps = kOpThreads / 32;
   __shared__ uint32_t s_sw[kWarps];
@@ -123,24 +305,17 @@ __global__ void __launch_bounds__(kOpThreads)
   const uint32_t base = tile * kOpTile + (uint32_t)warp * (32 * kOpItems) + (uint32_t)lane;
   const uint32_t lt = lanemask_lt();
   int32_t s[kOpItems], d[kOpItems];
-  uint32_t m[kMode == 0 ? 1 : kOpItems];
 #pragma unroll
   for (int q = 0; q < kOpItems; ++q) {
     const uint32_t r = base + 32u * q;
     s[q] = r < n ? src[r] : 0;
     d[q] = r < n ? dst[r] : 0;
   }
-  uint32_t wtotal = 0;  // output rows of this warp
+  uint32_t wtotal = 0;  // kept rows of this warp
 #pragma unroll
   for (int q = 0; q < kOpItems; ++q) {
     const uint32_t r = base + 32u * q;
-    const int32_t key = col ? d[q] : s[q];
-    if constexpr (kMode == 0) {
-      wtotal += __popc(__ballot_sync(0xFFFFFFFFu, r < n && compare(key, op, value)));
-    } else {
-      m[q] = r < n ? lookup(table, mask, key) : 0u;
-      wtotal += __reduce_add_sync(0xFFFFFFFFu, m[q]);
-    }
+    wtotal += __popc(__ballot_sync(0xFFFFFFFFu, r < n && compare(col ? d[q] : s[q], op, value)));
   }
   if (lane == 0) s_sw[warp] = wtotal;
   __syncthreads();
@@ -148,39 +323,26 @@ __global__ void __launch_bounds__(kOpThreads)
     const uint32_t t = lane < kWarps ? s_sw[lane] : 0u;
     const uint32_t inc = warp_inclusive_sum(t);
     const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
-    const uint64_t excl = scan_prefix(sc.status, sc.ch, tile, ntiles, pack2(0, total), sc.err);
+    const uint64_t excl = scan_prefix(sc.status, sc.ch, tile, ntiles, (uint64_t)total, sc.err);
     if (lane < kWarps) s_sw[lane] = inc - t;
     if (lane == 0) {
       s_prefix = excl;
-      if (tile == ntiles - 1) *n_out = unpackB(excl) + (uint64_t)total;
+      if (tile == ntiles - 1) *n_out = excl + (uint64_t)total;
     }
   }
   __syncthreads();
-  uint32_t w = (uint32_t)unpackB(s_prefix) + s_sw[warp];  // next output row of this warp
-  int32_t* os = kMode == 0 ? src : out_src;
-  int32_t* od = kMode == 0 ? dst : out_dst;
+  uint32_t w = (uint32_t)s_prefix + s_sw[warp];  // next output row of this warp
 #pragma unroll
   for (int q = 0; q < kOpItems; ++q) {
     const uint32_t r = base + 32u * q;
-    const int32_t key = col ? d[q] : s[q];
-    if constexpr (kMode == 0) {
-      const bool keep = r < n && compare(key, op, value);
-      const uint32_t b = __ballot_sync(0xFFFFFFFFu, keep);
-      if (keep) {
-        const uint32_t p = w + __popc(b & lt);
-        os[p] = s[q];
-        od[p] = d[q];
-      }
-      w += __popc(b);
-    } else {
-      const uint32_t inc = warp_inclusive_sum(m[q]);
-      uint32_t p = w + inc - m[q];
-      for (uint32_t t = 0; t < m[q]; ++t, ++p) {
-        os[p] = s[q];
-        od[p] = d[q];
-      }
-      w += __shfl_sync(0xFFFFFFFFu, inc, 31);
+    const bool keep = r < n && compare(col ? d[q] : s[q], op, value);
+    const uint32_t b = __ballot_sync(0xFFFFFFFFu, keep);
+    if (keep) {
+      const uint32_t p = w + __popc(b & lt);
+      src[p] = s[q];
+      dst[p] = d[q];
     }
+    w += __popc(b);
   }
 }
 
@@ -225,8 +387,7 @@ int run_select(int32_t* src, int32_t* dst, uint32_t n, int col, int op, int32_t 
   const uint32_t tiles = (n + kOpTile - 1) / kOpTile;
   {
     ProfScope ps("select", s);
-    k_compact<0><<<tiles, kOpThreads, 0, s>>>(src, dst, n, col, op, value, nullptr, 0, nullptr,
-                                              nullptr, cs.sc, cs.n_out);
+    k_compact<<<tiles, kOpThreads, 0, s>>>(src, dst, n, col, op, value, cs.sc, cs.n_out);
   }
   uint64_t h[2] = {0, 0};
   cudaError_t e = cudaGetLastError();
@@ -247,71 +408,153 @@ int run_select(int32_t* src, int32_t* dst, uint32_t n, int col, int op, int32_t 
   return RINGO_OK;
 }
 
+// The second table's key set (see KeySet); buffers in *owned, freed by the caller.
+static int build_keyset(const int32_t* keys, uint32_t nkeys, cudaStream_t s, KeySet* ks,
+                        std::vector<void*>* owned) {
+  const uint32_t kg = (nkeys + 255) / 256 < 8192 ? (nkeys + 255) / 256 : 8192;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* p = pool_alloc(bytes, s);
+    if (p) owned->push_back(p);
+    return p;
+  };
+  auto hash_of = [&](uint64_t nk) -> uint32_t {  // slots for nk distinct keys, load <= 1/2
+    uint32_t slots = 1;
+    while (slots < 2 * nk) slots <<= 1;
+    return slots;
+  };
+  *ks = KeySet{};
+  const uint32_t slots = hash_of(nkeys);
+  int32_t* mm = (int32_t*)alloc(256);
+  if (!mm) return RINGO_ENOMEM;
+  bool use_bits = false;
+  int32_t hmm[2] = {0, 0};
+  if (8ull * slots > kJoinHashCacheBytes) {
+    // a bitmap when it is smaller than the hash table
+    const int32_t init[2] = {0x7FFFFFFF, (int32_t)0x80000000};
+    cudaError_t e = cudaMemcpyAsync(mm, init, 8, cudaMemcpyHostToDevice, s);
+    k_key_range<<<kg, 256, 0, s>>>(keys, nkeys, mm);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hmm, mm, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error(std::string("join: ") + cudaGetErrorString(e));
+      return RINGO_ECUDA;
+    }
+    const uint64_t range = (uint64_t)((int64_t)hmm[1] - (int64_t)hmm[0]) + 1;
+    use_bits = 2 * 4 * ((range + 31) / 32) < 8ull * slots;
+  }
+  if (!use_bits) {
+    unsigned long long* table = (unsigned long long*)alloc(8ull * slots);
+    if (!table) return RINGO_ENOMEM;
+    if (cudaMemsetAsync(table, 0, 8ull * slots, s) != cudaSuccess) return RINGO_ECUDA;
+    {
+      ProfScope ps("join_build", s);
+      k_hash_build<<<kg, 256, 0, s>>>(keys, nkeys, table, slots - 1);
+    }
+    ks->table = table;
+    ks->mask = slots - 1;
+    return RINGO_OK;
+  }
+  const int64_t kmin = hmm[0];
+  const uint64_t range = (uint64_t)((int64_t)hmm[1] - kmin) + 1;
+  const size_t words = (size_t)((range + 31) / 32);
+  uint32_t* bits = (uint32_t*)alloc(8 * words + 256);
+  if (!bits) return RINGO_ENOMEM;
+  uint32_t* dup = bits + words;
+  unsigned long long* extra = (unsigned long long*)(dup + words);  // 8 * words bytes in: aligned
+  unsigned long long hextra = 0;
+  cudaError_t e = cudaMemsetAsync(bits, 0, 8 * words + 256, s);
+  {
+    ProfScope ps("join_build", s);
+    k_bits_build<<<kg, 256, 0, s>>>(keys, nkeys, kmin, bits, dup, extra);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hextra, extra, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_error(std::string("join: ") + cudaGetErrorString(e));
+    return RINGO_ECUDA;
+  }
+  ks->bits = bits;
+  ks->kmin = kmin;
+  ks->range = range;
+  if (hextra) {  // at most hextra distinct keys repeat
+    const uint32_t dslots = hash_of(hextra);
+    unsigned long long* table = (unsigned long long*)alloc(8ull * dslots);
+    if (!table) return RINGO_ENOMEM;
+    if (cudaMemsetAsync(table, 0, 8ull * dslots, s) != cudaSuccess) return RINGO_ECUDA;
+    {
+      ProfScope ps("join_build", s);
+      k_hash_dup<<<kg, 256, 0, s>>>(keys, nkeys, kmin, dup, table, dslots - 1);
+    }
+    ks->dup = dup;
+    ks->table = table;
+    ks->mask = dslots - 1;
+  }
+  return RINGO_OK;
+}
+
 int run_join(const int32_t* src, const int32_t* dst, uint32_t n, int col, const int32_t* keys,
              uint32_t nkeys, int32_t* out_src, int32_t* out_dst, uint64_t cap, cudaStream_t s,
              uint64_t* n_out) {
   *n_out = 0;
   if (n == 0 || nkeys == 0) return RINGO_OK;
-  uint32_t slots = 1;
-  while (slots < 2u * nkeys) slots <<= 1;  // load factor at most 1/2
-  const uint32_t mask = slots - 1;
-  unsigned long long* table = (unsigned long long*)pool_alloc(8ull * slots + 256, s);
-  if (!table) return RINGO_ENOMEM;
-  unsigned long long* total = table + slots;
-  int rc = RINGO_OK;
-  cudaError_t e = cudaMemsetAsync(table, 0, 8ull * slots + 8, s);
-  const uint32_t kg = (nkeys + 255) / 256 < 8192 ? (nkeys + 255) / 256 : 8192;
-  const uint32_t ng = (n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192;
-  unsigned long long htotal = 0;
+  std::vector<void*> owned;
+  auto done = [&](int rc) {
+    for (void* p : owned) pool_free(p, s);
+    return rc;
+  };
+  KeySet ks;
+  if (int rc = build_keyset(keys, nkeys, s, &ks, &owned)) return done(rc);
+  // marking pass: per-row flags, tile offsets, total
+  const uint32_t tiles = (n + kOpTile - 1) / kOpTile;
+  uint2* flags = (uint2*)pool_alloc((size_t)tiles * kOpTile / 4 + 256, s);  // 2 bits per row
+  if (!flags) return done(RINGO_ENOMEM);
+  owned.push_back(flags);
+  uint64_t* tile_off = (uint64_t*)pool_alloc(8ull * tiles + 256, s);
+  if (!tile_off) return done(RINGO_ENOMEM);
+  owned.push_back(tile_off);
+  CompactScratch cs;
+  if (int rc = compact_scratch(n, s, &cs)) return done(rc);
+  owned.push_back(cs.buf);
   {
-    ProfScope ps("join_build", s);
-    k_hash_build<<<kg, 256, 0, s>>>(keys, nkeys, table, mask);
+    ProfScope ps("join_mark", s);
+    k_join_mark<<<tiles, kOpThreads, 0, s>>>(col ? dst : src, n, ks, flags, tile_off, cs.sc,
+                                             cs.n_out);
   }
-  {
-    ProfScope ps("join_count", s);
-    k_join_count<<<ng, 256, 0, s>>>(col ? dst : src, n, table, mask, total);
-  }
-  if (e == cudaSuccess) e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&htotal, total, 8, cudaMemcpyDeviceToHost, s);
+  uint64_t htotal = 0;
+  uint32_t herr = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&htotal, cs.n_out, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, cs.sc.err, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     set_error(std::string("join: ") + cudaGetErrorString(e));
-    pool_free(table, s);
-    return RINGO_ECUDA;
+    return done(RINGO_ECUDA);
+  }
+  if (herr) {
+    set_error("join: a bounded device wait expired");
+    return done(RINGO_ETIMEOUT);
   }
   *n_out = htotal;
   if (htotal > cap || htotal > 0x7FFFFFFFull) {
     set_error("join: the output has more rows than cap (or 2^31 - 1); nothing written");
-    pool_free(table, s);
-    return RINGO_ERANGE;
+    return done(RINGO_ERANGE);
   }
   if (htotal) {
-    CompactScratch cs;
-    rc = compact_scratch(n, s, &cs);
-    if (rc == RINGO_OK) {
-      const uint32_t tiles = (n + kOpTile - 1) / kOpTile;
-      {
-        ProfScope ps("join_write", s);
-        k_compact<1><<<tiles, kOpThreads, 0, s>>>(const_cast<int32_t*>(src),
-                                                  const_cast<int32_t*>(dst), n, col, 0, 0, table,
-                                                  mask, out_src, out_dst, cs.sc, cs.n_out);
-      }
-      uint32_t herr = 0;
-      e = cudaGetLastError();
-      if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, cs.sc.err, 4, cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) {
-        set_error(std::string("join: ") + cudaGetErrorString(e));
-        rc = RINGO_ECUDA;
-      } else if (herr) {
-        set_error("join: a bounded device wait expired");
-        rc = RINGO_ETIMEOUT;
-      }
-      pool_free(cs.buf, s);
+    {
+      ProfScope ps("join_write", s);
+      k_join_write<<<tiles, kOpThreads, 0, s>>>(src, dst, n, col, ks, flags, tile_off, htotal,
+                                                out_src, out_dst);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error(std::string("join: ") + cudaGetErrorString(e));
+      return done(RINGO_ECUDA);
     }
   }
-  pool_free(table, s);
-  return rc;
+  return done(RINGO_OK);
 }
 
 }  // namespace ringo

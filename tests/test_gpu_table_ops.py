@@ -54,6 +54,64 @@ def test_join_sizes(n, nk):
         assert np.array_equal(gs.cpu().numpy(), ws) and np.array_equal(gd.cpu().numpy(), wd)
 
 
+def gpu_join(s, d, col, keys):
+    ts, td = torch.as_tensor(np.ascontiguousarray(s, np.int32)).cuda(), \
+        torch.as_tensor(np.ascontiguousarray(d, np.int32)).cuda()
+    gs, gd = ringo.ringo_table_join(ts, td, col, torch.as_tensor(np.ascontiguousarray(keys, np.int32)).cuda())
+    return gs.cpu().numpy(), gd.cpu().numpy()
+
+
+@pytest.mark.parametrize("dups", [False, True])
+def test_join_bitmap_key_set(dups):
+    # 700K keys in a 10M-wide range: the bitmap is smaller than the hash table,
+    # so the key set is a bitmap (plus a hash table of repeated keys' counts);
+    # rows just outside the range and at both ends of it
+    rng = np.random.default_rng(11 + dups)
+    keys = rng.choice(np.arange(-5_000_000, 5_000_001, dtype=np.int32), 700_000, replace=False)
+    keys[:2] = (-5_000_000, 5_000_000)
+    if dups:
+        keys = np.concatenate([keys, keys[1000:1500], keys[1000:1100], keys[:1]])
+    n = 1_000_003
+    s = rng.integers(-6_000_000, 6_000_000, n).astype(np.int32)
+    d = rng.integers(-6_000_000, 6_000_000, n).astype(np.int32)
+    s[:4] = (-5_000_001, -5_000_000, 5_000_000, 5_000_001)
+    d[-4:] = (-5_000_001, -5_000_000, 5_000_000, 5_000_001)
+    s[100:200] = keys[1000:1100]  # keys met up to three times
+    for col in (0, 1):
+        gs, gd = gpu_join(s, d, col, keys)
+        ws, wd = oracle.table_join(s, d, col, keys)
+        assert np.array_equal(gs, ws) and np.array_equal(gd, wd), col
+
+
+def test_join_large_hash_key_set_full_range():
+    # 1.2M keys over the whole int32 range (a bitmap would be larger than the
+    # hash table), both extremes among the keys and the rows
+    rng = np.random.default_rng(12)
+    keys = rng.integers(-2**31, 2**31 - 1, 1_200_000, dtype=np.int64).astype(np.int32)
+    keys[:2] = (-2**31, 2**31 - 1)
+    n = 600_001
+    s = np.concatenate([rng.choice(keys, n // 2), rng.integers(-2**31, 2**31 - 1, n - n // 2)]).astype(np.int32)
+    rng.shuffle(s)
+    s[:2] = (-2**31, 2**31 - 1)
+    d = rng.integers(-2**31, 2**31 - 1, n).astype(np.int32)
+    gs, gd = gpu_join(s, d, 0, keys)
+    ws, wd = oracle.table_join(s, d, 0, keys)
+    assert np.array_equal(gs, ws) and np.array_equal(gd, wd)
+
+
+def test_join_cap_too_small_writes_nothing_bitmap():
+    import ctypes
+    keys = torch.arange(0, 1_400_000, 2, dtype=torch.int32, device="cuda")  # bitmap key set
+    s = torch.arange(2_000_000, dtype=torch.int32, device="cuda")
+    out = torch.full((10,), -1, dtype=torch.int32, device="cuda")
+    n = ctypes.c_int64()
+    rc = ringo.load().ringo_table_join(s.data_ptr(), s.data_ptr(), s.numel(), 0, keys.data_ptr(),
+                                       keys.numel(), out.data_ptr(), out.data_ptr(), 10,
+                                       ctypes.byref(n), None)
+    assert rc == ringo.RINGO_ERANGE and n.value == 700_000
+    assert out.tolist() == [-1] * 10
+
+
 def test_join_cap_too_small_writes_nothing():
     import ctypes
     s = torch.arange(100, dtype=torch.int32, device="cuda")
