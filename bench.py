@@ -505,24 +505,31 @@ def run_select_join(args, src, dst, stream) -> dict:
     ws, wd = torch.empty_like(src), torch.empty_like(dst)
     out = {}
 
-    def timed(fn, runs=3):
+    splits = {}
+
+    def timed(fn, runs=3, name=None):
         ms = []
         for r in range(runs + 1):
             ws.copy_(src)
             wd.copy_(dst)
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if r:
+                ringo.ringo_profile_start()
             a.record(stream)
             res = fn()
             b.record(stream)
             torch.cuda.synchronize()
             if r:
                 ms.append(a.elapsed_time(b))
+                for p in ringo.ringo_profile_stop():  # per-kernel device time, summed over runs
+                    splits.setdefault(name, {}).setdefault(p["name"], 0.0)
+                    splits[name][p["name"]] += p["total_ms"] / runs
         return res, statistics.median(ms)
 
     paper = PAPER_TABLE_OPS_S.get(args.workload, {})
-    n1, ms1 = timed(lambda: ringo.ringo_table_select(ws, wd, 0, "<", lo_val))
-    n2, ms2 = timed(lambda: ringo.ringo_table_select(ws, wd, 0, ">=", lo_val))
+    n1, ms1 = timed(lambda: ringo.ringo_table_select(ws, wd, 0, "<", lo_val), name="select_10k")
+    n2, ms2 = timed(lambda: ringo.ringo_table_select(ws, wd, 0, ">=", lo_val), name="select_all_but_10k")
     cap = N
     js, jd = torch.empty_like(src), torch.empty_like(dst)
 
@@ -535,14 +542,15 @@ def run_select_join(args, src, dst, stream) -> dict:
         assert rc == 0, rc
         return n.value
 
-    n3, ms3 = timed(lambda: join(keys_small))
-    n4, ms4 = timed(lambda: join(keys_large))
+    n3, ms3 = timed(lambda: join(keys_small), name="join_10k")
+    n4, ms4 = timed(lambda: join(keys_large), name="join_all_but_10k")
     for name, rows, ms, in_rows in (("select_10k", n1, ms1, N), ("select_all_but_10k", n2, ms2, N),
                                     ("join_10k", n3, ms3, N + keys_small.numel()),
                                     ("join_all_but_10k", n4, ms4, N + keys_large.numel())):
         p = paper.get(name)
         out[name] = {"ms": round(ms, 3), "output_rows": rows, "rows_per_s": in_rows / (ms / 1e3),
-                     "input_rows": in_rows, "paper_s": p, "vs_paper": (p * 1e3 / ms) if p else None}
+                     "input_rows": in_rows, "paper_s": p, "vs_paper": (p * 1e3 / ms) if p else None,
+                     "kernel_ms": {k: round(v, 3) for k, v in splits.get(name, {}).items()}}
     del ws, wd, js, jd
     torch.cuda.empty_cache()
     out["note"] = ("median of 3 runs; select runs in place on a fresh copy each time; join rows/s "

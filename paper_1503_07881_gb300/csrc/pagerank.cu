@@ -85,7 +85,7 @@ __device__ __forceinline__ Run run_cat(const Run& a, const Run& b) {
 // in-edges lie inside the tile; part[2t] = the tile's share of its first node
 // when that node starts in an earlier tile, part[2t + 1] = the share of its
 // last node when that node goes on past the tile.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 5)
     k_pr_edges(const int64_t* __restrict__ in_off, const int32_t* __restrict__ in_nbr, uint32_t V,
                uint64_t E, const uint32_t* __restrict__ tnode, const double* __restrict__ contrib,
                double* __restrict__ sum, double* __restrict__ part) {
@@ -100,16 +100,15 @@ __global__ void __launch_bounds__(256)
   const uint32_t len = (uint32_t)(E - e0 < kPrTile ? E - e0 : kPrTile);
   const uint64_t e1 = e0 + len;
   const uint32_t r0 = tnode[2 * t], r1 = tnode[2 * t + 1];
-  // contributions of the tile's edges (0 past its end), node-start marks cleared
+  // where the first node starts and the last one ends: only these two can be
+  // cut by the tile's edges
+  const uint64_t a_first = (uint64_t)in_off[r0], b_last = (uint64_t)in_off[r1 + 1];
+  // the tile's in-neighbours (loads in flight while the marks are placed)
+  uint32_t u[kPrPer];
 #pragma unroll
   for (uint32_t q = 0; q < kPrPer; ++q) {
     const uint32_t i = q * 256 + tid;
-    double c = 0.0;
-    if (i < len) {
-      const uint32_t u = (uint32_t)__ldcs(in_nbr + e0 + i);
-      c = u < V ? __ldg(contrib + u) : 0.0;
-    }
-    s_c[pad8(i)] = c;
+    u[q] = i < len ? (uint32_t)__ldcs(in_nbr + e0 + i) : 0xFFFFFFFFu;
     s_own[pad8(i)] = 0;
   }
   __syncthreads();
@@ -119,6 +118,9 @@ __global__ void __launch_bounds__(256)
     const uint64_t p = (uint64_t)in_off[r] - e0;
     if (p < len) atomicMax(&s_own[pad8((uint32_t)p)], (int32_t)(r - r0));
   }
+  // contributions of the tile's edges (0 past its end)
+#pragma unroll
+  for (uint32_t q = 0; q < kPrPer; ++q) s_c[pad8(q * 256 + tid)] = u[q] < V ? __ldg(contrib + u[q]) : 0.0;
   __syncthreads();
   // inclusive max-scan of the marks: key[j] = node of position 8 tid + j
   const uint32_t base = tid * kPrPer;
@@ -187,13 +189,16 @@ __global__ void __launch_bounds__(256)
     acc += val[j];
     const int32_t kn = j + 1 < kPrPer ? key[j + 1] : next;
     if (kn != key[j]) {
+      // a node after the first starts inside the tile, a node before the
+      // last ends inside it
       const uint32_t v = r0 + (uint32_t)key[j];
-      const uint64_t a = (uint64_t)in_off[v], b = (uint64_t)in_off[v + 1];
-      if (a >= e0 && b <= e1) {
+      const bool cut_before = key[j] == 0 && a_first < e0;
+      const bool cut_after = v == r1 && b_last > e1;
+      if (!cut_before && !cut_after) {
         sum[v] = acc;
       } else {
-        if (a < e0) part[2 * t] = acc;
-        if (b > e1) part[2 * t + 1] = acc;
+        if (cut_before) part[2 * t] = acc;
+        if (cut_after) part[2 * t + 1] = acc;
       }
       acc = 0.0;
     }

@@ -38,6 +38,8 @@ constexpr uint32_t kOpTile = kOpThreads * kOpItems;  // 4096 rows
 // a join's key hash table up to this size stays in cache; above it, a bitmap
 // over the key range is used when that is smaller
 constexpr uint64_t kJoinHashCacheBytes = 8ull << 20;
+// a join's key hash table up to this many slots is copied into shared memory
+constexpr uint32_t kJoinSmemSlots = 2048;
 
 struct OpScan {
   uint64_t* status;  // [tiles]
@@ -62,8 +64,7 @@ __device__ __forceinline__ uint32_t hash_slot(int32_t k, uint32_t mask) {
 }
 
 // multiplicity of k in the hash table (0 if absent)
-__device__ __forceinline__ uint32_t lookup(const unsigned long long* __restrict__ table, uint32_t mask,
-                                           int32_t k) {
+__device__ __forceinline__ uint32_t lookup(const unsigned long long* table, uint32_t mask, int32_t k) {
   uint32_t h = hash_slot(k, mask);
   for (uint32_t probe = 0; probe <= mask; ++probe) {
     const unsigned long long slot = table[h];
@@ -173,51 +174,146 @@ __global__ void k_hash_dup(const int32_t* __restrict__ keys, uint32_t nkeys, int
   }
 }
 
-// Join, marking pass: one 4096-row tile per block, claimed in order; warp w
-// reads rows [tile * 4096 + 512 w, + 512), 32 per step.  flags[(tile * 8 + w)
-// * 16 + step] = (rows whose key occurs, rows whose key occurs more than
-// once) as lane bitmasks; tile_off[tile] = output rows of all earlier tiles
-// (two-level decoupled look-back over 62-bit sums), *n_out the total.
+// Key-set forms of the join's marking pass.
+enum JoinMode { kJoinSmemHash = 0, kJoinBitmap = 1, kJoinHash = 2 };
+
+// 16-bit filter index of a key (multiplicative hashing, top bits)
+__device__ __forceinline__ uint32_t filter_bit(int32_t k) { return ((uint32_t)k * 0x9E3779B1u) >> 16; }
+
+// Join, marking pass: persistent blocks take 4096-row tiles in a fixed
+// stride (no tile waits on another); warp w reads rows [tile * 4096 + 512 w,
+// + 512), 32 per step.  flags[(tile * 8 + w) * 16 + step] = (rows whose key
+// occurs, rows whose key occurs more than once) as lane bitmasks;
+// tile_cnt[tile] = the tile's output rows.
+//   kJoinSmemHash: a hash table of at most kJoinSmemSlots slots, copied into
+//     shared memory with a 64K-bit filter of its keys; most absent keys cost
+//     one filter test;
+//   kJoinBitmap / kJoinHash: the key set in global memory, the first access
+//     of all 16 rows of a thread issued before any is used.
+template <int kMode>
 __global__ void __launch_bounds__(kOpThreads)
     k_join_mark(const int32_t* __restrict__ keycol, uint32_t n, KeySet ks, uint2* __restrict__ flags,
-                uint64_t* __restrict__ tile_off, OpScan sc, uint64_t* n_out) {
+                uint64_t* __restrict__ tile_cnt) {
   constexpr int kWarps = kOpThreads / 32;
-  __shared__ unsigned long long s_w[kWarps];
-  __shared__ uint32_t s_tile;
+  constexpr bool kSmem = kMode == kJoinSmemHash;
+  __shared__ unsigned long long s_tab[kSmem ? kJoinSmemSlots : 1];
+  __shared__ uint32_t s_filter[kSmem ? 2048 : 1];
+  __shared__ unsigned long long s_w[2][kWarps];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(sc.counter, 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const uint32_t ntiles = (n + kOpTile - 1) / kOpTile;
-  if (tile >= ntiles) return;
-  const uint32_t base = tile * kOpTile + (uint32_t)warp * (32 * kOpItems) + (uint32_t)lane;
-  int32_t k[kOpItems];
-#pragma unroll
-  for (int q = 0; q < kOpItems; ++q) {
-    const uint32_t r = base + 32u * q;
-    k[q] = r < n ? keycol[r] : 0;
-  }
-  unsigned long long mine = 0;
-  uint2* wf = flags + ((size_t)tile * kWarps + warp) * kOpItems;
-#pragma unroll
-  for (int q = 0; q < kOpItems; ++q) {
-    const uint32_t r = base + 32u * q;
-    const uint32_t m = r < n ? multiplicity(ks, k[q]) : 0u;
-    const uint32_t once = __ballot_sync(0xFFFFFFFFu, m != 0u);
-    const uint32_t more = __ballot_sync(0xFFFFFFFFu, m > 1u);
-    if (lane == 0) wf[q] = make_uint2(once, more);
-    mine += m;
-  }
-  mine = warp_sum(mine);
-  if (lane == 0) s_w[warp] = mine;
-  __syncthreads();
-  if (warp == 0) {
-    const unsigned long long total = warp_sum(lane < kWarps ? s_w[lane] : 0ull);
-    const uint64_t excl = scan_prefix(sc.status, sc.ch, tile, ntiles, (uint64_t)total, sc.err);
-    if (lane == 0) {
-      tile_off[tile] = excl;
-      if (tile == ntiles - 1) *n_out = excl + total;
+  if constexpr (kSmem) {
+    for (uint32_t i = tid; i < 2048; i += kOpThreads) s_filter[i] = 0;
+    __syncthreads();
+    for (uint32_t i = tid; i <= ks.mask; i += kOpThreads) {
+      const unsigned long long v = ks.table[i];
+      s_tab[i] = v;
+      if ((uint32_t)v) {
+        const uint32_t f = filter_bit((int32_t)(v >> 32));
+        atomicOr(&s_filter[f >> 5], 1u << (f & 31));
+      }
     }
+    __syncthreads();
+  }
+  const uint32_t ntiles = (n + kOpTile - 1) / kOpTile;
+  int buf = 0;
+  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, buf ^= 1) {
+    const uint32_t base = tile * kOpTile + (uint32_t)warp * (32 * kOpItems) + (uint32_t)lane;
+    int32_t k[kOpItems];
+#pragma unroll
+    for (int q = 0; q < kOpItems; ++q) {
+      const uint32_t r = base + 32u * q;
+      k[q] = r < n ? keycol[r] : 0;
+    }
+    uint32_t m[kOpItems];
+    if constexpr (kMode == kJoinSmemHash) {
+#pragma unroll
+      for (int q = 0; q < kOpItems; ++q) {
+        const uint32_t f = filter_bit(k[q]);
+        m[q] = 0u;
+        if (base + 32u * q < n && ((s_filter[f >> 5] >> (f & 31)) & 1u)) m[q] = lookup(s_tab, ks.mask, k[q]);
+      }
+    } else if constexpr (kMode == kJoinBitmap) {
+#pragma unroll
+      for (int q = 0; q < kOpItems; ++q) {
+        const uint64_t off = (uint64_t)((int64_t)k[q] - ks.kmin);
+        m[q] = base + 32u * q < n && off < ks.range ? __ldg(ks.bits + (off >> 5)) : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < kOpItems; ++q) {
+        const uint64_t off = (uint64_t)((int64_t)k[q] - ks.kmin);
+        m[q] = (m[q] >> (off & 31)) & 1u;
+        if (m[q] && ks.dup && ((__ldg(ks.dup + (off >> 5)) >> (off & 31)) & 1u))
+          m[q] = lookup(ks.table, ks.mask, k[q]);
+      }
+    } else {
+      unsigned long long sl[kOpItems];
+#pragma unroll
+      for (int q = 0; q < kOpItems; ++q)
+        sl[q] = base + 32u * q < n ? ks.table[hash_slot(k[q], ks.mask)] : 0ull;
+#pragma unroll
+      for (int q = 0; q < kOpItems; ++q) {
+        if ((uint32_t)sl[q] == 0u) m[q] = 0u;  // empty first slot (or past the end)
+        else if ((uint32_t)(sl[q] >> 32) == (uint32_t)k[q]) m[q] = (uint32_t)sl[q];
+        else m[q] = lookup(ks.table, ks.mask, k[q]);  // collision: probe on
+      }
+    }
+    unsigned long long mine = 0;
+    uint2* wf = flags + ((size_t)tile * kWarps + warp) * kOpItems;
+#pragma unroll
+    for (int q = 0; q < kOpItems; ++q) {
+      const uint32_t once = __ballot_sync(0xFFFFFFFFu, m[q] != 0u);
+      const uint32_t more = __ballot_sync(0xFFFFFFFFu, m[q] > 1u);
+      if (lane == 0) wf[q] = make_uint2(once, more);
+      mine += m[q];
+    }
+    mine = warp_sum(mine);
+    if (lane == 0) s_w[buf][warp] = mine;
+    __syncthreads();  // s_w[buf] is written again only after the next barrier
+    if (tid == 0) {
+      unsigned long long t = 0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) t += s_w[buf][w];
+      tile_cnt[tile] = t;
+    }
+  }
+}
+
+// tile_off[i] = cnt[0] + .. + cnt[i - 1] for i < ntiles, *total = the sum:
+// blocks of 4096 counts (16 consecutive per thread), claimed in order, with
+// the two-level decoupled look-back across blocks
+__global__ void __launch_bounds__(kOpThreads)
+    k_scan_counts(const uint64_t* __restrict__ cnt, uint32_t ntiles, uint64_t* __restrict__ tile_off,
+                  OpScan sc, uint64_t* total) {
+  __shared__ uint64_t s_sw[kOpThreads / 32 + 1];
+  __shared__ uint32_t s_blk;
+  __shared__ uint64_t s_prefix;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_blk = atomicAdd(sc.counter, 1u);
+  __syncthreads();
+  const uint32_t blk = s_blk;
+  const uint32_t nblk = (ntiles + kOpTile - 1) / kOpTile;
+  if (blk >= nblk) return;
+  const uint32_t i0 = blk * kOpTile + (uint32_t)tid * kOpItems;
+  uint64_t c[kOpItems], mine = 0;
+#pragma unroll
+  for (int q = 0; q < kOpItems; ++q) {
+    c[q] = i0 + q < ntiles ? cnt[i0 + q] : 0ull;
+    mine += c[q];
+  }
+  uint64_t btotal;
+  uint64_t run = block_exclusive_sum<kOpThreads>(mine, s_sw, btotal);
+  if (tid < 32) {
+    const uint64_t excl = scan_prefix(sc.status, sc.ch, blk, nblk, btotal, sc.err);
+    if (tid == 0) {
+      s_prefix = excl;
+      if (blk == nblk - 1) *total = excl + btotal;
+    }
+  }
+  __syncthreads();
+  run += s_prefix;
+#pragma unroll
+  for (int q = 0; q < kOpItems; ++q) {
+    if (i0 + q < ntiles) tile_off[i0 + q] = run;
+    run += c[q];
   }
 }
 
@@ -506,21 +602,35 @@ int run_join(const int32_t* src, const int32_t* dst, uint32_t n, int col, const 
   };
   KeySet ks;
   if (int rc = build_keyset(keys, nkeys, s, &ks, &owned)) return done(rc);
-  // marking pass: per-row flags, tile offsets, total
+  // marking pass: per-row flags and per-tile counts; then the tiles' offsets
   const uint32_t tiles = (n + kOpTile - 1) / kOpTile;
   uint2* flags = (uint2*)pool_alloc((size_t)tiles * kOpTile / 4 + 256, s);  // 2 bits per row
   if (!flags) return done(RINGO_ENOMEM);
   owned.push_back(flags);
-  uint64_t* tile_off = (uint64_t*)pool_alloc(8ull * tiles + 256, s);
-  if (!tile_off) return done(RINGO_ENOMEM);
-  owned.push_back(tile_off);
+  uint64_t* tile_cnt = (uint64_t*)pool_alloc(16ull * tiles + 256, s);
+  if (!tile_cnt) return done(RINGO_ENOMEM);
+  owned.push_back(tile_cnt);
+  uint64_t* tile_off = tile_cnt + tiles;
   CompactScratch cs;
-  if (int rc = compact_scratch(n, s, &cs)) return done(rc);
+  if (int rc = compact_scratch(tiles, s, &cs)) return done(rc);
   owned.push_back(cs.buf);
   {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int mode = ks.bits ? kJoinBitmap : (ks.mask < kJoinSmemSlots ? kJoinSmemHash : kJoinHash);
+    auto kern = mode == kJoinSmemHash ? k_join_mark<kJoinSmemHash>
+                : mode == kJoinBitmap ? k_join_mark<kJoinBitmap>
+                                      : k_join_mark<kJoinHash>;
+    int per_sm = 0;  // persistent: the blocks that fit at once
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kOpThreads, 0);
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t want = (uint64_t)sms * (uint64_t)per_sm;
+    const uint32_t grid = tiles < want ? tiles : (uint32_t)want;
     ProfScope ps("join_mark", s);
-    k_join_mark<<<tiles, kOpThreads, 0, s>>>(col ? dst : src, n, ks, flags, tile_off, cs.sc,
-                                             cs.n_out);
+    kern<<<grid, kOpThreads, 0, s>>>(col ? dst : src, n, ks, flags, tile_cnt);
+    k_scan_counts<<<(tiles + kOpTile - 1) / kOpTile, kOpThreads, 0, s>>>(tile_cnt, tiles, tile_off,
+                                                                        cs.sc, cs.n_out);
   }
   uint64_t htotal = 0;
   uint32_t herr = 0;
