@@ -99,6 +99,21 @@ def test_join_large_hash_key_set_full_range():
     assert np.array_equal(gs, ws) and np.array_equal(gd, wd)
 
 
+@pytest.mark.parametrize("nk,spread", [(300, 1 << 22), (1_000_000, 1 << 22), (1_000_000, 1 << 31)])
+def test_join_many_tiles(nk, spread):
+    # 20M rows = 4883 tiles, so the scan of tile counts spans two blocks; the
+    # three key-set forms: 300 keys (shared-memory table), 1M keys within a
+    # 4M-wide range (bitmap), 1M keys over the whole range (hash table)
+    rng = np.random.default_rng(nk + spread)
+    ids = rng.choice(spread, 2_000_000, replace=False).astype(np.int64) - spread // 2
+    s = rng.choice(ids, 20_000_000).astype(np.int32)
+    d = rng.choice(ids, 20_000_000).astype(np.int32)
+    keys = np.concatenate([rng.choice(ids, nk, replace=False), rng.choice(ids, nk // 100)]).astype(np.int32)
+    gs, gd = gpu_join(s, d, 0, keys)
+    ws, wd = oracle.table_join(s, d, 0, keys)
+    assert np.array_equal(gs, ws) and np.array_equal(gd, wd)
+
+
 def test_join_cap_too_small_writes_nothing_bitmap():
     import ctypes
     keys = torch.arange(0, 1_400_000, 2, dtype=torch.int32, device="cuda")  # bitmap key set
