@@ -8,8 +8,9 @@
 // Each node's sum over its in-edges is formed in a fixed order, so the
 // result is the same on every run.  The in-edges are cut into 2048-edge
 // tiles (whatever the node boundaries):
-//   edges: a block gathers its tile's contributions into shared memory
-//          (coalesced index loads, independent gathers), finds each edge's
+//   edges: each thread of a block gathers the contributions of 8
+//          consecutive edges of the tile into registers (two 16-byte index
+//          loads, 8 independent gathers), finds each edge's
 //          node with a max-scan of node starts, and sums every node's run
 //          with a segmented scan over the threads' 8-edge runs; a node that
 //          lies inside the tile gets its sum written, a node cut by the tile
@@ -89,7 +90,6 @@ __global__ void __launch_bounds__(256, 5)
     k_pr_edges(const int64_t* __restrict__ in_off, const int32_t* __restrict__ in_nbr, uint32_t V,
                uint64_t E, const uint32_t* __restrict__ tnode, const double* __restrict__ contrib,
                double* __restrict__ sum, double* __restrict__ part) {
-  __shared__ double s_c[kPrTile + kPrTile / 8];
   __shared__ int32_t s_own[kPrTile + kPrTile / 8];
   __shared__ int32_t s_kf[256];
   __shared__ int32_t s_wm[8];
@@ -103,14 +103,22 @@ __global__ void __launch_bounds__(256, 5)
   // where the first node starts and the last one ends: only these two can be
   // cut by the tile's edges
   const uint64_t a_first = (uint64_t)in_off[r0], b_last = (uint64_t)in_off[r1 + 1];
-  // the tile's in-neighbours (loads in flight while the marks are placed)
+  // this thread's 8 consecutive in-neighbours (in flight while the marks are
+  // placed); positions past the tile's end read as no neighbour
+  const uint32_t base = tid * kPrPer;
   uint32_t u[kPrPer];
+  const int32_t* nb = in_nbr + e0 + base;
+  if (base + kPrPer <= len && (((uintptr_t)nb) & 15) == 0) {
+    const int4 x = __ldg(reinterpret_cast<const int4*>(nb));
+    const int4 y = __ldg(reinterpret_cast<const int4*>(nb) + 1);
+    u[0] = (uint32_t)x.x; u[1] = (uint32_t)x.y; u[2] = (uint32_t)x.z; u[3] = (uint32_t)x.w;
+    u[4] = (uint32_t)y.x; u[5] = (uint32_t)y.y; u[6] = (uint32_t)y.z; u[7] = (uint32_t)y.w;
+  } else {
 #pragma unroll
-  for (uint32_t q = 0; q < kPrPer; ++q) {
-    const uint32_t i = q * 256 + tid;
-    u[q] = i < len ? (uint32_t)__ldcs(in_nbr + e0 + i) : 0xFFFFFFFFu;
-    s_own[pad8(i)] = 0;
+    for (uint32_t j = 0; j < kPrPer; ++j) u[j] = base + j < len ? (uint32_t)nb[j] : 0xFFFFFFFFu;
   }
+#pragma unroll
+  for (uint32_t q = 0; q < kPrPer; ++q) s_own[pad8(q * 256 + tid)] = 0;
   __syncthreads();
   // nodes r0+1 .. r1 start inside the tile; where several start at the same
   // place (all but the last without in-edges) the last one wins
@@ -118,12 +126,12 @@ __global__ void __launch_bounds__(256, 5)
     const uint64_t p = (uint64_t)in_off[r] - e0;
     if (p < len) atomicMax(&s_own[pad8((uint32_t)p)], (int32_t)(r - r0));
   }
-  // contributions of the tile's edges (0 past its end)
+  // contributions of this thread's edges, kept in registers (0 past the end)
+  double val[kPrPer];
 #pragma unroll
-  for (uint32_t q = 0; q < kPrPer; ++q) s_c[pad8(q * 256 + tid)] = u[q] < V ? __ldg(contrib + u[q]) : 0.0;
+  for (uint32_t j = 0; j < kPrPer; ++j) val[j] = u[j] < V ? __ldg(contrib + u[j]) : 0.0;
   __syncthreads();
   // inclusive max-scan of the marks: key[j] = node of position 8 tid + j
-  const uint32_t base = tid * kPrPer;
   int32_t key[kPrPer];
   int32_t mx = 0;
 #pragma unroll
@@ -142,12 +150,10 @@ __global__ void __launch_bounds__(256, 5)
   int32_t m = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
   if (lane == 0) m = 0;
   for (uint32_t k = 0; k < warp; ++k) m = max(m, s_wm[k]);
-  double val[kPrPer];
 #pragma unroll
   for (uint32_t j = 0; j < kPrPer; ++j) {
     m = max(m, key[j]);
     key[j] = m;
-    val[j] = s_c[pad8(base + j)];
   }
   // this thread's run of its last node, then a segmented scan over threads
   Run mine;
