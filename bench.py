@@ -267,10 +267,19 @@ def run_ours(args, world, rank, local):
                 "in_off": torch.empty(V + 1, dtype=torch.int64, pin_memory=True),
                 "in_nbr": torch.empty(E, dtype=torch.int32, pin_memory=True)}
 
-        def e2e_step():
-            g = ringo.ringo_table_to_graph_host(hs, hd)
-            g.copy_to_host(outs)
+        split = {"to_graph_host_ms": 0.0, "copy_to_host_ms": 0.0, "free_ms": 0.0}
+
+        def e2e_step(record=False):
+            t0 = time.perf_counter()
+            g = ringo.ringo_table_to_graph_host(hs, hd)  # returns once V and E are known
+            t1 = time.perf_counter()
+            g.copy_to_host(outs)  # returns once the host arrays are filled
+            t2 = time.perf_counter()
             g.free()
+            if record:
+                split["to_graph_host_ms"] += (t1 - t0) * 1e3
+                split["copy_to_host_ms"] += (t2 - t1) * 1e3
+                split["free_ms"] += (time.perf_counter() - t2) * 1e3
 
         e2e_step()
         torch.cuda.synchronize()
@@ -280,12 +289,13 @@ def run_ours(args, world, rank, local):
         e2 = torch.cuda.Event(enable_timing=True)
         s2.record(stream)
         for _ in range(k2):
-            e2e_step()
+            e2e_step(record=True)
         e2.record(stream)
         torch.cuda.synchronize()
         ms2 = max_over_ranks(s2.elapsed_time(e2) / k2, world)
         e2e = {"value": N * world / (ms2 / 1e3), "unit": "edges/s", "ms_per_step": round(ms2, 3),
-               "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 4 * V + 16 * (V + 1) + 8 * E}
+               "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 4 * V + 16 * (V + 1) + 8 * E,
+               "host_split_ms": {k: round(v / k2, 2) for k, v in split.items()}}
         del hs, hd, outs
 
     # graph -> table (Section 3.4) and PageRank (Table "paralg") on the same graph
