@@ -445,8 +445,11 @@ RINGO_API int64_t ringo_clock_ns(void);
 /*
  * ringo_server_create -- starts the workers on the current device.  b stays
  * owned by the caller and must outlive the server.  cfg may be NULL
- * (defaults).  Errors: EINVAL (NULL b or out, budget <= 0, negative config
- * field), ERANGE (more than 16 workers).
+ * (defaults).  The budget is taken into the library's device memory pool
+ * once here (when the device has that much free), so requests do not wait
+ * on device memory being mapped; the pool keeps it for later calls.
+ * Errors: EINVAL (NULL b or out, budget <= 0, negative config field),
+ * ERANGE (more than 16 workers).
  */
 RINGO_API int ringo_server_create(const ringo_base* b, int64_t hbm_budget_bytes,
                                   const ringo_server_config* cfg, ringo_server** out);

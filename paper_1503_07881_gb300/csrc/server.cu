@@ -381,6 +381,17 @@ int ringo_server_create(const ringo_base* b, int64_t hbm_budget_bytes,
   cudaGetDevice(&S->device);
   S->budget_bytes = hbm_budget_bytes;
   S->cfg = c;
+  {
+    // hold the budget in the library's device pool (which keeps freed
+    // memory), so no request waits on device memory being mapped; skipped
+    // when the device cannot hold it all at once
+    void* p = pool_alloc((size_t)hbm_budget_bytes, nullptr);
+    if (p) {
+      pool_free(p, nullptr);
+      cudaStreamSynchronize(nullptr);
+    }
+    cudaGetLastError();
+  }
   for (int i = 0; i < c.workers; ++i) S->workers.emplace_back(worker_main, S);
   *out = S;
   return RINGO_OK;
