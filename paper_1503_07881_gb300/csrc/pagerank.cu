@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(256, 5)
   uint32_t u[kPrPer];
   const int32_t* nb = in_nbr + e0 + base;
   if (base + kPrPer <= len && (((uintptr_t)nb) & 15) == 0) {
-    const int4 x = __ldg(reinterpret_cast<const int4*>(nb));
-    const int4 y = __ldg(reinterpret_cast<const int4*>(nb) + 1);
+    const int4 x = __ldcs(reinterpret_cast<const int4*>(nb));  // streamed: keep L2 for contrib
+    const int4 y = __ldcs(reinterpret_cast<const int4*>(nb) + 1);
     u[0] = (uint32_t)x.x; u[1] = (uint32_t)x.y; u[2] = (uint32_t)x.z; u[3] = (uint32_t)x.w;
     u[4] = (uint32_t)y.x; u[5] = (uint32_t)y.y; u[6] = (uint32_t)y.z; u[7] = (uint32_t)y.w;
   } else {

@@ -104,8 +104,9 @@ __global__ void __launch_bounds__(256)
         const uint64_t e = e0 + t;
         const uint32_t r = r0 + (uint32_t)s_own[pad8(t)];
         const int32_t mm = __ldcs(nbr + e);
-        key[e] = node_ids[r];
-        val[e] = (uint32_t)mm < V ? __ldg(node_ids + mm) : 0;
+        // streaming stores, so the written columns do not push node_ids out of L2
+        __stcs(key + e, node_ids[r]);
+        __stcs(val + e, (uint32_t)mm < V ? __ldg(node_ids + mm) : 0);
       }
     } else {  // the tile spans more nodes than the window: search per edge
       for (uint64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
