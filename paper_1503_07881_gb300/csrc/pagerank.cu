@@ -155,14 +155,43 @@ __global__ void __launch_bounds__(256, 5)
     m = max(m, key[j]);
     key[j] = m;
   }
-  // this thread's run of its last node, then a segmented scan over threads
+  // a node's share of the tile goes to its sum, or to one of the tile's two
+  // slots when the tile's edges cut the node (only the first and the last
+  // node can be cut: a node after the first starts inside the tile, a node
+  // before the last ends inside it)
+  auto emit = [&](int32_t k, double x) {
+    const uint32_t v = r0 + (uint32_t)k;
+    const bool cut_before = k == 0 && a_first < e0;
+    const bool cut_after = v == r1 && b_last > e1;
+    if (!cut_before && !cut_after) {
+      sum[v] = x;
+    } else {
+      if (cut_before) part[2 * t] = x;
+      if (cut_after) part[2 * t + 1] = x;
+    }
+  };
+  // the runs of this thread's 8 edges, one add per edge: a run that both
+  // starts and ends here is complete now; the first run may continue one of
+  // earlier threads (`head`), the last may go on into later ones (`acc`)
+  double head = 0.0, acc = val[0];
+  bool closed = false;  // the first run ended inside this thread
+#pragma unroll
+  for (uint32_t j = 0; j + 1 < kPrPer; ++j) {
+    if (key[j + 1] != key[j]) {
+      if (closed) emit(key[j], acc);
+      else head = acc;
+      closed = true;
+      acc = val[j + 1];
+    } else {
+      acc += val[j + 1];
+    }
+  }
+  // segmented scan over threads of (first node, last node, sum of the last
+  // node's positions)
   Run mine;
   mine.kf = key[0];
   mine.kl = key[kPrPer - 1];
-  mine.tail = 0.0;
-#pragma unroll
-  for (uint32_t j = 0; j < kPrPer; ++j)
-    if (key[j] == mine.kl) mine.tail += val[j];
+  mine.tail = acc;
   Run inc = mine;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -188,26 +217,12 @@ __global__ void __launch_bounds__(256, 5)
   prev.tail = __shfl_up_sync(0xFFFFFFFFu, inc.tail, 1);
   if (lane > 0) before = warp == 0 ? prev : run_cat(before, prev);
   const int32_t next = tid + 1 < 256 ? s_kf[tid + 1] : 0x7FFFFFFF;  // node after this thread
-  // every run that ends in this thread's positions gives one node's share
-  double acc = before.kl == key[0] ? before.tail : 0.0;
-#pragma unroll
-  for (uint32_t j = 0; j < kPrPer; ++j) {
-    acc += val[j];
-    const int32_t kn = j + 1 < kPrPer ? key[j + 1] : next;
-    if (kn != key[j]) {
-      // a node after the first starts inside the tile, a node before the
-      // last ends inside it
-      const uint32_t v = r0 + (uint32_t)key[j];
-      const bool cut_before = key[j] == 0 && a_first < e0;
-      const bool cut_after = v == r1 && b_last > e1;
-      if (!cut_before && !cut_after) {
-        sum[v] = acc;
-      } else {
-        if (cut_before) part[2 * t] = acc;
-        if (cut_after) part[2 * t + 1] = acc;
-      }
-      acc = 0.0;
-    }
+  const bool carried = before.kl == key[0];  // the first run started in an earlier thread
+  if (closed) {
+    emit(key[0], carried ? before.tail + head : head);
+    if (next != key[kPrPer - 1]) emit(key[kPrPer - 1], acc);
+  } else if (next != key[0]) {  // one run over all 8 edges, ending here
+    emit(key[0], carried ? before.tail + acc : acc);
   }
 }
 
