@@ -17,9 +17,11 @@
 //          edges leaves a partial sum in the tile's two slots;
 //   fix-up: one warp per node that ends in a tile it did not start in adds
 //          its partial sums in tile order;
-//   nodes: PR(v), the next contributions PR(v) / outdeg(v), and per-block
-//          sums of PR over nodes without out-edges, reduced in a fixed order.
-// The first and last node of every tile are found once per call.
+//   nodes: PR(v), the next contributions PR(v) * (1 / outdeg(v)), and
+//          per-block sums of PR over nodes without out-edges, reduced in a
+//          fixed order.
+// The first and last node of every tile and the reciprocal out-degrees are
+// found once per call.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -249,9 +251,19 @@ __global__ void k_pr_fixup(const int64_t* __restrict__ in_off, uint64_t E,
   }
 }
 
+// inv_od[v] = 1 / outdeg(v), 0 for a node without out-edges (once per call:
+// an fp64 division costs many times a multiplication on this part)
+__global__ void k_pr_inv_outdeg(const int64_t* __restrict__ out_off, uint32_t V,
+                                double* __restrict__ inv_od) {
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+    const int64_t od = out_off[v + 1] - out_off[v];
+    inv_od[v] = od > 0 ? 1.0 / (double)od : 0.0;
+  }
+}
+
 // New ranks; next contributions; block sums of dangling rank.
 __global__ void __launch_bounds__(256)
-    k_pr_nodes(const int64_t* __restrict__ out_off, uint32_t V, double damping, int first,
+    k_pr_nodes(const double* __restrict__ inv_od, uint32_t V, double damping, int first,
                const PrState* __restrict__ st, double* __restrict__ pr, double* __restrict__ sum,
                double* __restrict__ contrib, double* __restrict__ partial) {
   __shared__ double s_w[8];
@@ -261,9 +273,9 @@ __global__ void __launch_bounds__(256)
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
     const double p = first ? inv_v : base + damping * sum[v];
     pr[v] = p;
-    const int64_t od = out_off[v + 1] - out_off[v];
-    contrib[v] = od > 0 ? p / (double)od : 0.0;
-    if (od == 0) dang += p;
+    const double inv = inv_od[v];
+    contrib[v] = p * inv;
+    if (inv == 0.0) dang += p;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dang += __shfl_xor_sync(0xFFFFFFFFu, dang, o);
@@ -295,10 +307,11 @@ int run_pagerank(const int64_t* out_off, const int64_t* in_off, const int32_t* i
                  uint64_t E, double damping, int32_t iterations, double* rank, cudaStream_t s) {
   if (V == 0) return RINGO_OK;
   // scratch: contrib[V], sum[V] (zero: nodes without in-edges keep 0), node
-  // partials[kNodeGrid], state, tile shares[2 * tiles], tile nodes[2 * tiles]
+  // partials[kNodeGrid], state, tile shares[2 * tiles], tile nodes[2 * tiles],
+  // 1 / outdeg[V]
   const uint64_t tiles = (E + kPrTile - 1) / kPrTile;
   if (tiles > 0x7FFFFFFFull) return RINGO_ERANGE;
-  const size_t bytes = 16 * (size_t)V + 8 * kNodeGrid + 256 + 16 * tiles + 8 * tiles + 64;
+  const size_t bytes = 24 * (size_t)V + 8 * kNodeGrid + 256 + 16 * tiles + 8 * tiles + 64;
   char* buf = (char*)pool_alloc(bytes, s);
   if (!buf) return RINGO_ENOMEM;
   double* contrib = (double*)buf;
@@ -307,6 +320,7 @@ int run_pagerank(const int64_t* out_off, const int64_t* in_off, const int32_t* i
   PrState* st = (PrState*)(partial + kNodeGrid);
   double* part = (double*)(st + 1);
   uint32_t* tnode = (uint32_t*)(part + 2 * tiles);
+  double* inv_od = (double*)(tnode + 2 * tiles);  // 8-byte aligned: 8 * tiles bytes on
   const uint32_t node_blocks = (V + 255) / 256;
   const uint32_t node_grid = node_blocks < kNodeGrid ? node_blocks : kNodeGrid;
   const uint64_t tw = (tiles + 7) / 8;  // 8 warps per block, one tile each
@@ -314,10 +328,11 @@ int run_pagerank(const int64_t* out_off, const int64_t* in_off, const int32_t* i
   int rc = RINGO_OK;
   cudaError_t e = cudaMemsetAsync(buf, 0, bytes, s);
   if (tiles) k_pr_tile_nodes<<<tile_grid, 256, 0, s>>>(in_off, V, E, (uint32_t)tiles, tnode);
+  k_pr_inv_outdeg<<<node_grid, 256, 0, s>>>(out_off, V, inv_od);
   // iteration 0 sets the uniform vector and its contributions
   {
     ProfScope ps("pagerank_nodes", s);
-    k_pr_nodes<<<node_grid, 256, 0, s>>>(out_off, V, damping, 1, st, rank, sum, contrib, partial);
+    k_pr_nodes<<<node_grid, 256, 0, s>>>(inv_od, V, damping, 1, st, rank, sum, contrib, partial);
   }
   k_pr_reduce<<<1, 256, 0, s>>>(partial, node_grid, st);
   for (int32_t it = 0; it < iterations; ++it) {
@@ -328,7 +343,7 @@ int run_pagerank(const int64_t* out_off, const int64_t* in_off, const int32_t* i
     }
     {
       ProfScope ps("pagerank_nodes", s);
-      k_pr_nodes<<<node_grid, 256, 0, s>>>(out_off, V, damping, 0, st, rank, sum, contrib,
+      k_pr_nodes<<<node_grid, 256, 0, s>>>(inv_od, V, damping, 0, st, rank, sum, contrib,
                                            partial);
     }
     k_pr_reduce<<<1, 256, 0, s>>>(partial, node_grid, st);
