@@ -287,11 +287,15 @@ def run_ours(args, world, rank, local):
         barrier(world)
         s2 = torch.cuda.Event(enable_timing=True)
         e2 = torch.cuda.Event(enable_timing=True)
+        ringo.ringo_profile_start()
         s2.record(stream)
         for _ in range(k2):
             e2e_step(record=True)
         e2.record(stream)
         torch.cuda.synchronize()
+        for p in ringo.ringo_profile_stop():  # host-input steps of the call, per step
+            if p["name"] in ("host:input_alloc", "input_h2d"):
+                split[p["name"] + "_ms"] = p["total_ms"]
         ms2 = max_over_ranks(s2.elapsed_time(e2) / k2, world)
         e2e = {"value": N * world / (ms2 / 1e3), "unit": "edges/s", "ms_per_step": round(ms2, 3),
                "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 4 * V + 16 * (V + 1) + 8 * E,

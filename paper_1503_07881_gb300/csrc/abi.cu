@@ -35,12 +35,6 @@ namespace {
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-uint32_t next_pow2(uint64_t x) {
-  uint64_t p = 1;
-  while (p < x && p < (1ull << 31)) p <<= 1;
-  return (uint32_t)p;
-}
-
 void free_graph_arrays(ringo_graph* g) {
   pool_free(g->node_ids, g->stream);
   pool_free(g->out_off, g->stream);
@@ -287,14 +281,24 @@ static int table_to_graph_impl(const int32_t* src, const int32_t* dst, int64_t n
     rc = make_empty(g);
   } else if (host) {
     const size_t bytes = sizeof(int32_t) * (size_t)nrows;
-    int32_t* d_src = (int32_t*)pool_alloc(bytes, g->stream);
-    int32_t* d_dst = (int32_t*)pool_alloc(bytes, g->stream);
+    int32_t* d_src = nullptr;
+    int32_t* d_dst = nullptr;
+    {
+      HostScope hs("host:input_alloc");
+      d_src = (int32_t*)pool_alloc(bytes, g->stream);
+      d_dst = (int32_t*)pool_alloc(bytes, g->stream);
+    }
+    bool copied = false;
+    if (d_src && d_dst) {
+      ProfScope ps("input_h2d", g->stream);
+      copied = cudaMemcpyAsync(d_src, src, bytes, cudaMemcpyHostToDevice, g->stream) ==
+                   cudaSuccess &&
+               cudaMemcpyAsync(d_dst, dst, bytes, cudaMemcpyHostToDevice, g->stream) ==
+                   cudaSuccess;
+    }
     if (!d_src || !d_dst) {
       rc = RINGO_ENOMEM;
-    } else if (cudaMemcpyAsync(d_src, src, bytes, cudaMemcpyHostToDevice, g->stream) !=
-                   cudaSuccess ||
-               cudaMemcpyAsync(d_dst, dst, bytes, cudaMemcpyHostToDevice, g->stream) !=
-                   cudaSuccess) {
+    } else if (!copied) {
       set_error(std::string("host->device copy failed: ") +
                 cudaGetErrorString(cudaGetLastError()));
       rc = RINGO_ECUDA;
