@@ -15,6 +15,7 @@ scaling); the reported time is the max over ranks.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -790,11 +791,19 @@ def run_served(args, spec, base, rates, duration: float) -> dict:
         for p in warm:
             srv.wait(srv.submit(p, topk=SERVE_TOPK))
         srv.close()
-        server = serve_with_server(ringo, base, preds, arr, workers=args.serve_workers)
+        gc.disable()  # no collector pauses in the client's submit loop
+        try:
+            server = serve_with_server(ringo, base, preds, arr, workers=args.serve_workers)
+        finally:
+            gc.enable()
         row = {"rate_per_s": rate, "duration_s": duration, "requests": len(preds),
                "workers": args.serve_workers, "server": server}
         if not args.no_plain:
-            plain = serve_plain(ringo, base, preds, arr)
+            gc.disable()
+            try:
+                plain = serve_plain(ringo, base, preds, arr)
+            finally:
+                gc.enable()
             row["plain_loop"] = plain
             row["p99_speedup_vs_plain"] = plain["p99_ms"] / server["p99_ms"]
         out.append(row)
@@ -944,7 +953,7 @@ def main():
     ap.add_argument("--predicates", type=int, default=BATCH_PREDS)
     ap.add_argument("--serve-rates", type=lambda x: [float(v) for v in x.split(",")],
                     default=[100.0, 500.0])
-    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--serve-workers", type=int, default=1, help="server worker threads (streams)")
     args = ap.parse_args()
     if args.warmup < 3:
