@@ -152,3 +152,19 @@ def test_select_then_convert_matches_oracle():
     want = oracle.table_to_graph(*oracle.table_select(s, d, 0, "<", v))
     for k in ("node_ids", "out_off", "out_nbr", "in_off", "in_nbr"):
         assert np.array_equal(got[k], want[k])
+
+
+def test_empty_inputs():
+    e = torch.empty(0, dtype=torch.int32, device="cuda")
+    s = torch.arange(10, dtype=torch.int32, device="cuda")
+    assert ringo.ringo_table_select(e, e.clone(), 0, "<", 5) == 0
+    gs, gd = ringo.ringo_table_join(e, e.clone(), 0, torch.tensor([1, 2], dtype=torch.int32, device="cuda"))
+    assert gs.numel() == 0 and gd.numel() == 0
+    gs, gd = ringo.ringo_table_join(s, s.clone(), 1, e)  # no keys: nothing matches
+    assert gs.numel() == 0 and gd.numel() == 0
+    # nothing kept / everything kept
+    t = s.clone()
+    assert ringo.ringo_table_select(t, s.clone(), 0, ">", 100) == 0
+    t, u = s.clone(), s.clone() * 2
+    assert ringo.ringo_table_select(t, u, 1, ">=", 0) == 10
+    assert torch.equal(t, s) and torch.equal(u, s * 2)
