@@ -270,6 +270,10 @@ RINGO_API int ringo_table_select(int32_t* src, int32_t* dst, int64_t nrows, int 
  * once per occurrence, in row order, written to caller-owned device columns
  * out_src[cap], out_dst[cap].  *n_out receives the join's row count; if it
  * exceeds cap (or 2^31 - 1) nothing is written and ERANGE is returned.
+ * Device scratch during the call: 2 bits per row of the table, and the key
+ * set: an open-addressing table of at most 16 bytes per key, or, when
+ * smaller, two bitmaps over the keys' value range (at most 1 GB, for keys
+ * spanning the whole int32 range) plus a table of the repeated keys.
  * Errors: EINVAL (bad pointers, sizes or col), ERANGE (nrows >= 2^31,
  * nkeys >= 2^30, output above cap), ENOMEM, ETIMEOUT, ECUDA.
  */
