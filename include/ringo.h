@@ -271,7 +271,7 @@ RINGO_API int ringo_table_select(int32_t* src, int32_t* dst, int64_t nrows, int 
  * out_src[cap], out_dst[cap].  *n_out receives the join's row count; if it
  * exceeds cap (or 2^31 - 1) nothing is written and ERANGE is returned.
  * Device scratch during the call: 2 bits per row of the table, and the key
- * set: an open-addressing table of at most 16 bytes per key, or, when
+ * set: an open-addressing table of 16 to 32 bytes per key, or, when
  * smaller, two bitmaps over the keys' value range (at most 1 GB, for keys
  * spanning the whole int32 range) plus a table of the repeated keys.
  * Errors: EINVAL (bad pointers, sizes or col), ERANGE (nrows >= 2^31,
