@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kScanThreads, 6)
   int32_t* __restrict__ usrc_start = ctl->usrc_start;
   const int top = npos - 1;
   uint32_t ce2 = 0, cs2 = 0;  // heads of earlier items of this warp (positions recomputed)
-#pragma unroll 1
+#pragma unroll 4
   for (int i = 0; i < kScanItems; ++i) {
     const bool h = (he >> i) & 1u;
     const bool head_s = (hs >> i) & 1u;
@@ -139,7 +139,9 @@ __global__ void __launch_bounds__(kScanThreads, 6)
     const uint32_t sidx = head_s ? s : s - 1;
     ekeys[e] = ((uint64_t)db << 32) | sidx;
     out_nbr[e] = (int32_t)db;
-    for (int p = 0; p < top; ++p) atomicAdd(&s_hist[p][(db >> (8 * p)) & 0xFFu], 1u);
+#pragma unroll
+    for (int p = 0; p < kInPasses - 1; ++p)  // fixed trip count: predicated, no loop branch
+      if (p < top) atomicAdd(&s_hist[p][(db >> (8 * p)) & 0xFFu], 1u);
     if (head_s) {
       usrc[s] = unbias((uint32_t)(k >> 32));
       usrc_start[s] = (int32_t)e;
