@@ -310,7 +310,6 @@ __global__ void __launch_bounds__(256)
 // digits; node tiles of all segments share each launch.  V is read from the
 // control blocks, so the launches can be recorded before V is known.
 constexpr uint32_t kTopkTile = 4096;  // nodes per tile
-constexpr int kTopkSortMax = 4096;
 
 struct TopkTask {
   uint64_t prefix;     // digits of the k-th key fixed so far
