@@ -208,12 +208,14 @@ RINGO_API int ringo_graph_to_node_table(const ringo_graph* g, int32_t* d_ids, in
  *                               + sum of PR over nodes without out-edges / V),
  * `iterations` steps (0 gives the uniform vector), d = damping in [0, 1].
  * Writes PR in node-index order to caller-owned device d_rank[V].  Enqueued
- * on `stream` (NULL: the graph's stream); scratch of about 16 V + E / 1024
- * bytes comes from the library's pool.  Each node's sum is formed in a fixed
- * order (per-warp lanes, or fixed chunks for nodes of more than 8192
- * in-edges), so runs agree bit for bit; a sequential loop sums in another
- * order and agrees to within fp64 rounding (about max in-degree x 1e-16
- * relative per step).
+ * on `stream` (NULL: the graph's stream); scratch of about 24 V + E / 85
+ * bytes comes from the library's pool.  PR(u) / outdeg(u) is computed as
+ * PR(u) * (1 / outdeg(u)) with the reciprocal formed once.  Each node's sum
+ * is formed in a fixed order (the in-edges cut into 2048-edge tiles: runs of
+ * 8 edges per thread, a scan over the tile's threads, then the node's tile
+ * shares in tile order), so runs agree bit for bit; a sequential loop sums
+ * in another order and agrees to within fp64 rounding (about max in-degree
+ * x 1e-16 relative per step).
  * Errors: EINVAL (NULL g, NULL d_rank with V > 0, iterations < 0, damping
  * outside [0, 1]), ENOMEM, ECUDA.
  */
