@@ -197,6 +197,23 @@ def test_pagerank_closed_forms_and_conservation():
     assert abs(oracle.pagerank(g).sum() - 1.0) < 1e-12
 
 
+def test_pagerank_star_two_state_recurrence():
+    # k leaves each pointing at one hub (the hub has no out-edges): by symmetry
+    # every leaf has the same rank, so ten steps reduce to a recurrence on two
+    # numbers, evaluated here in exact rational arithmetic
+    from fractions import Fraction as F
+    k, d = 9, F(85, 100)
+    V = k + 1
+    leaf, hub = F(1, V), F(1, V)
+    for _ in range(10):
+        leaf, hub = (1 - d) / V + d * hub / V, (1 - d) / V + d * (k * leaf + hub / V)
+    s = np.arange(100, 100 + k, dtype=np.int32)  # leaves 100.., hub 5 sorts first
+    g = oracle.table_to_graph(s, np.full(k, 5, np.int32))
+    got = oracle.pagerank(g, 0.85, 10)
+    assert got[0] == pytest.approx(float(hub), rel=1e-14)
+    assert np.allclose(got[1:], float(leaf), rtol=1e-14, atol=0)
+
+
 def test_pagerank_pins_catch_dropped_dangling_mass():
     g = oracle.table_to_graph(np.array([1, 1, 3], np.int32), np.array([2, 3, 1], np.int32))
     bad = oracle.pagerank(g, drop_dangling=True)
