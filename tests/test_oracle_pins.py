@@ -280,6 +280,18 @@ def test_triangles_closed_forms():
     s = np.array([1, 2, 3, 1, 2, 3, 3, 2], np.int32)
     d = np.array([2, 3, 1, 1, 1, 3, 2, 2], np.int32)
     assert oracle.count_triangles(oracle.undirected_graph(s, d)) == 1
+    # a complete bipartite graph has none; k disjoint triangles have k; a
+    # complete graph minus one edge has C(n, 3) - (n - 2)
+    a, b = np.meshgrid(np.arange(6, dtype=np.int32), np.arange(10, 17, dtype=np.int32))
+    assert oracle.count_triangles(oracle.undirected_graph(a.ravel(), b.ravel())) == 0
+    t = np.arange(0, 300, 3, dtype=np.int32)
+    s = np.concatenate([t, t + 1, t + 2])
+    d = np.concatenate([t + 1, t + 2, t])
+    assert oracle.count_triangles(oracle.undirected_graph(s, d)) == 100
+    n = 9
+    p = [q for q in itertools.combinations(range(n), 2) if q != (2, 5)]
+    g = oracle.undirected_graph([x for x, _ in p], [y for _, y in p])
+    assert oracle.count_triangles(g) == comb(n, 3) - (n - 2)
 
 
 def test_triangle_pins_catch_planted_mistake():
