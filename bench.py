@@ -19,7 +19,6 @@ import gc
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -179,18 +178,18 @@ def sort_source_digest() -> str:
 
 
 def ncu_traffic_per_key_pass() -> float | None:
-    """DRAM bytes per key per radix pass from the committed ncu summary, if it
-    was taken on the current onesweep source."""
-    path = os.path.join(ROOT, "profiles", "onesweep_pass_lj_ncu.md")
+    """DRAM bytes per key per radix pass from the committed ncu figures
+    (profiles/sweep_traffic.json, written beside the ncu summary), if they
+    were taken on the current sort source."""
+    path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     try:
-        text = open(path).read()
-    except OSError:
+        with open(path) as f:
+            rec = json.load(f)
+        per_key = float(rec["dram_bytes_per_key_pass"])
+        digest = str(rec["source_digest"])
+    except (OSError, KeyError, ValueError, TypeError):
         return None
-    m = re.search(r"dram_bytes_per_key_pass:\s*([0-9.]+)", text)
-    d = re.search(r"source_digest:\s*([0-9a-f]+)", text)
-    if not m or not d or d.group(1) != sort_source_digest():
-        return None
-    return float(m.group(1))
+    return per_key if digest == sort_source_digest() else None
 
 
 # --------------------------------------------------------------- our arm --

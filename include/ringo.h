@@ -153,14 +153,19 @@ RINGO_API void ringo_graph_free(ringo_graph* g);
  * allocate device memory at the time of the call (a fixed memory budget
  * reserved up front, a serving loop that must not enter the allocator).
  * The paper has no counterpart: this is a property of this library only.
- *   No device or pinned host memory is allocated.  Scratch space is one
- *   fixed __device__ array inside the library (about 41 MB on every GPU that
- *   loads it, held until the process exits), so:
+ *   The call allocates no device or pinned host memory.  Scratch space is
+ *   one fixed __device__ array inside the library (about 41 MB per GPU, held
+ *   until the process exits), so:
  *   - nrows <= RINGO_NOALLOC_MAX_ROWS, else RINGO_ERANGE;
  *   - calls whose GPU work overlaps (other streams or threads) race on that
  *     array and give wrong results: callers serialise them;
- *   - the first call on each device looks up the array's device address;
- *     make that first call before any stream capture.
+ *   - the array is placed on a GPU when the library's device code is loaded
+ *     there, which (CUDA's lazy module loading being the default) is the
+ *     first call on that device: that call looks up the array's address,
+ *     takes the array's device memory, and returns RINGO_ENOMEM if there is
+ *     none left.  Make the first call per device at set-up time.
+ *   - the call blocks (two stream synchronisations, sizes read back in
+ *     between), so it cannot be used inside a stream capture.
  *   src, dst          device columns of nrows int32 IDs (borrowed)
  *   node_ids          device, node_capacity entries       } caller-owned
  *   out_off, in_off   device, node_capacity + 1 entries   } outputs, same
@@ -169,7 +174,9 @@ RINGO_API void ringo_graph_free(ringo_graph* g);
  *   node_capacity     must be >= distinct sources + distinct destinations of
  *                     the table (2 * nrows always suffices), else RINGO_ERANGE
  *   num_nodes, num_edges  host outputs: V and E
- * Blocks until the result is complete (two stream synchronisations).
+ * Returns once the result is complete.  A node_capacity that turns out too
+ * small is found after the sort (RINGO_ERANGE); the call has then written
+ * out_nbr, in_nbr and the scratch array, and the next call is unaffected.
  */
 #define RINGO_NOALLOC_MAX_ROWS (1 << 20)
 RINGO_API int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* dst, int64_t nrows,

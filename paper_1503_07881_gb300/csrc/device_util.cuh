@@ -71,6 +71,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// Barrier among the first `count` threads of the block (named barrier `id`;
+// 0 is the one __syncthreads uses).
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
 // Orders this thread's earlier generic-proxy shared-memory accesses before
 // later asynchronous-proxy (bulk copy) accesses to the same memory.
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -280,6 +288,20 @@ struct Claim {
   uint32_t tile;   // local tile of the segment
   uint32_t valid;  // 0: past the last slot
 };
+__device__ __forceinline__ Claim claim_next(SegMap m, uint32_t* counter) {
+  Claim c;
+  const uint32_t g = atomicAdd(counter, 1u);
+  if (g >= __ldg(m.start + m.nseg)) {
+    c.seg = 0;
+    c.tile = 0;
+    c.valid = 0;
+    return c;
+  }
+  c.seg = seg_of(m, g);
+  c.tile = g - __ldg(m.start + c.seg);
+  c.valid = 1;
+  return c;
+}
 __device__ __forceinline__ void claim_slot(SegMap m, uint32_t* counter, Claim* out) {
   const uint32_t g = atomicAdd(counter, 1u);
   if (g >= __ldg(m.start + m.nseg)) {

@@ -11,14 +11,19 @@
 // buffers.  It allocates no device or pinned host memory.
 //
 // The scratch array (g_noalloc_scratch, about 41 MB) exists once on every GPU
-// that loads this library and stays there until the process exits.  Its
-// address is looked up once per device (cudaGetSymbolAddress) with that
-// device current; that lookup happens on the first call on a device, which
-// should therefore come before any stream capture.  All calls share the
-// array: two calls whose work overlaps on the GPU (different streams or
-// threads) race and corrupt each other's results; callers must serialise
-// them.  The array keeps whatever the last call left in it, so each call
-// clears the parts that must start at zero.
+// where this library's device code is loaded and stays there until the
+// process exits.  With CUDA's lazy module loading (the default) that happens
+// on the first call on each device: its address is looked up then
+// (cudaGetSymbolAddress, with that device current), which makes the driver
+// load the module and place the array, so that first call does take device
+// memory and can fail with RINGO_ENOMEM when none is left.  Callers make it
+// at set-up time, while memory is still free.  Every call blocks (it
+// synchronises the stream twice and reads sizes back in between), so no call
+// can be made inside a stream capture.  All calls share the array: two calls
+// whose work overlaps on the GPU (different streams or threads) race and
+// corrupt each other's results; callers must serialise them.  The array
+// keeps whatever the last call left in it, so each call clears the parts
+// that must start at zero.
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -99,6 +104,11 @@ int scratch_address(unsigned char** out) {
     if (e != cudaSuccess || !p) {
       set_error(std::string("cudaGetSymbolAddress of the scratch array failed: ") +
                 cudaGetErrorString(e));
+      // placing the array (first call on this device) needs device memory
+      if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return RINGO_ENOMEM;
+      }
       return RINGO_ECUDA;
     }
     g_scratch_addr[dev] = (unsigned char*)p;

@@ -399,13 +399,23 @@ def ringo_table_to_graph_noalloc(src: torch.Tensor, dst: torch.Tensor, out: dict
     if src.numel() != dst.numel():
         raise ValueError("src and dst differ in length")
     n = src.numel()
+    want = {"node_ids": torch.int32, "out_off": torch.int64, "out_nbr": torch.int32,
+            "in_off": torch.int64, "in_nbr": torch.int32}
+    for name, dtype in want.items():
+        t = out.get(name)
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != dtype \
+                or not t.is_contiguous():
+            raise ValueError(f"out[{name!r}] must be a contiguous CUDA {dtype} tensor")
+    node_cap = out["node_ids"].numel()
+    if min(out["out_off"].numel(), out["in_off"].numel()) < node_cap + 1:
+        raise ValueError("out_off and in_off need node_ids.numel() + 1 entries")
     v = ctypes.c_int64()
     e = ctypes.c_int64()
     _check(load().ringo_table_to_graph_noalloc(
         _col_ptr(src, "src") if n else None, _col_ptr(dst, "dst") if n else None, n,
         _stream_ptr(stream), out["node_ids"].data_ptr(), out["out_off"].data_ptr(),
         out["out_nbr"].data_ptr(), out["in_off"].data_ptr(), out["in_nbr"].data_ptr(),
-        out["node_ids"].numel(), min(out["out_nbr"].numel(), out["in_nbr"].numel()),
+        node_cap, min(out["out_nbr"].numel(), out["in_nbr"].numel()),
         ctypes.byref(v), ctypes.byref(e)), "ringo_table_to_graph_noalloc")
     return v.value, e.value
 

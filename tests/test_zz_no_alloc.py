@@ -73,3 +73,48 @@ def test_noalloc_limits_and_empty():
     a = _noalloc_call(empty, empty)
     assert a["num_nodes"] == 0 and a["num_edges"] == 0
     assert a["out_off"].tolist() == [0] and a["in_off"].tolist() == [0]
+
+
+def test_noalloc_node_capacity_error_then_next_call_unaffected():
+    """node_capacity is checked after the sort, once the distinct source and
+    destination counts are known; the call has written scratch and the
+    neighbour buffers by then, and the next call must not notice."""
+    lib = ringo.load()
+    src, dst = tg.make_table(tg.SPECS["tiny"].scaled(20_000), seed=31, device="cuda")
+    n = src.numel()
+    bufs = [torch.empty(k, dtype=t, device="cuda") for k, t in
+            ((1, torch.int32), (2, torch.int64), (n, torch.int32), (2, torch.int64),
+             (n, torch.int32))]
+    v, e = ctypes.c_int64(), ctypes.c_int64()
+    rc = lib.ringo_table_to_graph_noalloc(
+        src.data_ptr(), dst.data_ptr(), n, torch.cuda.current_stream().cuda_stream,
+        *[b.data_ptr() for b in bufs], 1, n, ctypes.byref(v), ctypes.byref(e))
+    assert rc == ringo.RINGO_ERANGE
+    assert b"node_capacity" in lib.ringo_last_error()
+    s2, d2 = tg.signed_table(300_000, 40_000, seed=32, device="cuda")
+    _same(_noalloc_call(s2, d2), _regular(s2, d2))
+
+
+def test_noalloc_python_wrapper():
+    """The same entry point through the binding, with its argument checks."""
+    src, dst = tg.make_table(tg.SPECS["lj"].scaled(250_000), seed=33, device="cuda")
+    n = src.numel()
+    out = {"node_ids": torch.empty(2 * n, dtype=torch.int32, device="cuda"),
+           "out_off": torch.empty(2 * n + 1, dtype=torch.int64, device="cuda"),
+           "out_nbr": torch.empty(n, dtype=torch.int32, device="cuda"),
+           "in_off": torch.empty(2 * n + 1, dtype=torch.int64, device="cuda"),
+           "in_nbr": torch.empty(n, dtype=torch.int32, device="cuda")}
+    V, E = ringo.ringo_table_to_graph_noalloc(src, dst, out)
+    got = {"num_nodes": V, "num_edges": E,
+           "node_ids": out["node_ids"][:V].cpu().numpy(),
+           "out_off": out["out_off"][:V + 1].cpu().numpy(),
+           "out_nbr": out["out_nbr"][:E].cpu().numpy(),
+           "in_off": out["in_off"][:V + 1].cpu().numpy(),
+           "in_nbr": out["in_nbr"][:E].cpu().numpy()}
+    _same(got, _regular(src, dst))
+    short = dict(out, out_off=out["out_off"][:2 * n])  # one entry short
+    with pytest.raises(ValueError):
+        ringo.ringo_table_to_graph_noalloc(src, dst, short)
+    wrong = dict(out, in_nbr=out["in_nbr"].to(torch.int64))
+    with pytest.raises(ValueError):
+        ringo.ringo_table_to_graph_noalloc(src, dst, wrong)
