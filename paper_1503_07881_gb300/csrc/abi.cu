@@ -90,7 +90,7 @@ WsLayout layout_for(uint32_t n) {
   L.st0 = o; o = align_up(o + sizeof(uint32_t) * tiles * kRadix);
   L.st1 = o; o = align_up(o + sizeof(uint32_t) * tiles * kRadix);
   L.chunks = (tiles + kChunkTiles - 1) / kChunkTiles;
-  L.chunk_bytes = align_up(sizeof(uint32_t) * L.chunks * (2 * kRadix + 1));
+  L.chunk_bytes = align_up(radix_chunk_bytes(L.chunks));
   L.ch0 = o; o = align_up(o + L.chunk_bytes);
   L.ch1 = o; o = align_up(o + L.chunk_bytes);
   // per scan: tile statuses, then chunk sums, chunk prefixes, chunk counters
@@ -146,12 +146,7 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
     hctl->status[0] = (uint32_t*)(ws + L.st0);
     hctl->status[1] = (uint32_t*)(ws + L.st1);
     hctl->status_rows = tiles;
-    for (int r = 0; r < 2; ++r) {
-      uint32_t* ch = (uint32_t*)(ws + (r ? L.ch1 : L.ch0));
-      hctl->chunk_agg[r] = ch;
-      hctl->chunk_inc[r] = ch + L.chunks * kRadix;
-      hctl->chunk_cnt[r] = ch + 2 * L.chunks * kRadix;
-    }
+    for (int r = 0; r < 2; ++r) place_radix_chunks(hctl, r, ws + (r ? L.ch1 : L.ch0), L.chunks);
     hctl->chunk_rows = (uint32_t)L.chunks;
     place_scan(hctl, 0, ws + L.sc0, tiles);
     place_scan(hctl, 1, ws + L.sc1, tiles);

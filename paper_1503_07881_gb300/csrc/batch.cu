@@ -59,7 +59,7 @@ __host__ __device__ inline SegLayout seg_layout(uint32_t n) {
   const uint64_t tiles = (n + (uint64_t)kSortTile - 1) / kSortTile;
   const uint64_t mtiles = (2ull * n + kMergeTile - 1) / kMergeTile + 1;
   const uint64_t ch = nchunks(tiles);
-  const uint64_t chunk_bytes = al(4 * ch * (2 * kRadix + 1));
+  const uint64_t chunk_bytes = al(radix_chunk_bytes(ch));
   L.tiles = (uint32_t)tiles;
   L.mtiles = (uint32_t)mtiles;
   L.chunks = (uint32_t)ch;
@@ -131,12 +131,8 @@ __global__ void k_init_ctls(Ctl* __restrict__ ctls, const SegDesc* __restrict__ 
   c->status[0] = (uint32_t*)(d.zbase + L.z_st0);
   c->status[1] = (uint32_t*)(d.sbase + L.st1);
   c->status_rows = L.tiles;
-  for (int r = 0; r < 2; ++r) {
-    uint32_t* ch = (uint32_t*)(r ? d.sbase + L.ch1 : d.zbase + L.z_ch0);
-    c->chunk_agg[r] = ch;
-    c->chunk_inc[r] = ch + (uint64_t)L.chunks * kRadix;
-    c->chunk_cnt[r] = ch + 2ull * L.chunks * kRadix;
-  }
+  for (int r = 0; r < 2; ++r)
+    place_radix_chunks(c, r, r ? d.sbase + L.ch1 : d.zbase + L.z_ch0, L.chunks);
   c->chunk_rows = L.chunks;
   place_scan_dev(c, 0, d.zbase + L.z_sc0, L.tiles);
   place_scan_dev(c, 1, d.zbase + L.z_sc1, L.tiles);

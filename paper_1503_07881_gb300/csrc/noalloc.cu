@@ -54,7 +54,7 @@ constexpr size_t kOffKeysB = up(kOffKeysA + 8 * ((size_t)kMaxRows + 1));
 constexpr size_t kOffSt0 = up(kOffKeysB + 8 * ((size_t)kMaxRows + 1));
 constexpr size_t kOffSt1 = up(kOffSt0 + 4 * kTiles * kRadix);
 constexpr size_t kChunks = (kTiles + kChunkTiles - 1) / kChunkTiles;
-constexpr size_t kChunkBytes = up(4 * kChunks * (2 * kRadix + 1));
+constexpr size_t kChunkBytes = up(radix_chunk_bytes(kChunks));
 constexpr size_t kOffCh0 = up(kOffSt1 + 4 * kTiles * kRadix);
 constexpr size_t kOffCh1 = up(kOffCh0 + kChunkBytes);
 constexpr size_t kOffSc0 = up(kOffCh1 + kChunkBytes);
@@ -173,12 +173,7 @@ extern "C" int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* d
   h.status[1] = (uint32_t*)(ws + kOffSt1);
   h.status_rows = tiles;
   const size_t chunks = (tiles + kChunkTiles - 1) / kChunkTiles;
-  for (int r = 0; r < 2; ++r) {
-    uint32_t* ch = (uint32_t*)(ws + (r ? kOffCh1 : kOffCh0));
-    h.chunk_agg[r] = ch;
-    h.chunk_inc[r] = ch + chunks * kRadix;
-    h.chunk_cnt[r] = ch + 2 * chunks * kRadix;
-  }
+  for (int r = 0; r < 2; ++r) place_radix_chunks(&h, r, ws + (r ? kOffCh1 : kOffCh0), chunks);
   h.chunk_rows = (uint32_t)chunks;
   place_scan(&h, 0, ws + kOffSc0, tiles);
   place_scan(&h, 1, ws + kOffSc1, tiles);
@@ -194,7 +189,7 @@ extern "C" int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* d
   const Launch run = solo_launch(dctl, &h, n);
   NA_TRY(cudaMemcpyAsync(dctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
   NA_TRY(cudaMemsetAsync(ws + kOffSt0, 0, 4 * (size_t)tiles * kRadix, s));
-  NA_TRY(cudaMemsetAsync(ws + kOffCh0, 0, 4 * chunks * (2 * kRadix + 1), s));
+  NA_TRY(cudaMemsetAsync(ws + kOffCh0, 0, radix_chunk_bytes(chunks), s));
   NA_TRY(cudaMemsetAsync(ws + kOffSc0, 0, kOffUsrc - kOffSc0, s));
   if ((rc = enqueue_phase1(run, s)) != RINGO_OK) return rc;
   NA_TRY(cudaMemcpyAsync(&h, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));

@@ -106,9 +106,12 @@ struct alignas(16) Ctl {
   uint32_t status_rows;
   // chunk level of the radix look-back (kChunkTiles tiles per chunk), two
   // regions alternating with the passes like `status`:
-  uint32_t* chunk_agg[2];     // [chunks][kRadix] digit counts added by the chunk's tiles
-  uint32_t* chunk_inc[2];     // [chunks][kRadix] kStInc | inclusive prefix, once known
-  uint32_t* chunk_cnt[2];     // [chunks] tiles that have added their counts
+  //   chunk_agg[c][d] = (tiles of chunk c that have added << 32) | digit-d
+  //                     count they added; one 64-bit word, so a single load
+  //                     tells whether the sum is complete
+  //   chunk_inc[c][d] = kStInc | inclusive prefix of digit d through chunk c
+  uint64_t* chunk_agg[2];     // [chunks][kRadix]
+  uint32_t* chunk_inc[2];     // [chunks][kRadix]
   uint32_t chunk_rows;
   uint64_t* scan_status[3];   // [tiles] each: dedup, dst_rank, merge
   uint64_t* scan_chunk_agg[3];  // [chunks of those tiles] packed sums
@@ -140,6 +143,16 @@ struct alignas(16) Ctl {
   uint32_t solo_blocks[2];
   uint32_t solo_counters[32];
 };
+
+// Bytes of one region of the radix chunk look-back (aggregates, then
+// prefixes), and its placement.
+__host__ __device__ constexpr uint64_t radix_chunk_bytes(uint64_t chunks) {
+  return 12ull * chunks * kRadix;
+}
+__host__ __device__ inline void place_radix_chunks(Ctl* c, int r, void* p, uint64_t chunks) {
+  c->chunk_agg[r] = static_cast<uint64_t*>(p);
+  c->chunk_inc[r] = reinterpret_cast<uint32_t*>(static_cast<char*>(p) + 8ull * chunks * kRadix);
+}
 
 // Merge-path splits of the merge tiles (phase 2).  They live in the radix key
 // buffer, which no phase-2 kernel reads: at most (2n + 2047) / 2048 + 1

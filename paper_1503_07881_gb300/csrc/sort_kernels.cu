@@ -182,18 +182,21 @@ void launch_plan(const Launch& L, int which, cudaStream_t s) {
 
 // Two-level decoupled look-back for digit d of `tile`: first over the
 // earlier tiles of the tile's own chunk (their aggregates or an inclusive
-// prefix), then over earlier chunks: a chunk whose tiles have all added their
-// counts contributes its aggregate, a chunk whose inclusive prefix is known
-// ends the walk.  A chunk's aggregate is complete soon after its tiles have
-// counted, so no wait follows the chain of inclusive prefixes tile by tile.
-// Bounded like every wait here.
+// prefix, kLbTiles status words per round trip), then over earlier chunks,
+// kLbChunks per round trip: a chunk whose inclusive prefix is known ends the
+// walk, a chunk whose tiles have all added their counts contributes its
+// aggregate.  Every word read is self-validating (flag or tile count in the
+// same word), so all loads are relaxed and a round needs no fence.  A
+// chunk's aggregate is complete soon after its tiles have counted, so no
+// wait follows the chain of inclusive prefixes tile by tile.  Bounded like
+// every wait here.
+constexpr int kLbTiles = kChunkTiles / 2;
+constexpr int kLbChunks = 4;
 __device__ __forceinline__ uint32_t digit_lookback2(const uint32_t* __restrict__ st,
-                                                    const uint32_t* __restrict__ cagg,
+                                                    const uint64_t* __restrict__ cagg,
                                                     const uint32_t* __restrict__ cinc,
-                                                    const uint32_t* __restrict__ ccnt,
                                                     uint32_t tile, uint32_t ntiles, uint32_t d,
                                                     Ctl* ctl) {
-  constexpr int W = kChunkTiles / 2;
   const volatile uint32_t* verr = &ctl->err;
   uint32_t excl = 0, spins = 0;
   const uint32_t c = tile >> kChunkShift;
@@ -201,14 +204,14 @@ __device__ __forceinline__ uint32_t digit_lookback2(const uint32_t* __restrict__
   // 1. tiles [first, tile) of this chunk
   int64_t j = (int64_t)tile - 1;
   while (j >= (int64_t)first) {
-    uint32_t v[W];
+    uint32_t v[kLbTiles];
 #pragma unroll
-    for (int k = 0; k < W; ++k)
+    for (int k = 0; k < kLbTiles; ++k)
       v[k] = (j - k >= (int64_t)first) ? ld_relaxed_u32(st + (size_t)(j - k) * kRadix + d) : 0u;
     int used = 0;
     bool done = false, stall = false;
 #pragma unroll
-    for (int q = 0; q < W; ++q) {
+    for (int q = 0; q < kLbTiles; ++q) {
       if (done || stall || j - q < (int64_t)first) continue;
       const uint32_t x = v[q];
       if (x == 0) {
@@ -233,41 +236,67 @@ __device__ __forceinline__ uint32_t digit_lookback2(const uint32_t* __restrict__
   // 2. chunks c-1, c-2, ...
   int64_t cc = (int64_t)c - 1;
   while (cc >= 0) {
-    const uint32_t inc = ld_relaxed_u32(cinc + (size_t)cc * kRadix + d);
-    if (inc & kStInc) return excl + (inc & ~kStInc);
-    const uint32_t cnt = ld_acquire_u32(ccnt + cc);
-    const uint32_t need = min((uint32_t)kChunkTiles, ntiles - ((uint32_t)cc << kChunkShift));
-    if (cnt >= need) {
-      excl += ld_relaxed_u32(cagg + (size_t)cc * kRadix + d);
-      --cc;
-      continue;
+    uint32_t inc[kLbChunks];
+    uint64_t agg[kLbChunks];
+#pragma unroll
+    for (int k = 0; k < kLbChunks; ++k) {
+      const bool in = cc - k >= 0;
+      inc[k] = in ? ld_relaxed_u32(cinc + (size_t)(cc - k) * kRadix + d) : 0u;
+      agg[k] = in ? ld_relaxed_u64(cagg + (size_t)(cc - k) * kRadix + d) : 0ull;
     }
-    if (spin_backoff(spins) || ((spins & 255) == 0 && *verr)) {
-      atomicOr(&ctl->err, kErrLookback);
-      return excl;
+    int used = 0;
+    bool done = false, stall = false;
+#pragma unroll
+    for (int k = 0; k < kLbChunks; ++k) {
+      if (done || stall || cc - k < 0) continue;
+      if (inc[k] & kStInc) {
+        excl += inc[k] & ~kStInc;
+        done = true;
+        continue;
+      }
+      const uint32_t need =
+          min((uint32_t)kChunkTiles, ntiles - ((uint32_t)(cc - k) << kChunkShift));
+      if ((uint32_t)(agg[k] >> 32) >= need) {
+        excl += (uint32_t)agg[k];
+        used = k + 1;
+      } else {
+        stall = true;
+      }
+    }
+    if (done) return excl;
+    cc -= used;
+    if (stall) {
+      if (spin_backoff(spins) || ((spins & 255) == 0 && *verr)) {
+        atomicOr(&ctl->err, kErrLookback);
+        return excl;
+      }
     }
   }
   return excl;
 }
 
-// The pass as used by default.  One 4096-key tile per block, four blocks per
-// SM.  Per tile:
+// The pass.  One 4096-key tile per block, four blocks per SM.  Per tile:
 //   0. the tile arrives in shared memory by one bulk asynchronous copy
-//      (cp.async.bulk + mbarrier; the first pass copies the two columns);
-//   1. digit counts per warp (shared-memory reductions), published at once,
-//      also into the chunk aggregate of the two-level look-back;
-//   2. warp offsets within each digit plus the tile's digit starts;
-//   3. ranks: the lanes of a warp holding the same digit find each other
-//      through a shared peer mask (atomicOr of lane bits), the highest of
-//      them advances the warp's digit offset for the group;
-//   4. the keys move to their ranked places in the same buffer;
-//   5. two-level look-back;
+//      (cp.async.bulk + mbarrier; the first pass copies the two columns and
+//      packs the keys as it reads them);
+//   1. digit counts per warp (shared-memory adds), published at once, also
+//      into the chunk aggregate of the two-level look-back;
+//   2. thread d owns digit d: per-warp starts within the tile;
+//   3. stable ranks: the lanes of a warp holding the same digit find each
+//      other through a shared peer mask (atomicOr of lane bits); the highest
+//      of them advances the warp's running position of that digit for the
+//      whole group, so each key gets its final place in the staged tile;
+//   4. the keys move to their places in the same buffer;
+//   5. two-level look-back (thread d, digit d) -> global digit offsets;
 //   6. coalesced scatter of the staged tile.
-// Keys sit in registers only during step 4, so a block needs few registers.
-struct SweepV6Smem {
+// The digit position is a template parameter (byte BYTE of the key's high or
+// low word, taken with one byte permute), and full tiles take a path without
+// bounds checks, so the per-key work is a few shared-memory operations and
+// no branches.
+struct SweepSmem {
   uint64_t keys[kSortTile];               // the tile: input, then staged in digit order
-  uint32_t whist[kSortWarps][kRadix];
-  uint32_t mask[kSortWarps][kRadix + 1];  // slot kRadix: lanes past the end
+  uint32_t whist[kSortWarps][kRadix];     // per-warp counts, then running positions
+  uint32_t mask[kSortWarps][kRadix + 1];  // peer masks; slot kRadix: lanes past the end
   int32_t delta[kRadix];
   uint32_t sw[kSortWarps + 1];
   Claim claim;
@@ -275,12 +304,150 @@ struct SweepV6Smem {
   uint64_t bar;
 };
 
+template <int BYTE>
+__device__ __forceinline__ uint32_t byte_of(uint32_t w) {
+  return __byte_perm(w, 0u, 0x4440u + BYTE);
+}
+
+// The word of key j that holds this pass's digit.  Packed first pass: the
+// columns sit in the tile buffer as src[0..4096) then dst[0..4096).
+template <bool HI, bool PACK>
+__device__ __forceinline__ uint32_t key_word(const SweepSmem& S, uint32_t j) {
+  if (PACK) {
+    const int32_t* cols = reinterpret_cast<const int32_t*>(S.keys);
+    return (uint32_t)cols[HI ? j : kSortTile + j] ^ kBias;
+  }
+  const uint64_t k = S.keys[j];
+  return HI ? (uint32_t)(k >> 32) : (uint32_t)k;
+}
+template <bool PACK>
+__device__ __forceinline__ uint64_t key_at(const SweepSmem& S, uint32_t j) {
+  if (PACK) {
+    const int32_t* cols = reinterpret_cast<const int32_t*>(S.keys);
+    return ((uint64_t)((uint32_t)cols[j] ^ kBias) << 32) | ((uint32_t)cols[kSortTile + j] ^ kBias);
+  }
+  return S.keys[j];
+}
+
+// Steps 1-6 for one tile of `cnt` keys (FULL: cnt == kSortTile).
+template <int BYTE, bool HI, bool PACK, bool FULL>
+__device__ __forceinline__ void sweep_body(SweepSmem& S, Ctl* __restrict__ ctl, SortCtl& sc,
+                                           const PassDesc& pd, uint32_t tile, uint32_t ntiles,
+                                           uint32_t cnt, uint32_t n, int pass, int reg) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t wslot = warp * (kSortItems * 32) + lane;
+  // 1. counts
+  uint32_t* whist = S.whist[warp];
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const uint32_t j = wslot + i * 32;
+    if (FULL || j < cnt) atomicAdd(whist + byte_of<BYTE>(key_word<HI, PACK>(S, j)), 1u);
+  }
+  __syncthreads();
+  // 2. thread tid owns digit tid
+  uint32_t c[kSortWarps];
+  uint32_t bin_total = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) {
+    c[w] = S.whist[w][tid];
+    bin_total += c[w];
+  }
+  uint32_t* __restrict__ st = ctl->status[reg];
+  uint32_t* my_st = st + (size_t)tile * kRadix + tid;
+  st_relaxed_u32(my_st, tile == 0 ? (kStInc | bin_total) : (1u + bin_total));
+  const uint32_t chunk = tile >> kChunkShift;
+  uint64_t* cagg = ctl->chunk_agg[reg];
+  uint32_t* cinc = ctl->chunk_inc[reg];
+  // one more tile of this chunk, and its count, in one atomic word
+  atomicAdd(reinterpret_cast<unsigned long long*>(cagg + (size_t)chunk * kRadix + tid),
+            (1ull << 32) | bin_total);
+  uint32_t tile_total;
+  const uint32_t bin_start = block_exclusive_sum<kSortThreads>(bin_total, S.sw, tile_total);
+  {
+    uint32_t run = bin_start;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+      S.whist[w][tid] = run;
+      run += c[w];
+    }
+  }
+  __syncthreads();
+  // 3. ranks -> places in the staged tile
+  const uint32_t lt = lanemask_lt();
+  const uint32_t bit = 1u << lane;
+  const uint32_t wmask = smem_addr(S.mask[warp]);
+  const uint32_t whaddr = smem_addr(whist);
+  uint32_t lpos[kSortItems / 2];  // two 16-bit places per register
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const uint32_t j = wslot + i * 32;
+    const bool ok = FULL || j < cnt;
+    const uint32_t d = ok ? byte_of<BYTE>(key_word<HI, PACK>(S, j)) : (uint32_t)kRadix;
+    asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(wmask + 4 * d), "r"(bit) : "memory");
+    __syncwarp();
+    uint32_t peers;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(peers) : "r"(wmask + 4 * d) : "memory");
+    __syncwarp();
+    const uint32_t leader = 31u - __clz(peers);
+    uint32_t old = 0;
+    // the group's highest lane clears the mask entry and advances the
+    // digit's running place by the group size (predicated, no branch)
+    const uint32_t lead = ((uint32_t)lane == leader) & (ok ? 1u : 0u);
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n"
+        " @p st.shared.u32 [%2], 0;\n"
+        " @p atom.shared.add.u32 %0, [%3], %4;\n}\n"
+        : "+r"(old)
+        : "r"(lead), "r"(wmask + 4 * d), "r"(whaddr + 4 * d), "r"((uint32_t)__popc(peers))
+        : "memory");
+    __syncwarp();
+    old = __shfl_sync(0xFFFFFFFFu, old, leader);
+    const uint32_t pos = old + (uint32_t)__popc(peers & lt);
+    if (i & 1) lpos[i >> 1] |= pos << 16;
+    else lpos[i >> 1] = pos;
+  }
+  // 4. keys to their places
+  uint64_t key[kSortItems];
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) key[i] = key_at<PACK>(S, wslot + i * 32);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    if (FULL || wslot + i * 32 < cnt) S.keys[(lpos[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu] = key[i];
+  }
+  // 5. look-back
+  uint32_t excl = 0;
+  if (tile > 0) {
+    excl = digit_lookback2(st, cagg, cinc, tile, ntiles, tid, ctl);
+    st_relaxed_u32(my_st, kStInc | (excl + bin_total));
+  }
+  if ((tile & (kChunkTiles - 1)) == 0 && chunk > 0)
+    st_relaxed_u32(cinc + (size_t)(chunk - 1) * kRadix + tid, kStInc | excl);
+  if ((tile & (kChunkTiles - 1)) == kChunkTiles - 1 || tile == ntiles - 1)
+    st_relaxed_u32(cinc + (size_t)chunk * kRadix + tid, kStInc | (excl + bin_total));
+  S.delta[tid] = (int32_t)(sc.base[pass][tid] + excl) - (int32_t)bin_start;
+  __syncthreads();
+  // 6. scatter
+  uint64_t* __restrict__ out = pd.out;
+#pragma unroll
+  for (int q = 0; q < kSortItems; ++q) {
+    const uint32_t j = (uint32_t)tid + q * kSortThreads;
+    if (FULL || j < cnt) {
+      const uint64_t k = S.keys[j];
+      const uint32_t w = HI ? (uint32_t)(k >> 32) : (uint32_t)k;
+      const uint32_t pos = (uint32_t)(S.delta[byte_of<BYTE>(w)] + (int32_t)j);
+      if (pos < n) out[pos] = k;
+    }
+  }
+}
+
+template <int BYTE, bool HI>
 __global__ void __launch_bounds__(kSortThreads, 4)
     k_onesweep(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter, int which, int pass,
                int gpass) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  SweepV6Smem& S = *reinterpret_cast<SweepV6Smem*>(smem_raw);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  SweepSmem& S = *reinterpret_cast<SweepSmem*>(smem_raw);
+  const int tid = threadIdx.x;
   if (tid == 0) {
     claim_slot(m, counter, &S.claim);
     mbar_init(&S.bar, 1);
@@ -306,30 +473,25 @@ __global__ void __launch_bounds__(kSortThreads, 4)
       const uint32_t cidx = tile >> kChunkShift;
       ctl->chunk_agg[nreg][(size_t)cidx * kRadix + tid] = 0;
       ctl->chunk_inc[nreg][(size_t)cidx * kRadix + tid] = 0;
-      if (tid == 0) ctl->chunk_cnt[nreg][cidx] = 0;
     }
   }
   const PassDesc pd = sc.pass[pass];
   const uint32_t n = sc.n;
   const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
   if (!pd.active || tile >= ntiles) return;
-  uint32_t* __restrict__ st = ctl->status[reg];
   const uint32_t base = tile * (uint32_t)kSortTile;
   const uint32_t cnt = min((uint32_t)kSortTile, n - base);
-  const uint32_t shift = pd.shift;
   const uint64_t* __restrict__ in = pd.in;
   const int32_t* __restrict__ src = ctl->src;
   const int32_t* __restrict__ dst = ctl->dst;
-  int32_t* cols = reinterpret_cast<int32_t*>(&S.keys[0]);  // first pass: src | dst
-
+  int32_t* cols = reinterpret_cast<int32_t*>(&S.keys[0]);  // packed pass: src | dst
   // 0. bulk copy of the tile (what is not a multiple of 16 bytes, or not
   //    16-byte aligned, comes in with plain loads)
   uint32_t bulk;
   if (in) bulk = cnt & ~1u;
   else bulk = ((((uintptr_t)src) | ((uintptr_t)dst)) & 15) == 0 ? (cnt & ~3u) : 0u;
   if (tid == 0) {
-    const uint32_t bytes = bulk * 8u;  // 8-byte keys, or two 4-byte columns
-    mbar_arrive_expect_tx(&S.bar, bytes);
+    mbar_arrive_expect_tx(&S.bar, bulk * 8u);  // 8-byte keys, or two 4-byte columns
     if (bulk) {
       if (in) {
         bulk_g2s(&S.keys[0], in + base, bulk * 8u, &S.bar);
@@ -358,125 +520,37 @@ __global__ void __launch_bounds__(kSortThreads, 4)
   }
   while (!mbar_try_wait(&S.bar, 0)) {
   }
-  auto digit_at = [&](uint32_t j) -> uint32_t {
-    if (in) return (uint32_t)(S.keys[j] >> shift) & (kRadix - 1);
-    // packed key = bias(src) << 32 | bias(dst)
-    const uint32_t v = shift >= 32 ? ((uint32_t)cols[j] ^ kBias) : ((uint32_t)cols[kSortTile + j] ^ kBias);
-    return (v >> (shift & 31)) & (kRadix - 1);
-  };
-  const uint32_t wslot = warp * (kSortItems * 32);
-  // 1. counts
-#pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
-    const uint32_t j = wslot + i * 32 + lane;
-    if (j < cnt) atomicAdd(&S.whist[warp][digit_at(j)], 1u);
-  }
-  __syncthreads();
-  // 2. thread tid owns digit tid
-  uint32_t bin_total = 0;
-#pragma unroll
-  for (int w = 0; w < kSortWarps; ++w) {
-    const uint32_t c = S.whist[w][tid];
-    S.whist[w][tid] = bin_total;
-    bin_total += c;
-  }
-  uint32_t* my_st = st + (size_t)tile * kRadix + tid;
-  st_relaxed_u32(my_st, tile == 0 ? (kStInc | bin_total) : (1u + bin_total));
-  const uint32_t chunk = tile >> kChunkShift;
-  uint32_t* cagg = ctl->chunk_agg[reg];
-  uint32_t* cinc = ctl->chunk_inc[reg];
-  uint32_t* ccnt = ctl->chunk_cnt[reg];
-  if (bin_total) atomicAdd(cagg + (size_t)chunk * kRadix + tid, bin_total);
-  uint32_t tile_total;
-  const uint32_t bin_start = block_exclusive_sum<kSortThreads>(bin_total, S.sw, tile_total);
-  if (tid == 0) {
-    // the block barrier inside the sum orders every thread's chunk-aggregate
-    // add before this fence (fences are cumulative), so one release fence
-    // makes all of them visible before the chunk counter moves
-    __threadfence();
-    atomicAdd(ccnt + chunk, 1u);
-  }
-#pragma unroll
-  for (int w = 0; w < kSortWarps; ++w) S.whist[w][tid] += bin_start;
-  __syncthreads();
-  // 3. ranks
-  const uint32_t lt = lanemask_lt();
-  uint32_t* wmask = S.mask[warp];
-  uint32_t* whist = S.whist[warp];
-  uint32_t lpos[kSortItems / 2];  // two 16-bit positions per register
-#pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
-    const uint32_t j = wslot + i * 32 + lane;
-    const bool ok = j < cnt;
-    const uint32_t dig = ok ? digit_at(j) : kRadix;
-    atomicOr(&wmask[dig], 1u << lane);
-    __syncwarp();
-    const uint32_t peers = wmask[dig];
-    __syncwarp();
-    const int leader = 31 - __clz(peers);
-    uint32_t old = 0;
-    if (lane == leader) {
-      wmask[dig] = 0;
-      if (ok) old = atomicAdd(&whist[dig], (uint32_t)__popc(peers));
-    }
-    __syncwarp();
-    old = __shfl_sync(0xFFFFFFFFu, old, leader);
-    const uint32_t pos = old + __popc(peers & lt);
-    if (i & 1) lpos[i >> 1] |= pos << 16;
-    else lpos[i >> 1] = pos;
-  }
-  // 4. move the keys to their ranked places
-  uint64_t key[kSortItems];
-#pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
-    const uint32_t j = wslot + i * 32 + lane;
-    if (in) {
-      key[i] = S.keys[j];
-    } else {
-      key[i] = ((uint64_t)((uint32_t)cols[j] ^ kBias) << 32) | ((uint32_t)cols[kSortTile + j] ^ kBias);
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < kSortItems; ++i) {
-    const uint32_t j = wslot + i * 32 + lane;
-    if (j < cnt) S.keys[(lpos[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu] = key[i];
-  }
-  // 5. look-back
-  uint32_t excl = 0;
-  if (tile > 0) {
-    excl = digit_lookback2(st, cagg, cinc, ccnt, tile, ntiles, tid, ctl);
-    st_relaxed_u32(my_st, kStInc | (excl + bin_total));
-  }
-  if ((tile & (kChunkTiles - 1)) == 0 && chunk > 0)
-    st_relaxed_u32(cinc + (size_t)(chunk - 1) * kRadix + tid, kStInc | excl);
-  if ((tile & (kChunkTiles - 1)) == kChunkTiles - 1 || tile == ntiles - 1)
-    st_relaxed_u32(cinc + (size_t)chunk * kRadix + tid, kStInc | (excl + bin_total));
-  S.delta[tid] = (int32_t)(sc.base[pass][tid] + excl) - (int32_t)bin_start;
-  __syncthreads();
-  // 6. scatter
-  uint64_t* __restrict__ out = pd.out;
-#pragma unroll 4
-  for (uint32_t j = tid; j < cnt; j += kSortThreads) {
-    const uint64_t k = S.keys[j];
-    const uint32_t dig = (uint32_t)(k >> shift) & (kRadix - 1);
-    const uint32_t pos = (uint32_t)(S.delta[dig] + (int32_t)j);
-    if (pos < n) out[pos] = k;
+  const bool full = cnt == (uint32_t)kSortTile;
+  if (!HI && !in) {
+    if (full) sweep_body<BYTE, HI, true, true>(S, ctl, sc, pd, tile, ntiles, cnt, n, pass, reg);
+    else sweep_body<BYTE, HI, true, false>(S, ctl, sc, pd, tile, ntiles, cnt, n, pass, reg);
+  } else {
+    if (full) sweep_body<BYTE, HI, false, true>(S, ctl, sc, pd, tile, ntiles, cnt, n, pass, reg);
+    else sweep_body<BYTE, HI, false, false>(S, ctl, sc, pd, tile, ntiles, cnt, n, pass, reg);
   }
 }
+
+using SweepFn = void (*)(Ctl*, SegMap, uint32_t*, int, int, int);
+// [hi][byte]: the digit of out-sort pass p is byte p % 4 of the low word
+// (p < 4) or of the high word; in-sort pass p is byte p of the high word
+static const SweepFn kSweep[2][4] = {
+    {k_onesweep<0, false>, k_onesweep<1, false>, k_onesweep<2, false>, k_onesweep<3, false>},
+    {k_onesweep<0, true>, k_onesweep<1, true>, k_onesweep<2, true>, k_onesweep<3, true>}};
 
 static std::mutex g_sweep_attr_mu;
 static uint64_t g_sweep_attr_devs = 0;  // bit d: set on device d
 
-// The onesweep kernel's dynamic shared memory limit, set once per device
+// The onesweep kernels' dynamic shared memory limit, set once per device
 // (not a stream operation, so it must happen before any stream capture).
 void prepare_launches() {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_sweep_attr_mu);
   if (dev < 64 && !((g_sweep_attr_devs >> dev) & 1)) {
-    cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(SweepV6Smem));
+    for (int h = 0; h < 2; ++h)
+      for (int b = 0; b < 4; ++b)
+        cudaFuncSetAttribute(kSweep[h][b], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SweepSmem));
     g_sweep_attr_devs |= 1ull << dev;
   }
 }
@@ -485,8 +559,11 @@ void launch_onesweep(const Launch& L, int which, int pass, int gpass, uint32_t* 
                      cudaStream_t s) {
   if (L.row_slots == 0) return;
   prepare_launches();
-  k_onesweep<<<L.row_slots, kSortThreads, sizeof(SweepV6Smem), s>>>(L.ctls, L.rows, counter,
-                                                                    which, pass, gpass);
+  // shift = (which ? 32 : 0) + 8 * pass; see k_plan
+  const int shift = (which ? 32 : 0) + kRadixBits * pass;
+  const SweepFn fn = kSweep[shift >= 32][(shift & 31) >> 3];
+  fn<<<L.row_slots, kSortThreads, sizeof(SweepSmem), s>>>(L.ctls, L.rows, counter, which, pass,
+                                                          gpass);
 }
 
 }  // namespace ringo
