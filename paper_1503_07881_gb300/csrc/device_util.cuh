@@ -93,6 +93,11 @@ __device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, uint32_t 
       ::"r"(smem_addr(sdst)), "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
+// Asks the memory system to bring `bytes` (multiple of 16; 16-byte aligned
+// address) from global memory into L2, with no destination in this block.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* gsrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gsrc), "r"(bytes) : "memory");
+}
 // Bounded wait for a bulk copy phase.  Gives up (returns false) after about a
 // second, or at once when another block has already recorded an error.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
@@ -287,10 +292,12 @@ struct Claim {
   uint32_t seg;
   uint32_t tile;   // local tile of the segment
   uint32_t valid;  // 0: past the last slot
+  uint32_t slot;   // the global slot
 };
 __device__ __forceinline__ Claim claim_next(SegMap m, uint32_t* counter) {
   Claim c;
   const uint32_t g = atomicAdd(counter, 1u);
+  c.slot = g;
   if (g >= __ldg(m.start + m.nseg)) {
     c.seg = 0;
     c.tile = 0;
@@ -304,6 +311,7 @@ __device__ __forceinline__ Claim claim_next(SegMap m, uint32_t* counter) {
 }
 __device__ __forceinline__ void claim_slot(SegMap m, uint32_t* counter, Claim* out) {
   const uint32_t g = atomicAdd(counter, 1u);
+  out->slot = g;
   if (g >= __ldg(m.start + m.nseg)) {
     out->valid = 0;
     return;

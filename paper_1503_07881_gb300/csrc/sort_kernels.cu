@@ -293,14 +293,29 @@ __device__ __forceinline__ uint32_t digit_lookback2(const uint32_t* __restrict__
 // low word, taken with one byte permute), and full tiles take a path without
 // bounds checks, so the per-key work is a few shared-memory operations and
 // no branches.
+// A block prefetches into L2 the tile of the slot this far ahead of its
+// own: about the number of blocks resident at once (four per SM).
+constexpr uint32_t kPrefetchAhead = 4 * 152;
+
+// What thread 0 learns about the block's tile, for the whole block.
+struct SweepTile {
+  uint32_t valid;  // 0: no slot left
+  uint32_t work;   // 1: this pass moves keys of this tile
+  uint32_t seg, tile, slot;
+  uint32_t n;      // keys of this sort in the tile's segment
+  uint32_t cnt;    // keys in the tile
+  uint32_t bulk;   // keys brought by the bulk copy; the rest by plain loads
+  const uint64_t* in;  // NULL: pack from the columns
+  uint64_t* out;
+};
+
 struct SweepSmem {
   uint64_t keys[kSortTile];               // the tile: input, then staged in digit order
   uint32_t whist[kSortWarps][kRadix];     // per-warp counts, then running positions
   uint32_t mask[kSortWarps][kRadix + 1];  // peer masks; slot kRadix: lanes past the end
   int32_t delta[kRadix];
   uint32_t sw[kSortWarps + 1];
-  Claim claim;
-  uint32_t ok;
+  SweepTile t;
   uint64_t bar;
 };
 
@@ -332,8 +347,9 @@ __device__ __forceinline__ uint64_t key_at(const SweepSmem& S, uint32_t j) {
 // Steps 1-6 for one tile of `cnt` keys (FULL: cnt == kSortTile).
 template <int BYTE, bool HI, bool PACK, bool FULL>
 __device__ __forceinline__ void sweep_body(SweepSmem& S, Ctl* __restrict__ ctl, SortCtl& sc,
-                                           const PassDesc& pd, uint32_t tile, uint32_t ntiles,
-                                           uint32_t cnt, uint32_t n, int pass, int reg) {
+                                           uint64_t* __restrict__ out, uint32_t tile,
+                                           uint32_t ntiles, uint32_t cnt, uint32_t n, int pass,
+                                           int reg) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t wslot = warp * (kSortItems * 32) + lane;
   // 1. counts
@@ -428,7 +444,6 @@ __device__ __forceinline__ void sweep_body(SweepSmem& S, Ctl* __restrict__ ctl, 
   S.delta[tid] = (int32_t)(sc.base[pass][tid] + excl) - (int32_t)bin_start;
   __syncthreads();
   // 6. scatter
-  uint64_t* __restrict__ out = pd.out;
 #pragma unroll
   for (int q = 0; q < kSortItems; ++q) {
     const uint32_t j = (uint32_t)tid + q * kSortThreads;
@@ -449,9 +464,78 @@ __global__ void __launch_bounds__(kSortThreads, 4)
   SweepSmem& S = *reinterpret_cast<SweepSmem*>(smem_raw);
   const int tid = threadIdx.x;
   if (tid == 0) {
-    claim_slot(m, counter, &S.claim);
     mbar_init(&S.bar, 1);
     mbar_init_fence();
+    const uint32_t g = atomicAdd(counter, 1u);
+    const uint32_t total = __ldg(m.start + m.nseg);
+    // the first segment's fields are read while the claim is in flight: a
+    // single-table launch needs nothing else before its copy starts
+    const Ctl* c = ctls;
+    const SortCtl* sc = which ? &c->in_sort : &c->out_sort;
+    PassDesc pd = sc->pass[pass];
+    uint32_t n = sc->n;
+    SweepTile t{};
+    t.slot = g;
+    if (g < total) {
+      uint32_t seg = 0, tile = g;
+      if (m.nseg > 1) {
+        seg = seg_of(m, g);
+        tile = g - __ldg(m.start + seg);
+        c = ctls + seg;
+        sc = which ? &c->in_sort : &c->out_sort;
+        pd = sc->pass[pass];
+        n = sc->n;
+      }
+      t.valid = 1;
+      t.seg = seg;
+      t.tile = tile;
+      t.n = n;
+      if (pd.active && tile < (n + kSortTile - 1) / kSortTile) {
+        const uint32_t base = tile * (uint32_t)kSortTile;
+        t.work = 1;
+        t.cnt = min((uint32_t)kSortTile, n - base);
+        t.in = pd.in;
+        t.out = pd.out;
+        // bulk copy of the tile (what is not a multiple of 16 bytes, or not
+        // 16-byte aligned, comes in with plain loads)
+        if (pd.in) {
+          t.bulk = t.cnt & ~1u;
+          mbar_arrive_expect_tx(&S.bar, t.bulk * 8u);
+          if (t.bulk) bulk_g2s(&S.keys[0], pd.in + base, t.bulk * 8u, &S.bar);
+        } else {
+          const int32_t* src = c->src;
+          const int32_t* dst = c->dst;
+          t.bulk = ((((uintptr_t)src) | ((uintptr_t)dst)) & 15) == 0 ? (t.cnt & ~3u) : 0u;
+          mbar_arrive_expect_tx(&S.bar, t.bulk * 8u);  // two 4-byte columns
+          if (t.bulk) {
+            int32_t* cols = reinterpret_cast<int32_t*>(&S.keys[0]);
+            bulk_g2s(cols, src + base, t.bulk * 4u, &S.bar);
+            bulk_g2s(cols + kSortTile, dst + base, t.bulk * 4u, &S.bar);
+          }
+        }
+      }
+    }
+    S.t = t;
+    // the tile a block will claim about one wave of resident blocks from now
+    // goes to L2 already, so that block's copy does not wait on DRAM
+    const uint32_t ahead = g + kPrefetchAhead;
+    if (ahead < total) {
+      const uint32_t ps = m.nseg > 1 ? seg_of(m, ahead) : 0u;
+      const uint32_t pt = ahead - (m.nseg > 1 ? __ldg(m.start + ps) : 0u);
+      const Ctl* pc = ctls + ps;
+      const SortCtl& psc = which ? pc->in_sort : pc->out_sort;
+      const uint32_t pn = psc.n, pb = pt * (uint32_t)kSortTile;
+      if (psc.pass[pass].active && pb < pn) {
+        const uint32_t pcnt = min((uint32_t)kSortTile, pn - pb);
+        const uint64_t* pin = psc.pass[pass].in;
+        if (pin) {
+          if (pcnt & ~1u) bulk_prefetch_l2(pin + pb, (pcnt & ~1u) * 8u);
+        } else if (((((uintptr_t)pc->src) | ((uintptr_t)pc->dst)) & 15) == 0 && (pcnt & ~3u)) {
+          bulk_prefetch_l2(pc->src + pb, (pcnt & ~3u) * 4u);
+          bulk_prefetch_l2(pc->dst + pb, (pcnt & ~3u) * 4u);
+        }
+      }
+    }
   }
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w) {
@@ -460,10 +544,10 @@ __global__ void __launch_bounds__(kSortThreads, 4)
   }
   if (tid < kSortWarps) S.mask[tid][kRadix] = 0;
   __syncthreads();
-  if (!S.claim.valid) return;
-  Ctl* __restrict__ ctl = ctls + S.claim.seg;
-  SortCtl& sc = which ? ctl->in_sort : ctl->out_sort;
-  const uint32_t tile = S.claim.tile;
+  const SweepTile t = S.t;
+  if (!t.valid) return;
+  Ctl* __restrict__ ctl = ctls + t.seg;
+  const uint32_t tile = t.tile;
   const int reg = gpass & 1, nreg = reg ^ 1;
   if (tile < ctl->status_rows) {
     // clear this tile's row (and, for a chunk's first tile, the chunk's row)
@@ -475,58 +559,38 @@ __global__ void __launch_bounds__(kSortThreads, 4)
       ctl->chunk_inc[nreg][(size_t)cidx * kRadix + tid] = 0;
     }
   }
-  const PassDesc pd = sc.pass[pass];
-  const uint32_t n = sc.n;
+  if (!t.work) return;
+  const uint32_t n = t.n, cnt = t.cnt, bulk = t.bulk;
   const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
-  if (!pd.active || tile >= ntiles) return;
   const uint32_t base = tile * (uint32_t)kSortTile;
-  const uint32_t cnt = min((uint32_t)kSortTile, n - base);
-  const uint64_t* __restrict__ in = pd.in;
-  const int32_t* __restrict__ src = ctl->src;
-  const int32_t* __restrict__ dst = ctl->dst;
-  int32_t* cols = reinterpret_cast<int32_t*>(&S.keys[0]);  // packed pass: src | dst
-  // 0. bulk copy of the tile (what is not a multiple of 16 bytes, or not
-  //    16-byte aligned, comes in with plain loads)
-  uint32_t bulk;
-  if (in) bulk = cnt & ~1u;
-  else bulk = ((((uintptr_t)src) | ((uintptr_t)dst)) & 15) == 0 ? (cnt & ~3u) : 0u;
-  if (tid == 0) {
-    mbar_arrive_expect_tx(&S.bar, bulk * 8u);  // 8-byte keys, or two 4-byte columns
-    if (bulk) {
-      if (in) {
-        bulk_g2s(&S.keys[0], in + base, bulk * 8u, &S.bar);
-      } else {
-        bulk_g2s(cols, src + base, bulk * 4u, &S.bar);
-        bulk_g2s(cols + kSortTile, dst + base, bulk * 4u, &S.bar);
+  if (cnt > bulk) {
+    if (t.in) {
+      for (uint32_t j = bulk + tid; j < cnt; j += kSortThreads) S.keys[j] = t.in[base + j];
+    } else {
+      int32_t* cols = reinterpret_cast<int32_t*>(&S.keys[0]);
+      for (uint32_t j = bulk + tid; j < cnt; j += kSortThreads) {
+        cols[j] = ctl->src[base + j];
+        cols[kSortTile + j] = ctl->dst[base + j];
       }
     }
-    S.ok = mbar_wait_bounded(&S.bar, 0, &ctl->err) ? 1u : 0u;
   }
-  if (in) {
-    for (uint32_t j = bulk + tid; j < cnt; j += kSortThreads) S.keys[j] = in[base + j];
-  } else {
-    for (uint32_t j = bulk + tid; j < cnt; j += kSortThreads) {
-      cols[j] = src[base + j];
-      cols[kSortTile + j] = dst[base + j];
-    }
-  }
-  __syncthreads();
-  if (!S.ok) {  // the copy did not land in time (never expected)
+  // every thread waits for the copy; the block agrees before going on
+  const bool ok = mbar_wait_bounded(&S.bar, 0, &ctl->err);
+  if (!__syncthreads_and(ok)) {  // the copy did not land in time (never expected)
     if (tid == 0) {
       atomicOr(&ctl->err, kErrLookback);
       mbar_wait_bounded(&S.bar, 0, nullptr);
     }
     return;
   }
-  while (!mbar_try_wait(&S.bar, 0)) {
-  }
+  SortCtl& sc = which ? ctl->in_sort : ctl->out_sort;
   const bool full = cnt == (uint32_t)kSortTile;
-  if (!HI && !in) {
-    if (full) sweep_body<BYTE, HI, true, true>(S, ctl, sc, pd, tile, ntiles, cnt, n, pass, reg);
-    else sweep_body<BYTE, HI, true, false>(S, ctl, sc, pd, tile, ntiles, cnt, n, pass, reg);
+  if (!HI && !t.in) {
+    if (full) sweep_body<BYTE, HI, true, true>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
+    else sweep_body<BYTE, HI, true, false>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
   } else {
-    if (full) sweep_body<BYTE, HI, false, true>(S, ctl, sc, pd, tile, ntiles, cnt, n, pass, reg);
-    else sweep_body<BYTE, HI, false, false>(S, ctl, sc, pd, tile, ntiles, cnt, n, pass, reg);
+    if (full) sweep_body<BYTE, HI, false, true>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
+    else sweep_body<BYTE, HI, false, false>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
   }
 }
 
