@@ -518,6 +518,31 @@ typedef struct {
 RINGO_API int ringo_profile_start(void);
 RINGO_API int ringo_profile_stop(ringo_kernel_stat* out, int32_t cap, int32_t* n_out);
 
+/*
+ * Failure-injection hooks for tests of the error paths.  The paper has no
+ * counterpart; they make a failure on the host side only, so nothing on the
+ * device faults or waits without bound.
+ *
+ * ringo_test_inject_alloc_failure -- the next `skip` device allocations of
+ *   the library succeed and the one after fails (the call that made it
+ *   returns RINGO_ENOMEM and frees what it holds); then the hook disarms.
+ *   skip < 0 disarms it.  Always RINGO_OK.
+ * ringo_test_inject_lookback_timeout -- the next ringo_table_to_graph (or
+ *   _host) bounds each of its device waits by spin_limit spins (a spin is a
+ *   poll with a short sleep; the default bound is 2^21, about a second) and
+ *   its first radix pass never claims tile 0, so the tiles after it wait on
+ *   it until the bound: the call returns RINGO_ETIMEOUT and frees what it
+ *   holds.  EINVAL unless 1 <= spin_limit <= 2^21.  Taken by the next
+ *   conversion on any thread.
+ * ringo_test_pool_used -- bytes currently allocated from the library's
+ *   device pool on the current device (the pool keeps freed memory cached;
+ *   this counts only live allocations, after their stream has reached the
+ *   frees).  EINVAL for NULL, ECUDA without a usable device.
+ */
+RINGO_API int ringo_test_inject_alloc_failure(int32_t skip);
+RINGO_API int ringo_test_inject_lookback_timeout(uint32_t spin_limit);
+RINGO_API int ringo_test_pool_used(uint64_t* bytes);
+
 #ifdef __cplusplus
 }
 #endif

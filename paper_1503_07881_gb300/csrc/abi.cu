@@ -167,6 +167,13 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
     }                                  \
   } while (0)
     const Launch run = solo_launch(dctl, hctl, n);
+    if (const uint32_t lim = take_lookback_timeout()) {
+      // failure-detection test: every wait of this conversion is bounded by
+      // `lim` spins, and the first radix pass starts claiming at slot 1, so
+      // its tile 0 is never processed and the tiles after it wait on it
+      hctl->spin_limit = lim;
+      hctl->solo_counters[1] = 1;
+    }
     TRY(cudaMemcpyAsync(dctl, hctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     // status region 0 must start clear; each pass clears the other region
     TRY(cudaMemsetAsync(ws + L.st0, 0, L.st1 - L.st0, s));

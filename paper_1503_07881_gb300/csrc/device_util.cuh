@@ -38,11 +38,12 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
 }
-// Back off in a spin loop; true once the wait has exceeded kSpinLimit.
-__device__ __forceinline__ bool spin_backoff(uint32_t& spins) {
+// Back off in a spin loop; true once the wait has exceeded `limit` spins
+// (0: kSpinLimit).
+__device__ __forceinline__ bool spin_backoff(uint32_t& spins, uint32_t limit = 0) {
   ++spins;
   if (spins > 32) __nanosleep(spins > 4096 ? 512 : 64);
-  return spins > kSpinLimit;
+  return spins > (limit ? limit : kSpinLimit);
 }
 
 // ---- mbarrier + bulk asynchronous copy (global -> shared) ----
@@ -101,12 +102,14 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* gsrc, uint32_t byte
 // Bounded wait for a bulk copy phase.  Gives up (returns false) after about a
 // second, or at once when another block has already recorded an error.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
-                                                  const volatile uint32_t* err) {
+                                                  const volatile uint32_t* err,
+                                                  uint32_t limit = 0) {
+  const uint32_t lim = limit ? limit : kSpinLimit;
   uint32_t spins = 0;
   while (!mbar_try_wait(bar, parity)) {
     ++spins;
     if (err && (spins & 1023) == 0 && *err) return false;
-    if (spins > kSpinLimit) return false;
+    if (spins > lim) return false;
   }
   return true;
 }
@@ -174,6 +177,7 @@ struct ScanChunks {
   uint64_t* agg;   // [chunks] packed sums added by the chunk's tiles
   uint64_t* inc;   // [chunks] kScanInc | inclusive prefix once known
   uint32_t* cnt;   // [chunks] tiles that have added their value
+  uint32_t limit;  // bound of the waits (0: kSpinLimit)
 };
 
 // Two-level tile prefix for the compaction kernels: like warp_lookback, but a
@@ -209,7 +213,7 @@ __device__ __forceinline__ uint64_t warp_lookback2(uint64_t* status, ScanChunks 
       const int stop = incm ? __ffs(incm) - 1 : cnt_in;
       const uint32_t missing = __ballot_sync(0xFFFFFFFFu, lane < stop && (s >> 62) == 0);
       if (missing) {
-        if (spin_backoff(spins) || ((spins & 255) == 0 && *verr)) {
+        if (spin_backoff(spins, ch.limit) || ((spins & 255) == 0 && *verr)) {
           if (lane == 0) atomicOr(err, kErrScan);
           return excl;
         }
@@ -236,7 +240,7 @@ __device__ __forceinline__ uint64_t warp_lookback2(uint64_t* status, ScanChunks 
     const int stop = incm ? __ffs(incm) - 1 : 32;
     const uint32_t ready = __ballot_sync(0xFFFFFFFFu, k < 0 || done || lane >= stop);
     if (ready != 0xFFFFFFFFu) {
-      if (spin_backoff(spins) || ((spins & 255) == 0 && *verr)) {
+      if (spin_backoff(spins, ch.limit) || ((spins & 255) == 0 && *verr)) {
         if (lane == 0) atomicOr(err, kErrScan);
         return excl;
       }

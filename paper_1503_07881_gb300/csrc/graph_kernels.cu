@@ -21,7 +21,8 @@ constexpr int kWarps = kScanThreads / 32;
 
 __device__ __forceinline__ int32_t unbias(uint32_t b) { return (int32_t)(b ^ kBias); }
 __device__ __forceinline__ ScanChunks chunks_of(const Ctl* ctl, int i) {
-  return ScanChunks{ctl->scan_chunk_agg[i], ctl->scan_chunk_inc[i], ctl->scan_chunk_cnt[i]};
+  return ScanChunks{ctl->scan_chunk_agg[i], ctl->scan_chunk_inc[i], ctl->scan_chunk_cnt[i],
+                    ctl->spin_limit};
 }
 }  // namespace
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
 #include <map>
 #include <mutex>
@@ -13,6 +14,7 @@
 #include <vector>
 
 #include "../../include/ringo.h"
+#include "ringo_internal.cuh"
 
 namespace ringo {
 
@@ -43,7 +45,31 @@ static cudaMemPool_t device_pool(int dev) {
   return pool;
 }
 
+// ------------------------------------------------------------ test hooks --
+// Failures made on the host for the failure-detection tests: nothing on the
+// device faults or hangs.  g_fail_countdown: allocations left to succeed
+// before one fails (-1: none armed).  g_lookback_timeout: spin bound given
+// to the next conversion, whose first radix pass then never claims its
+// first tile, so that tile's successors wait on it until the bound.
+static std::atomic<int64_t> g_fail_countdown{-1};
+static std::atomic<uint32_t> g_lookback_timeout{0};
+
+static bool injected_alloc_failure() {
+  int64_t c = g_fail_countdown.load();
+  while (c >= 0) {
+    if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 0;
+  }
+  return false;
+}
+
+uint32_t take_lookback_timeout() { return g_lookback_timeout.exchange(0u); }
+
 void* pool_alloc(size_t bytes, cudaStream_t s) {
+  if (injected_alloc_failure()) {
+    set_error(std::string("device allocation of ") + std::to_string(bytes) +
+              " bytes failed: injected failure (test hook)");
+    return nullptr;
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     set_error("cudaGetDevice failed");
@@ -227,5 +253,38 @@ extern "C" int ringo_profile_stop(ringo_kernel_stat* out, int32_t cap, int32_t* 
     ringo::g_event_cache.push_back(r.b);
   }
   ringo::g_prof.clear();
+  return RINGO_OK;
+}
+
+extern "C" int ringo_test_inject_alloc_failure(int32_t skip) {
+  ringo::g_fail_countdown.store(skip < 0 ? -1 : (int64_t)skip);
+  return RINGO_OK;
+}
+
+extern "C" int ringo_test_inject_lookback_timeout(uint32_t spin_limit) {
+  if (spin_limit == 0 || spin_limit > ringo::kSpinLimit) {
+    ringo::set_error("ringo_test_inject_lookback_timeout: spin_limit outside [1, 2^21]");
+    return RINGO_EINVAL;
+  }
+  ringo::g_lookback_timeout.store(spin_limit);
+  return RINGO_OK;
+}
+
+extern "C" int ringo_test_pool_used(uint64_t* bytes) {
+  if (!bytes) return RINGO_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    ringo::set_error("no usable current device");
+    return RINGO_ECUDA;
+  }
+  cudaMemPool_t pool = ringo::device_pool(dev);
+  if (!pool) return RINGO_ECUDA;
+  uint64_t used = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+    cudaGetLastError();
+    return RINGO_ECUDA;
+  }
+  *bytes = used;
   return RINGO_OK;
 }

@@ -20,6 +20,9 @@ void* pool_alloc(size_t bytes, cudaStream_t s);
 void pool_free(void* p, cudaStream_t s);
 // Free device memory plus the pool's cached, unused bytes.
 uint64_t pool_available();
+// Test hook: the spin bound armed for the next conversion (0: none); taking
+// it disarms it.
+uint32_t take_lookback_timeout();
 
 // Pinned host staging buffers, cached and reused.
 void* pinned_get(size_t bytes);

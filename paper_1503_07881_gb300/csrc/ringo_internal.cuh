@@ -48,6 +48,7 @@ constexpr uint32_t kErrScan = 2u;       // a scan look-back wait gave up
 constexpr uint32_t kErrRemap = 4u;      // a run index outside its map (bug)
 
 // A bounded wait: about a second at most before the kernel records an error.
+// A control block may set a lower bound of its own (Ctl::spin_limit).
 constexpr uint32_t kSpinLimit = 1u << 21;
 
 // radix look-back status word (one per tile and digit), 32 bits:
@@ -96,6 +97,7 @@ struct alignas(16) Ctl {
   uint32_t n_rows;
   uint32_t E, Vs, Vd, V;
   uint32_t err;
+  uint32_t spin_limit;        // bound of every device wait (0: kSpinLimit)
   // inputs
   const int32_t* src;
   const int32_t* dst;

@@ -227,7 +227,7 @@ __device__ __forceinline__ uint32_t digit_lookback2(const uint32_t* __restrict__
     if (done) return excl;
     j -= used;
     if (stall) {
-      if (spin_backoff(spins) || ((spins & 255) == 0 && *verr)) {
+      if (spin_backoff(spins, ctl->spin_limit) || ((spins & 255) == 0 && *verr)) {
         atomicOr(&ctl->err, kErrLookback);
         return excl;
       }
@@ -266,7 +266,7 @@ __device__ __forceinline__ uint32_t digit_lookback2(const uint32_t* __restrict__
     if (done) return excl;
     cc -= used;
     if (stall) {
-      if (spin_backoff(spins) || ((spins & 255) == 0 && *verr)) {
+      if (spin_backoff(spins, ctl->spin_limit) || ((spins & 255) == 0 && *verr)) {
         atomicOr(&ctl->err, kErrLookback);
         return excl;
       }
@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(kSortThreads, 4)
     }
   }
   // every thread waits for the copy; the block agrees before going on
-  const bool ok = mbar_wait_bounded(&S.bar, 0, &ctl->err);
+  const bool ok = mbar_wait_bounded(&S.bar, 0, &ctl->err, ctl->spin_limit);
   if (!__syncthreads_and(ok)) {  // the copy did not land in time (never expected)
     if (tid == 0) {
       atomicOr(&ctl->err, kErrLookback);

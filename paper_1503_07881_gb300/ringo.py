@@ -103,6 +103,9 @@ SIGNATURES = {
     "ringo_table_select": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int, ctypes.c_int, _I32, _P, _P]),
     "ringo_table_join": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I64, _P, _P, _I64, _P,
                                         _P]),
+    "ringo_test_inject_alloc_failure": (ctypes.c_int, [_I32]),
+    "ringo_test_inject_lookback_timeout": (ctypes.c_int, [ctypes.c_uint32]),
+    "ringo_test_pool_used": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64)]),
     "ringo_profile_start": (ctypes.c_int, []),
     "ringo_profile_stop": (ctypes.c_int, [ctypes.POINTER(KernelStat), _I32, _P]),
 }
@@ -380,6 +383,26 @@ def ringo_profile_stop() -> list[dict]:
     _check(load().ringo_profile_stop(arr, cap, ctypes.byref(n)), "ringo_profile_stop")
     return [{"name": arr[i].name.decode(), "launches": arr[i].launches,
              "total_ms": arr[i].total_ms} for i in range(min(n.value, cap))]
+
+
+def ringo_test_inject_alloc_failure(skip: int) -> None:
+    """Test hook: the device allocation after the next `skip` ones fails
+    (skip < 0 disarms)."""
+    _check(load().ringo_test_inject_alloc_failure(int(skip)), "ringo_test_inject_alloc_failure")
+
+
+def ringo_test_inject_lookback_timeout(spin_limit: int) -> None:
+    """Test hook: the next conversion's waits are bounded by `spin_limit`
+    spins and its first radix pass leaves tile 0 unclaimed."""
+    _check(load().ringo_test_inject_lookback_timeout(int(spin_limit)),
+           "ringo_test_inject_lookback_timeout")
+
+
+def ringo_test_pool_used() -> int:
+    """Test hook: bytes allocated from the library's device pool now."""
+    v = ctypes.c_uint64()
+    _check(load().ringo_test_pool_used(ctypes.byref(v)), "ringo_test_pool_used")
+    return v.value
 
 
 def ringo_version() -> str:

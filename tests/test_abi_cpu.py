@@ -61,3 +61,16 @@ def test_undirected_row_limit_checked_before_any_device_work():
     h = ctypes.c_void_p()
     rc = lib.ringo_table_to_undirected_graph(fake, fake, 1 << 30, None, ctypes.byref(h))
     assert rc == ringo.RINGO_ERANGE and not h.value
+
+
+def test_failure_injection_hooks_argument_handling():
+    """The test hooks check their arguments before arming anything (the
+    failures they make are exercised on the GPU in test_gpu_faults.py)."""
+    lib = ringo.load()
+    assert lib.ringo_test_inject_lookback_timeout(0) == ringo.RINGO_EINVAL
+    assert lib.ringo_test_inject_lookback_timeout((1 << 21) + 1) == ringo.RINGO_EINVAL
+    assert b"spin_limit" in lib.ringo_last_error()
+    assert lib.ringo_test_pool_used(None) == ringo.RINGO_EINVAL
+    # arming and disarming the allocation failure touches no device
+    assert lib.ringo_test_inject_alloc_failure(3) == ringo.RINGO_OK
+    assert lib.ringo_test_inject_alloc_failure(-1) == ringo.RINGO_OK
