@@ -102,6 +102,33 @@ RINGO_API int ringo_table_to_graph(const int32_t* src, const int32_t* dst, int64
 RINGO_API int ringo_table_to_graph_host(const int32_t* h_src, const int32_t* h_dst, int64_t nrows,
                               void* stream, ringo_graph** out);
 
+/*
+ * ringo_table_to_graph_host_io -- Section 3.4 conversion from host columns
+ * to host arrays in one call, for callers whose table and result live in
+ * host memory: the columns go up, the graph is built on the device, and the
+ * five arrays come back into caller-owned host buffers (layout as
+ * ringo_graph_copy_to_host).  The out-CSR (node_ids, out_off, out_nbr) is
+ * final before the in-sort starts and is copied back on a second stream
+ * while the in-CSR is built; in_off and in_nbr follow.  Pinned host buffers
+ * (cudaHostAlloc or registered) let the copies run at the link's rate and
+ * overlap the kernels; pageable ones work but serialise.
+ *   h_src, h_dst      host columns of nrows int32 IDs (borrowed for the call)
+ *   h_node_ids        node_capacity entries   } caller-owned outputs;
+ *   h_out_off, h_in_off  node_capacity + 1    } 2 * nrows nodes and nrows
+ *   h_out_nbr, h_in_nbr  edge_capacity        } edges always suffice
+ *   num_nodes, num_edges  host outputs: V and E
+ * Errors: EINVAL (NULL pointer, nrows < 0), ERANGE (nrows >= 2^31, or a
+ * capacity below V or E: found during the call, nothing of the graph is
+ * copied then), ENOMEM, ECUDA, ETIMEOUT.  Device memory is allocated for
+ * the call's duration only and freed before it returns.  Blocks.
+ */
+RINGO_API int ringo_table_to_graph_host_io(const int32_t* h_src, const int32_t* h_dst,
+                                           int64_t nrows, void* stream, int32_t* h_node_ids,
+                                           int64_t* h_out_off, int32_t* h_out_nbr,
+                                           int64_t* h_in_off, int32_t* h_in_nbr,
+                                           int64_t node_capacity, int64_t edge_capacity,
+                                           int64_t* num_nodes, int64_t* num_edges);
+
 RINGO_API int ringo_graph_num_nodes(const ringo_graph* g, int64_t* v);
 RINGO_API int ringo_graph_num_edges(const ringo_graph* g, int64_t* e);
 RINGO_API int ringo_graph_get_info(const ringo_graph* g, ringo_graph_info* info);

@@ -1,11 +1,13 @@
 // C ABI of libringo (declared in include/ringo.h) and the host side of the
 // table->graph conversion (paper, Section 3.4).  The kernel sequence itself
 // is in pipeline.cu:
-//   phase 1  histogram, 4 dst passes, dst ranks, 4 src passes, dedup,
-//            plan + 4 in-sort passes, destination-run starts
+//   phase 1  histogram, 4 dst passes, dst ranks, 4 src passes, dedup
 //   -- stream sync: E, Vs, Vd; node arrays and rank maps allocated --
-//   phase 2  merge, block tables, remap
+//   phase 2  merge, block tables, out-direction remap: the out-CSR is done
+//   phase 3  plan + 4 in-sort passes, destination runs (in_nbr), in_off
 //   -- stream sync: V and the error word --
+// With host outputs (ringo_table_to_graph_host_io) the out-CSR goes back to
+// the host on a second stream while phase 3 runs.
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -118,8 +120,21 @@ void place_rank_region(Ctl* h, int32_t* base, uint32_t Vs, uint32_t Vd) {
   h->dst_blk = h->src_blk + up4((Vs + 31) / 32);
 }
 
-// The conversion proper, for 1 <= n < 2^31 device rows.
-int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph* g) {
+// Caller-owned host arrays for the result (ringo_table_to_graph_host_io).
+struct HostOut {
+  int32_t* node_ids;
+  int64_t* out_off;
+  int32_t* out_nbr;
+  int64_t* in_off;
+  int32_t* in_nbr;
+  int64_t node_capacity, edge_capacity;
+};
+
+// The conversion proper, for 1 <= n < 2^31 device rows.  With `ho`, the
+// result is also copied into the caller's host arrays: the out-CSR on a
+// second stream while phase 3 runs, the in-CSR after it.
+int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph* g,
+            const HostOut* ho = nullptr) {
   cudaStream_t s = g->stream;
   const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
   const WsLayout L = layout_for(n);
@@ -131,6 +146,14 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
   int32_t* ranks = nullptr;
   int rc = RINGO_OK;
   Ctl* dctl = (Ctl*)(ws + L.ctl);
+  cudaStream_t cs = nullptr;  // host outputs: the out-CSR's copy stream
+  cudaEvent_t ev2 = nullptr;  // host outputs: phase 2 done
+  if (ho && (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaEventCreateWithFlags(&ev2, cudaEventDisableTiming) != cudaSuccess)) {
+    set_error("copy stream or event creation failed");
+    rc = RINGO_ECUDA;
+    goto done;
+  }
   if (!g->out_nbr || !g->in_nbr || !hctl) {
     rc = RINGO_ENOMEM;
     if (!hctl) set_error("pinned staging allocation failed");
@@ -207,6 +230,36 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
     place_rank_region(hctl, ranks, hctl->Vs, hctl->Vd);
     TRY(cudaMemcpyAsync(dctl, hctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     if ((rc = enqueue_phase2(run, s)) != RINGO_OK) goto done;
+    if (ho) {
+      // V is known once phase 2 is done; the out-CSR can go back while the
+      // in-sort runs
+      if (hctl->E > ho->edge_capacity) {
+        set_error("edge_capacity is below the number of distinct edges");
+        rc = RINGO_ERANGE;
+        goto done;
+      }
+      TRY(cudaMemcpyAsync(&hctl->V, &dctl->V, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+      TRY(cudaEventRecord(ev2, s));
+      if ((rc = enqueue_phase3(run, s)) != RINGO_OK) goto done;
+      TRY(cudaEventSynchronize(ev2));
+      const uint64_t V = hctl->V;
+      if ((int64_t)V > ho->node_capacity) {
+        set_error("node_capacity is below the number of nodes");
+        rc = RINGO_ERANGE;
+        goto done;
+      }
+      TRY(cudaStreamWaitEvent(cs, ev2, 0));
+      {
+        ProfScope ps("out_csr_d2h", cs);
+        if (V) TRY(cudaMemcpyAsync(ho->node_ids, g->node_ids, 4 * V, cudaMemcpyDeviceToHost, cs));
+        TRY(cudaMemcpyAsync(ho->out_off, g->out_off, 8 * (V + 1), cudaMemcpyDeviceToHost, cs));
+        if (hctl->E)
+          TRY(cudaMemcpyAsync(ho->out_nbr, g->out_nbr, 4ull * hctl->E, cudaMemcpyDeviceToHost,
+                              cs));
+      }
+    } else {
+      if ((rc = enqueue_phase3(run, s)) != RINGO_OK) goto done;
+    }
     TRY(cudaMemcpyAsync(hctl, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
     if (hctl->err & (kErrLookback | kErrScan)) {
@@ -226,9 +279,25 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
     g->info.num_dst_nodes = hctl->Vd;
     g->info.out_sort_passes = (int32_t)hctl->out_sort.active_passes;
     g->info.in_sort_passes = (int32_t)hctl->in_sort.active_passes;
+    if (ho) {
+      const uint64_t V = hctl->V, E = hctl->E;
+      ProfScope ps("in_csr_d2h", s);
+      TRY(cudaMemcpyAsync(ho->in_off, g->in_off, 8 * (V + 1), cudaMemcpyDeviceToHost, s));
+      if (E) TRY(cudaMemcpyAsync(ho->in_nbr, g->in_nbr, 4 * E, cudaMemcpyDeviceToHost, s));
+    }
 #undef TRY
   }
 done:
+  if (cs) {
+    // the copy stream's work must be over before its buffers can go
+    cudaStreamSynchronize(cs);
+    cudaStreamDestroy(cs);
+  }
+  if (ev2) cudaEventDestroy(ev2);
+  if (ho && rc == RINGO_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error(std::string("device->host copy: ") + cudaGetErrorString(cudaGetLastError()));
+    rc = RINGO_ECUDA;
+  }
   pool_free(ranks, s);
   pool_free(ws, s);
   if (hctl) pinned_put(hctl);
@@ -329,6 +398,72 @@ int ringo_table_to_graph(const int32_t* src, const int32_t* dst, int64_t nrows, 
 int ringo_table_to_graph_host(const int32_t* h_src, const int32_t* h_dst, int64_t nrows,
                               void* stream, ringo_graph** out) {
   return table_to_graph_impl(h_src, h_dst, nrows, stream, out, true);
+}
+
+int ringo_table_to_graph_host_io(const int32_t* h_src, const int32_t* h_dst, int64_t nrows,
+                                 void* stream, int32_t* h_node_ids, int64_t* h_out_off,
+                                 int32_t* h_out_nbr, int64_t* h_in_off, int32_t* h_in_nbr,
+                                 int64_t node_capacity, int64_t edge_capacity,
+                                 int64_t* num_nodes, int64_t* num_edges) {
+  if (!num_nodes || !num_edges || !h_out_off || !h_in_off || nrows < 0 ||
+      (nrows > 0 && (!h_src || !h_dst || !h_node_ids || !h_out_nbr || !h_in_nbr))) {
+    set_error("ringo_table_to_graph_host_io: nrows < 0 or NULL pointer");
+    return RINGO_EINVAL;
+  }
+  if (nrows > 0x7FFFFFFF) {
+    set_error("nrows exceeds 2^31 - 1");
+    return RINGO_ERANGE;
+  }
+  *num_nodes = 0;
+  *num_edges = 0;
+  if (nrows == 0) {
+    h_out_off[0] = 0;
+    h_in_off[0] = 0;
+    return RINGO_OK;
+  }
+  ringo_graph* g = new (std::nothrow) ringo_graph();
+  if (!g) return RINGO_ENOMEM;
+  g->stream = (cudaStream_t)stream;
+  cudaGetDevice(&g->device);
+  const size_t bytes = sizeof(int32_t) * (size_t)nrows;
+  int32_t* d_src = nullptr;
+  int32_t* d_dst = nullptr;
+  {
+    HostScope hs("host:input_alloc");
+    d_src = (int32_t*)pool_alloc(bytes, g->stream);
+    d_dst = d_src ? (int32_t*)pool_alloc(bytes, g->stream) : nullptr;
+  }
+  int rc = RINGO_OK;
+  if (!d_src || !d_dst) {
+    rc = RINGO_ENOMEM;
+  } else {
+    bool copied;
+    {
+      ProfScope ps("input_h2d", g->stream);
+      copied = cudaMemcpyAsync(d_src, h_src, bytes, cudaMemcpyHostToDevice, g->stream) ==
+                   cudaSuccess &&
+               cudaMemcpyAsync(d_dst, h_dst, bytes, cudaMemcpyHostToDevice, g->stream) ==
+                   cudaSuccess;
+    }
+    if (!copied) {
+      set_error(std::string("host->device copy failed: ") +
+                cudaGetErrorString(cudaGetLastError()));
+      rc = RINGO_ECUDA;
+    } else {
+      const HostOut ho{h_node_ids, h_out_off, h_out_nbr, h_in_off, h_in_nbr, node_capacity,
+                       edge_capacity};
+      rc = convert(d_src, d_dst, (uint32_t)nrows, g, &ho);
+    }
+  }
+  pool_free(d_src, g->stream);
+  pool_free(d_dst, g->stream);
+  if (rc == RINGO_OK) {
+    *num_nodes = g->info.num_nodes;
+    *num_edges = g->info.num_edges;
+  }
+  free_graph_arrays(g);
+  delete g;
+  return rc;
 }
 
 int ringo_table_to_undirected_graph(const int32_t* src, const int32_t* dst, int64_t nrows,

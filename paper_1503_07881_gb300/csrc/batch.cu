@@ -731,6 +731,7 @@ int run_wave(const ringo_base* b, const uint32_t* d_lo, const uint32_t* d_cnt,
     k_init_ctls<<<nseg, 256, 0, cs>>>(d_ctls, d_desc);
     prc = enqueue_phase1(L, cs);
     if (prc == RINGO_OK) prc = enqueue_phase2(L, cs);
+    if (prc == RINGO_OK) prc = enqueue_phase3(L, cs);
     if (prc == RINGO_OK && topk) {
       const SegMap tiles{d_ttiles, nseg};
       const uint32_t grid = persistent_blocks(8);

@@ -255,10 +255,15 @@ void launch_dst_rank(const Launch& L, uint32_t* counter, cudaStream_t s) {
 
 // ------------------------------------------------------------------ K5 ----
 // Input: the in-sorted keys (dst-run index << 32 | source-run index), E of
-// them, in (dst, src) order.  Writes in_nbr[k] = source-run index (turned
-// into a node index later) and, at each change of dst-run index d, the run's
-// first in-edge udst_start[d] = k (udst_start[Vd] = E).  Every dst-run index
-// occurs, so no compaction is needed.
+// them, in (dst, src) order.  Writes in_nbr[k] = the node index of the
+// source run (phase 2 has built the source-run -> node map) and, at each
+// change of dst-run index d, the run's first in-edge udst_start[d] = k
+// (udst_start[Vd] = E, in_off[V] = E).  Every dst-run index occurs, so no
+// compaction is needed.
+__device__ __forceinline__ int32_t map_index(const uint32_t* __restrict__ blk,
+                                             const int32_t* __restrict__ map, uint32_t len,
+                                             uint32_t j, uint32_t* err);
+
 __global__ void __launch_bounds__(256)
     k_dst_runs(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
   __shared__ Claim s_cl;
@@ -266,14 +271,21 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   if (!s_cl.valid) return;
   Ctl* __restrict__ ctl = ctls + s_cl.seg;
-  const uint32_t E = ctl->E, Vd = ctl->Vd;
+  const uint32_t E = ctl->E, Vd = ctl->Vd, Vs = ctl->Vs, V = ctl->V;
   const uint32_t base = s_cl.tile * (uint32_t)kScanTile;
   if (base >= E) return;
   const uint32_t end = min(E, base + (uint32_t)kScanTile);
   const uint64_t* __restrict__ keys = ctl->in_sort.result;
   int32_t* __restrict__ in_nbr = ctl->in_nbr;
   int32_t* __restrict__ ustart = ctl->udst_start;
-  if (base == 0 && threadIdx.x == 0) ustart[Vd] = (int32_t)E;
+  if (base == 0 && threadIdx.x == 0) {
+    ustart[Vd] = (int32_t)E;
+    ctl->in_off[V] = (int64_t)E;
+  }
+  // when every node is a source the source-run index is the node index
+  const bool ident = Vs == V;
+  const uint32_t* __restrict__ blk = ctl->src_blk;
+  const int32_t* __restrict__ map = ctl->src_rank;
   // a dst-run index is always below Vd; anything else is recorded, not written
   for (uint32_t k = base + threadIdx.x; k < end; k += blockDim.x) {
     const uint64_t key = __ldcs(keys + k);
@@ -282,12 +294,39 @@ __global__ void __launch_bounds__(256)
       if (d < Vd) ustart[d] = (int32_t)k;
       else atomicOr(&ctl->err, kErrRemap);
     }
-    in_nbr[k] = (int32_t)(uint32_t)key;
+    const uint32_t sidx = (uint32_t)key;
+    __stcs(in_nbr + k, ident ? (int32_t)sidx : map_index(blk, map, Vs, sidx, &ctl->err));
   }
 }
 
 void launch_dst_runs(const Launch& L, uint32_t* counter, cudaStream_t s) {
   if (L.row_slots) k_dst_runs<<<L.row_slots, 256, 0, s>>>(L.ctls, L.rows, counter);
+}
+
+// in_off[r] holds, after the merge, the index j of node r's first
+// destination run (the merge cursor); the run starts are known once the
+// in-sort is done: in_off[r] = udst_start[j].  Persistent over the merge
+// tiles of every segment (each covers kMergeTile nodes).
+__global__ void __launch_bounds__(256)
+    k_fill_in_off(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
+  __shared__ Claim s_cl;
+  while (true) {
+    if (threadIdx.x == 0) claim_slot(m, counter, &s_cl);
+    __syncthreads();
+    if (!s_cl.valid) return;
+    Ctl* __restrict__ ctl = ctls + s_cl.seg;
+    const uint32_t V = ctl->V, Vd = ctl->Vd;
+    const uint32_t r0 = s_cl.tile * (uint32_t)kMergeTile;
+    const uint32_t r1 = min(V, r0 + (uint32_t)kMergeTile);
+    int64_t* __restrict__ in_off = ctl->in_off;
+    const int32_t* __restrict__ ustart = ctl->udst_start;
+    for (uint32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+      const uint32_t j = (uint32_t)in_off[r];
+      if (j <= Vd) in_off[r] = ustart[j];
+      else atomicOr(&ctl->err, kErrRemap);
+    }
+    __syncthreads();
+  }
 }
 
 // ----------------------------------------------------------- node merge ---
@@ -297,6 +336,8 @@ void launch_dst_runs(const Launch& L, uint32_t* counter, cudaStream_t s) {
 // merge cursor (i, j) (src items and dst items consumed before it) gives
 //   out_off[r] = usrc_start[i]   and   in_off[r] = udst_start[j],
 // which holds for nodes in both lists and for nodes in only one of them.
+// The merge runs before the in-sort, when udst_start is not known yet, so it
+// stores j in in_off[r] and k_fill_in_off replaces it afterwards.
 // Also src_rank[i] and dst_rank[j]: the node index of each list entry.
 __device__ __forceinline__ uint32_t merge_path(const int32_t* a, uint32_t na, const int32_t* b,
                                                uint32_t nb, uint32_t diag) {
@@ -318,7 +359,7 @@ __device__ __forceinline__ uint32_t merge_path(const int32_t* a, uint32_t na, co
 // rank maps are written coalesced.
 struct MergeSmem {
   int32_t val[kMergeTile];        // usrc[i0, i1) then udst[j0, j1)
-  int32_t start[kMergeTile + 2];  // usrc_start[i0, i1] then udst_start[j0, j1]
+  int32_t start[kMergeTile + 1];  // usrc_start[i0, i1]
   int32_t rank[kMergeTile];       // tile-local node index of each input item
   uint32_t node[kMergeTile];      // emitted nodes: i | j << 12 | from_src << 24 (local)
   uint32_t sw[kWarps + 1];
@@ -360,11 +401,9 @@ __device__ __forceinline__ void merge_tile(Ctl* __restrict__ ctl, uint32_t tile,
   const uint32_t j0 = k0 - i0, j1 = k1 - i1;
   const uint32_t na = i1 - i0, nb = j1 - j0;
   const int32_t* __restrict__ us = ctl->usrc_start;
-  const int32_t* __restrict__ ud = ctl->udst_start;
   for (uint32_t t = tid; t < na; t += kScanThreads) S.val[t] = usrc[i0 + t];
   for (uint32_t t = tid; t < nb; t += kScanThreads) S.val[na + t] = udst[j0 + t];
   for (uint32_t t = tid; t <= na; t += kScanThreads) S.start[t] = us[i0 + t];
-  for (uint32_t t = tid; t <= nb; t += kScanThreads) S.start[na + 1 + t] = ud[j0 + t];
   if (tid == 0) {
     S.has_prev = i0 > 0 ? 1u : 0u;
     S.prev = i0 > 0 ? usrc[i0 - 1] : 0;
@@ -408,7 +447,7 @@ __device__ __forceinline__ void merge_tile(Ctl* __restrict__ ctl, uint32_t tile,
         const uint32_t V = unpackB(excl) + total;
         ctl->V = V;
         ctl->out_off[V] = (int64_t)ctl->E;
-        ctl->in_off[V] = (int64_t)ctl->E;
+        ctl->in_off[V] = (int64_t)Vd;  // destination-run index; E after the in-sort
       }
     }
   }
@@ -439,7 +478,7 @@ __device__ __forceinline__ void merge_tile(Ctl* __restrict__ ctl, uint32_t tile,
     const uint32_t i = p & 0xFFFu, j = (p >> 12) & 0xFFFu;
     node_ids[r0 + t] = (p >> 24) ? sa[i] : sb[j];
     out_off[r0 + t] = S.start[i];
-    in_off[r0 + t] = S.start[na + 1 + j];
+    in_off[r0 + t] = (int64_t)(j0 + j);  // destination-run cursor, see k_fill_in_off
   }
   int32_t* __restrict__ src_rank = ctl->src_rank;
   int32_t* __restrict__ dst_rank = ctl->dst_rank;
@@ -617,8 +656,9 @@ __device__ __forceinline__ void remap_range(int32_t* __restrict__ a, uint32_t ba
     a[e] = map_index(blk, map, len, (uint32_t)a[e], err);
 }
 
-// When every node is a source (Vs == V) the source-run index already is the
-// node index and in_nbr is left as it is; likewise out_nbr when Vd == V.
+// out_nbr only (k_dst_runs writes in_nbr in its final form).  When every
+// node is a destination (Vd == V) the dst-run index already is the node
+// index and out_nbr is left as it is.
 __global__ void __launch_bounds__(256)
     k_remap(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
   __shared__ Claim s_cl;
@@ -626,13 +666,16 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   if (!s_cl.valid) return;
   Ctl* __restrict__ ctl = ctls + s_cl.seg;
-  const uint32_t E = ctl->E, V = ctl->V, Vs = ctl->Vs, Vd = ctl->Vd;
+  const uint32_t E = ctl->E, V = ctl->V, Vd = ctl->Vd;
   const uint32_t base = s_cl.tile * (uint32_t)kScanTile;
   if (base >= E) return;
   const uint32_t end = min(E, base + (uint32_t)kScanTile);
   uint32_t* err = &ctl->err;
   if (Vd != V) remap_range(ctl->out_nbr, base, end, ctl->dst_blk, ctl->dst_rank, Vd, err);
-  if (Vs != V) remap_range(ctl->in_nbr, base, end, ctl->src_blk, ctl->src_rank, Vs, err);
+}
+
+void launch_fill_in_off(const Launch& L, uint32_t* counter, cudaStream_t s) {
+  k_fill_in_off<<<persistent_grid(8), 256, 0, s>>>(L.ctls, L.merge, counter);
 }
 
 void launch_remap(const Launch& L, uint32_t* counter, cudaStream_t s) {

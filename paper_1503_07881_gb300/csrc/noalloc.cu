@@ -214,6 +214,7 @@ extern "C" int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* d
   h.dst_blk = h.src_blk + up4((h.Vs + 31) / 32);
   NA_TRY(cudaMemcpyAsync(dctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
   if ((rc = enqueue_phase2(run, s)) != RINGO_OK) return rc;
+  if ((rc = enqueue_phase3(run, s)) != RINGO_OK) return rc;
   NA_TRY(cudaMemcpyAsync(&h, dctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
   NA_TRY(cudaStreamSynchronize(s));
 #undef NA_TRY

@@ -156,11 +156,11 @@ __host__ __device__ inline void place_radix_chunks(Ctl* c, int r, void* p, uint6
   c->chunk_inc[r] = reinterpret_cast<uint32_t*>(static_cast<char*>(p) + 8ull * chunks * kRadix);
 }
 
-// Merge-path splits of the merge tiles (phase 2).  They live in the radix key
-// buffer, which no phase-2 kernel reads: at most (2n + 2047) / 2048 + 1
-// words, far below its 8 (n + 1) bytes.
+// Merge-path splits of the merge tiles (phase 2).  They live in the in-CSR
+// neighbour array, which only phase 3 writes: at most (2n + 2047) / 2048 + 1
+// words, far below its n entries.
 __host__ __device__ inline uint32_t* merge_splits(const Ctl* c) {
-  return reinterpret_cast<uint32_t*>(c->keysA);
+  return reinterpret_cast<uint32_t*>(c->in_nbr);
 }
 
 constexpr uint32_t kBlkDense = 0x80000000u;
@@ -238,6 +238,7 @@ int run_pagerank(const int64_t* out_off, const int64_t* in_off, const int32_t* i
 void launch_merge(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_rank_blocks(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_remap(const Launch& L, uint32_t* counter, cudaStream_t s);
+void launch_fill_in_off(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_degrees(const int32_t* node_ids, const int64_t* off, uint32_t V,
                     const int32_t* ids, uint32_t n, int64_t* deg, cudaStream_t s);
 int launch_topk(const int32_t* node_ids, const int64_t* off, uint32_t V, uint32_t k,
@@ -246,11 +247,15 @@ int launch_topk(const int32_t* node_ids, const int64_t* off, uint32_t V, uint32_
 size_t topk_scratch_bytes(uint32_t V, uint32_t k);
 
 // The launch sequence, shared by every entry point (pipeline.cu).
-//   phase 1: histogram .. destination runs; afterwards E, Vs, Vd are final
-//   phase 2: merge, block tables, remap; needs node arrays and rank maps set
-//            in every control block (sized from Vs, Vd or from upper bounds)
+//   phase 1: histogram .. out-sort, dedup; afterwards E, Vs, Vd are final
+//   phase 2: node merge, block tables, out-direction remap; needs node
+//            arrays and rank maps set in every control block (sized from Vs,
+//            Vd or from upper bounds).  Afterwards V, node_ids, out_off and
+//            out_nbr are final (in_off holds destination-run indices).
+//   phase 3: in-sort, destination runs with the in-direction remap, in_off.
 int enqueue_phase1(const Launch& L, cudaStream_t s);
 int enqueue_phase2(const Launch& L, cudaStream_t s);
+int enqueue_phase3(const Launch& L, cudaStream_t s);
 // histogram, plan, the four dst passes, the rank step, the four src passes:
 // the out-sort alone (its keys end in out_sort.result)
 int enqueue_sort_only(const Launch& L, cudaStream_t s);

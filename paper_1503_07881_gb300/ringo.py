@@ -99,6 +99,8 @@ SIGNATURES = {
                                                        _P]),
     "ringo_graph_pagerank": (ctypes.c_int, [_P, ctypes.c_double, _I32, _P, _P]),
     "ringo_table_to_undirected_graph": (ctypes.c_int, [_P, _P, _I64, _P, _PP]),
+    "ringo_table_to_graph_host_io": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P, _P, _P, _P, _I64,
+                                                    _I64, _P, _P]),
     "ringo_graph_count_triangles": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "ringo_table_select": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int, ctypes.c_int, _I32, _P, _P]),
     "ringo_table_join": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I64, _P, _P, _I64, _P,
@@ -370,6 +372,55 @@ def ringo_table_to_graph_host(src, dst, stream=None) -> Graph:
                                          ctypes.byref(h)), "ringo_table_to_graph_host")
     del keep_s, keep_d
     return Graph(h.value, sp)
+
+
+def ringo_table_to_graph_host_io(src, dst, out: dict | None = None, stream=None) -> dict:
+    """Host columns in, host arrays out, in one call (the out-CSR comes
+    back while the in-CSR is built).  ``out`` may hold caller-owned CPU
+    tensors (pinned ones copy fastest): int32 ``node_ids`` / ``out_nbr`` /
+    ``in_nbr`` and int64 ``out_off`` / ``in_off`` with room for 2 * nrows
+    nodes and nrows edges; without it, pinned tensors of that size are made.
+    Returns a dict of views of the five arrays plus num_nodes / num_edges."""
+    def hptr(a):
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != torch.int32 or not a.is_contiguous():
+                raise ValueError("host column must be a contiguous CPU int32 tensor")
+            return a.data_ptr(), a.numel(), a
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        return a.ctypes.data, a.size, a
+
+    ps, ns, keep_s = hptr(src)
+    pd, nd, keep_d = hptr(dst)
+    if ns != nd:
+        raise ValueError("src and dst differ in length")
+    if out is None:
+        pin = torch.cuda.is_available()
+        out = {"node_ids": torch.empty(2 * ns, dtype=torch.int32, pin_memory=pin),
+               "out_off": torch.empty(2 * ns + 1, dtype=torch.int64, pin_memory=pin),
+               "out_nbr": torch.empty(max(ns, 1), dtype=torch.int32, pin_memory=pin),
+               "in_off": torch.empty(2 * ns + 1, dtype=torch.int64, pin_memory=pin),
+               "in_nbr": torch.empty(max(ns, 1), dtype=torch.int32, pin_memory=pin)}
+    want = {"node_ids": torch.int32, "out_off": torch.int64, "out_nbr": torch.int32,
+            "in_off": torch.int64, "in_nbr": torch.int32}
+    for name, dtype in want.items():
+        t = out.get(name)
+        if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"out[{name!r}] must be a contiguous CPU {dtype} tensor")
+    node_cap = out["node_ids"].numel()
+    if min(out["out_off"].numel(), out["in_off"].numel()) < node_cap + 1:
+        raise ValueError("out_off and in_off need node_ids.numel() + 1 entries")
+    v, e = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().ringo_table_to_graph_host_io(
+        ps if ns else None, pd if nd else None, ns, _stream_ptr(stream),
+        out["node_ids"].data_ptr(), out["out_off"].data_ptr(), out["out_nbr"].data_ptr(),
+        out["in_off"].data_ptr(), out["in_nbr"].data_ptr(), node_cap,
+        min(out["out_nbr"].numel(), out["in_nbr"].numel()), ctypes.byref(v), ctypes.byref(e)),
+        "ringo_table_to_graph_host_io")
+    del keep_s, keep_d
+    V, E = v.value, e.value
+    return {"num_nodes": V, "num_edges": E, "node_ids": out["node_ids"][:V],
+            "out_off": out["out_off"][:V + 1], "out_nbr": out["out_nbr"][:E],
+            "in_off": out["in_off"][:V + 1], "in_nbr": out["in_nbr"][:E]}
 
 
 def ringo_profile_start() -> None:

@@ -116,6 +116,49 @@ def test_unaligned_columns_and_host_entry():
     pins.assert_same_graph(hp.copy_to_host(), want, "pinned host entry")
 
 
+@pytest.mark.parametrize("n", [0, 1, 4097, 200_003])
+def test_host_io_entry(n):
+    """Host columns in, host arrays out: the out-CSR comes back on a second
+    stream while the in-CSR is built; the result equals the oracle's."""
+    s, d = tg.signed_table(n, max(2, n // 5), seed=17) if n else (
+        torch.empty(0, dtype=torch.int32), torch.empty(0, dtype=torch.int32))
+    want = oracle.table_to_graph(s.numpy(), d.numpy())
+    got = ringo.ringo_table_to_graph_host_io(s.pin_memory() if n else s,
+                                             d.pin_memory() if n else d)
+    pins.assert_same_graph({k: (v.numpy() if hasattr(v, "numpy") else v) for k, v in got.items()},
+                           want, f"host io, {n} rows")
+    if n:
+        # pageable numpy columns and caller-owned (pageable) outputs
+        out = {"node_ids": torch.empty(2 * n, dtype=torch.int32),
+               "out_off": torch.empty(2 * n + 1, dtype=torch.int64),
+               "out_nbr": torch.empty(n, dtype=torch.int32),
+               "in_off": torch.empty(2 * n + 1, dtype=torch.int64),
+               "in_nbr": torch.empty(n, dtype=torch.int32)}
+        got2 = ringo.ringo_table_to_graph_host_io(s.numpy(), d.numpy(), out=out)
+        pins.assert_same_graph({k: (v.numpy() if hasattr(v, "numpy") else v)
+                                for k, v in got2.items()}, want, f"host io pageable, {n} rows")
+
+
+def test_host_io_capacity_errors():
+    s, d = tg.signed_table(5000, 1000, seed=19)
+    want = oracle.table_to_graph(s.numpy(), d.numpy())
+    V = int(want["num_nodes"])
+    small = {"node_ids": torch.empty(V - 1, dtype=torch.int32),
+             "out_off": torch.empty(V, dtype=torch.int64),
+             "out_nbr": torch.empty(5000, dtype=torch.int32),
+             "in_off": torch.empty(V, dtype=torch.int64),
+             "in_nbr": torch.empty(5000, dtype=torch.int32)}
+    with pytest.raises(ringo.RingoError) as ei:
+        ringo.ringo_table_to_graph_host_io(s, d, out=small)
+    assert ei.value.status == ringo.RINGO_ERANGE
+    exact = dict(small, node_ids=torch.empty(V, dtype=torch.int32),
+                 out_off=torch.empty(V + 1, dtype=torch.int64),
+                 in_off=torch.empty(V + 1, dtype=torch.int64))
+    got = ringo.ringo_table_to_graph_host_io(s, d, out=exact)
+    pins.assert_same_graph({k: (v.numpy() if hasattr(v, "numpy") else v) for k, v in got.items()},
+                           want, "exact capacity")
+
+
 def test_degrees_and_topk():
     s, d = tg.make_table(tg.SPECS["twitter"].scaled(400_000), seed=6)
     want = oracle.table_to_graph(s.numpy(), d.numpy())
