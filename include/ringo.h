@@ -396,12 +396,15 @@ RINGO_API int ringo_select_gather(const ringo_base* b, const ringo_select* pred,
 RINGO_API int ringo_convert_batch(const ringo_base* b, const ringo_select* preds, int32_t npred,
                                   int64_t wave_rows, void* stream, ringo_batch** out);
 /*
- * ringo_batch_autotune -- picks the wave size for this predicate set: times
- * ringo_convert_batch with up to four candidate sizes (the largest that fits
- * in device memory, then halves, not below 2^24 rows) and keeps the fastest
- * for later ringo_convert_batch calls with wave_rows == 0 on the same device,
- * predicate count and row-count octave.  Without a tuned choice, wave_rows ==
- * 0 means the largest wave that fits in 85% of the available device memory.
+ * ringo_batch_autotune -- tunes batches of this shape: times
+ * ringo_convert_batch with up to four candidate wave sizes (the largest that
+ * fits in device memory, then halves, not below 2^24 rows), then, at the
+ * fastest size, every radix pass variant (ringo_sort_opts), and records the
+ * fastest combination for the GPU and the size class of the mean selection
+ * (see ringo_tune_set_cache).  Later ringo_convert_batch calls of that class
+ * with wave_rows == 0 use it (the wave capped by what fits in memory then).
+ * Without a tuned choice, wave_rows == 0 means the largest wave that fits in
+ * 85% of the available device memory, and the default pass variant.
  * Errors: as ringo_convert_batch; ENOMEM if no candidate fits.
  */
 RINGO_API int ringo_batch_autotune(const ringo_base* b, const ringo_select* preds, int32_t npred,
@@ -544,6 +547,48 @@ typedef struct {
 
 RINGO_API int ringo_profile_start(void);
 RINGO_API int ringo_profile_stop(ringo_kernel_stat* out, int32_t cap, int32_t* n_out);
+
+/*
+ * Tuning.  The radix passes have variants that suit different inputs, and
+ * batches a wave size; the best choice depends on the GPU and on the data,
+ * so it is measured on the caller's own tables and remembered per (GPU
+ * name, kind, size class): kind 0 is a single table, 1 a batch, and the size
+ * class is floor(log2(rows)) of the table or of the mean selection.  The
+ * paper has no counterpart (its conversion runs on CPU threads).
+ *   rank_method     0: a warp's lanes with the same digit find each other
+ *                      through shared-memory lane masks (default);
+ *                   1: through one warp ballot per digit bit (no shared
+ *                      atomics: better when many keys share a digit)
+ *   prefetch_waves  0..2: how far ahead, in waves of resident blocks, a
+ *                   pass asks L2 for the input of a tile (default 1)
+ *   wave_rows       batches only: rows per captured launch (0: automatic)
+ * ringo_tune_table -- times every pass variant on this table (device
+ *   columns; three conversions each, the first a warm-up) and records the
+ *   fastest for its class; later conversions of that class use it.
+ *   *best (and *best_ms, if not NULL) receive the choice.  EINVAL for a NULL
+ *   pointer or nrows <= 0; otherwise the errors of ringo_table_to_graph.
+ * ringo_tune_lookup -- the recorded choice for (current GPU, kind, class of
+ *   rows): *found = 1 and *opts, or *found = 0 and the defaults.
+ * ringo_tune_set_cache -- keep the choices in the JSON file at `path`: its
+ *   entries are read now (a missing file is created) and it is rewritten
+ *   after every new choice, so a later process reuses them.  NULL or "":
+ *   memory only.  EINVAL if the file exists and is not a tuning cache.
+ * ringo_sort_opts_force -- use these pass options for every conversion
+ *   from now on, whatever is recorded (tests and measurements of a
+ *   variant); NULL returns to the recorded choices.  EINVAL out of range.
+ */
+typedef struct {
+  int32_t rank_method;
+  int32_t prefetch_waves;
+  int64_t wave_rows;
+} ringo_sort_opts;
+
+RINGO_API int ringo_tune_table(const int32_t* src, const int32_t* dst, int64_t nrows,
+                               void* stream, ringo_sort_opts* best, double* best_ms);
+RINGO_API int ringo_tune_lookup(int32_t kind, int64_t rows, ringo_sort_opts* opts,
+                                int32_t* found);
+RINGO_API int ringo_tune_set_cache(const char* path);
+RINGO_API int ringo_sort_opts_force(const ringo_sort_opts* opts);
 
 /*
  * Failure-injection hooks for tests of the error paths.  The paper has no

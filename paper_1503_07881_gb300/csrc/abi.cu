@@ -189,7 +189,8 @@ int convert(const int32_t* d_src, const int32_t* d_dst, uint32_t n, ringo_graph*
       goto done;                       \
     }                                  \
   } while (0)
-    const Launch run = solo_launch(dctl, hctl, n);
+    Launch run = solo_launch(dctl, hctl, n);
+    run.opts = sort_opts_for(0, n);
     if (const uint32_t lim = take_lookback_timeout()) {
       // failure-detection test: every wait of this conversion is bounded by
       // `lim` spins, and the first radix pass starts claiming at slot 1, so

@@ -535,6 +535,7 @@ int solo_sort(const int32_t* a, const int32_t* b, uint32_t n, cudaStream_t s, So
   if (!h) return RINGO_ENOMEM;
   memset(h, 0, sizeof(Ctl));
   Launch run = solo_launch(dctl, h, n);
+  run.opts = sort_opts_for(0, n);
   cudaMemcpyAsync(&dctl->solo_rows[0], &h->solo_rows[0], 2 * sizeof(uint32_t),
                   cudaMemcpyHostToDevice, s);
   cudaStreamSynchronize(s);  // the staging copy is done before the buffer is reused
@@ -719,6 +720,7 @@ int run_wave(const ringo_base* b, const uint32_t* d_lo, const uint32_t* d_cnt,
   L.blocks = SegMap{d_blocks, nseg};
   L.row_slots = row_start[nseg];
   L.counters = d_counters;
+  L.opts = sort_opts_for(1, in_rows / nseg);
   int prc = RINGO_OK;
   HostScope* cap_scope = new HostScope("host:wave_capture");
   if (ok) ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
@@ -818,17 +820,7 @@ int run_wave(const ringo_base* b, const uint32_t* d_lo, const uint32_t* d_cnt,
 // wave's scratch and gathered input take about 50 B per row on top.  The
 // default is the largest wave that fits in 85% of the available device
 // memory; ringo_batch_autotune times candidates on a real predicate set and
-// the choice is kept per (device, predicate count, row-count octave).
-static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int32_t, int>, int64_t> g_tune;
-
-static std::tuple<int, int32_t, int> tune_key(int32_t npred, uint64_t rows) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  int oct = 0;
-  while ((rows >> oct) > 1) ++oct;
-  return std::make_tuple(dev, npred, oct);
-}
+// records the choice per (GPU, size class of the mean selection), tune.cu.
 
 int64_t fit_wave_rows(uint64_t total_rows) {
   const double usable = 0.85 * (double)pool_available();
@@ -840,12 +832,9 @@ int64_t fit_wave_rows(uint64_t total_rows) {
 }
 
 int64_t choose_wave_rows(int32_t npred, uint64_t total_rows) {
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tune.find(tune_key(npred, total_rows));
-    if (it != g_tune.end()) return it->second;
-  }
-  return fit_wave_rows(total_rows);
+  const int64_t fit = fit_wave_rows(total_rows);
+  const int64_t tuned = tuned_wave_rows(npred > 0 ? total_rows / (uint64_t)npred : 0);
+  return tuned > 0 ? std::min(tuned, fit) : fit;
 }
 
 uint64_t wave_seg_bytes(uint32_t n, uint32_t topk) {
@@ -1124,10 +1113,31 @@ int ringo_batch_autotune(const ringo_base* b, const ringo_select* preds, int32_t
     set_error("ringo_batch_autotune: no candidate wave fits in device memory");
     return RINGO_ENOMEM;
   }
+  // the pass variants at the chosen wave size (each run once; the variant
+  // in use has just run, so the device is warm)
+  SweepOpts best_o = sort_opts_for(1, npred > 0 ? total / (uint64_t)npred : 0);
   {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[tune_key(npred, total)] = best;
+    const ForcedOptsGuard keep;  // candidates are forced one after another
+    for (int r = 0; r <= 1; ++r) {
+      for (int pw = 0; pw <= 2; ++pw) {
+        const ringo_sort_opts o{r, pw, 0};
+        ringo_sort_opts_force(&o);
+        const auto t0 = std::chrono::steady_clock::now();
+        ringo_batch* bt = nullptr;
+        const int rc = ringo_convert_batch(b, preds, npred, best, stream, &bt);
+        const double ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        ringo_batch_free(bt);
+        if (rc != RINGO_OK) return rc;
+        if (ms < best_t) {
+          best_t = ms;
+          best_o.rank_method = r;
+          best_o.prefetch_waves = pw;
+        }
+      }
+    }
   }
+  record_tuned(1, npred > 0 ? total / (uint64_t)npred : 0, best_o, best, best_t, 0, 0);
   *best_wave_rows = best;
   if (best_ms) *best_ms = best_t;
   return RINGO_OK;

@@ -186,7 +186,8 @@ extern "C" int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* d
   h.in_nbr = in_nbr;
   // state left by the previous call: the control block is rewritten whole,
   // status region 0 and the scan statuses are cleared
-  const Launch run = solo_launch(dctl, &h, n);
+  Launch run = solo_launch(dctl, &h, n);
+  run.opts = sort_opts_for(0, n);
   NA_TRY(cudaMemcpyAsync(dctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
   NA_TRY(cudaMemsetAsync(ws + kOffSt0, 0, 4 * (size_t)tiles * kRadix, s));
   NA_TRY(cudaMemsetAsync(ws + kOffCh0, 0, radix_chunk_bytes(chunks), s));

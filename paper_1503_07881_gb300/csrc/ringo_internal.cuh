@@ -179,6 +179,18 @@ struct SegMap {
   uint32_t nseg;
 };
 
+// Choices of the radix pass that the tuner measures (tune.cu):
+//   rank_method     0: peers by shared-memory lane masks (one atomic OR and
+//                      one read per key), 1: peers by one warp ballot per
+//                      digit bit (no shared memory, 32 ALU operations per
+//                      key; no atomic conflicts when many keys share a digit)
+//   prefetch_waves  how far ahead (in waves of resident blocks) each block
+//                   asks L2 for a tile's input; 0: no prefetch
+struct SweepOpts {
+  int32_t rank_method = 0;
+  int32_t prefetch_waves = 1;
+};
+
 // The segment table and slot maps of one run, and its claim counters.
 struct Launch {
   Ctl* ctls;              // [nseg] device control blocks
@@ -188,6 +200,7 @@ struct Launch {
   uint32_t row_slots;     // rows.start[nseg]
   uint32_t nseg;
   uint32_t* counters;     // [kNumCounters] device, zero at the start of a run
+  SweepOpts opts;         // radix pass variant
 };
 // merge.start and blocks.start are written on the device after phase 1
 // (from Vs and Vd); their kernels are persistent and loop over the slots.
@@ -210,6 +223,24 @@ inline Launch solo_launch(Ctl* dctl, Ctl* h, uint32_t n_rows) {
   L.counters = dctl->solo_counters;
   return L;
 }
+
+// The pass options for a run of `kind` (0: one table, 1: a batch wave) whose
+// segments hold `rows` rows on average: the forced ones if set
+// (ringo_sort_opts_force), else the tuned choice for this GPU and size
+// class, else the defaults.  wave_rows (batches) likewise, 0 when none.
+SweepOpts sort_opts_for(int kind, uint64_t rows);
+int64_t tuned_wave_rows(uint64_t rows_per_pred);
+// Keeps the forced pass options (ringo_sort_opts_force) of its construction
+// and puts them back when it goes out of scope (tuners force candidates).
+struct ForcedOptsGuard {
+  ForcedOptsGuard();
+  ~ForcedOptsGuard();
+  bool was;
+  SweepOpts saved;
+};
+// Records a tuned choice (in memory and, when a cache file is set, on disk).
+void record_tuned(int kind, uint64_t rows, const SweepOpts& o, int64_t wave_rows, double ms,
+                  int out_passes, int in_passes);
 
 // --------------------------------------------------------- host launchers --
 // Each enqueues one kernel on `s`; `counter` is the launch's claim counter.

@@ -293,9 +293,8 @@ __device__ __forceinline__ uint32_t digit_lookback2(const uint32_t* __restrict__
 // low word, taken with one byte permute), and full tiles take a path without
 // bounds checks, so the per-key work is a few shared-memory operations and
 // no branches.
-// A block prefetches into L2 the tile of the slot this far ahead of its
-// own: about the number of blocks resident at once (four per SM).
-constexpr uint32_t kPrefetchAhead = 4 * 152;
+// Blocks of the pass resident at once per SM (the launch bounds' minimum).
+constexpr uint32_t kSweepBlocksPerSm = 4;
 
 // What thread 0 learns about the block's tile, for the whole block.
 struct SweepTile {
@@ -345,7 +344,7 @@ __device__ __forceinline__ uint64_t key_at(const SweepSmem& S, uint32_t j) {
 }
 
 // Steps 1-6 for one tile of `cnt` keys (FULL: cnt == kSortTile).
-template <int BYTE, bool HI, bool PACK, bool FULL>
+template <int BYTE, bool HI, int RANK, bool PACK, bool FULL>
 __device__ __forceinline__ void sweep_body(SweepSmem& S, Ctl* __restrict__ ctl, SortCtl& sc,
                                            uint64_t* __restrict__ out, uint32_t tile,
                                            uint32_t ntiles, uint32_t cnt, uint32_t n, int pass,
@@ -399,23 +398,43 @@ __device__ __forceinline__ void sweep_body(SweepSmem& S, Ctl* __restrict__ ctl, 
     const uint32_t j = wslot + i * 32;
     const bool ok = FULL || j < cnt;
     const uint32_t d = ok ? byte_of<BYTE>(key_word<HI, PACK>(S, j)) : (uint32_t)kRadix;
-    asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(wmask + 4 * d), "r"(bit) : "memory");
-    __syncwarp();
-    uint32_t peers;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(peers) : "r"(wmask + 4 * d) : "memory");
-    __syncwarp();
+    uint32_t peers, old = 0;
+    if constexpr (RANK == 0) {
+      asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(wmask + 4 * d), "r"(bit) : "memory");
+      __syncwarp();
+      asm volatile("ld.shared.u32 %0, [%1];" : "=r"(peers) : "r"(wmask + 4 * d) : "memory");
+      __syncwarp();
+    } else {
+      // one ballot per digit bit (and one for "past the end" in a partial
+      // tile): the lanes that agree on every bit
+      peers = 0xFFFFFFFFu;
+#pragma unroll
+      for (int q = 0; q < (FULL ? kRadixBits : kRadixBits + 1); ++q) {
+        const bool b = (d >> q) & 1u;
+        const uint32_t bb = __ballot_sync(0xFFFFFFFFu, b);
+        peers &= b ? bb : ~bb;
+      }
+    }
     const uint32_t leader = 31u - __clz(peers);
-    uint32_t old = 0;
-    // the group's highest lane clears the mask entry and advances the
+    // the group's highest lane (clears the mask entry and) advances the
     // digit's running place by the group size (predicated, no branch)
     const uint32_t lead = ((uint32_t)lane == leader) & (ok ? 1u : 0u);
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n"
-        " @p st.shared.u32 [%2], 0;\n"
-        " @p atom.shared.add.u32 %0, [%3], %4;\n}\n"
-        : "+r"(old)
-        : "r"(lead), "r"(wmask + 4 * d), "r"(whaddr + 4 * d), "r"((uint32_t)__popc(peers))
-        : "memory");
+    if constexpr (RANK == 0) {
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n"
+          " @p st.shared.u32 [%2], 0;\n"
+          " @p atom.shared.add.u32 %0, [%3], %4;\n}\n"
+          : "+r"(old)
+          : "r"(lead), "r"(wmask + 4 * d), "r"(whaddr + 4 * d), "r"((uint32_t)__popc(peers))
+          : "memory");
+    } else {
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n"
+          " @p atom.shared.add.u32 %0, [%2], %3;\n}\n"
+          : "+r"(old)
+          : "r"(lead), "r"(whaddr + 4 * d), "r"((uint32_t)__popc(peers))
+          : "memory");
+    }
     __syncwarp();
     old = __shfl_sync(0xFFFFFFFFu, old, leader);
     const uint32_t pos = old + (uint32_t)__popc(peers & lt);
@@ -456,10 +475,10 @@ __device__ __forceinline__ void sweep_body(SweepSmem& S, Ctl* __restrict__ ctl, 
   }
 }
 
-template <int BYTE, bool HI>
-__global__ void __launch_bounds__(kSortThreads, 4)
+template <int BYTE, bool HI, int RANK>
+__global__ void __launch_bounds__(kSortThreads, kSweepBlocksPerSm)
     k_onesweep(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter, int which, int pass,
-               int gpass) {
+               int gpass, uint32_t ahead_slots) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   SweepSmem& S = *reinterpret_cast<SweepSmem*>(smem_raw);
   const int tid = threadIdx.x;
@@ -516,10 +535,11 @@ __global__ void __launch_bounds__(kSortThreads, 4)
       }
     }
     S.t = t;
-    // the tile a block will claim about one wave of resident blocks from now
-    // goes to L2 already, so that block's copy does not wait on DRAM
-    const uint32_t ahead = g + kPrefetchAhead;
-    if (ahead < total) {
+    // the tile a block will claim `ahead_slots` claims from now (a whole
+    // number of waves of resident blocks) goes to L2 already, so that
+    // block's copy does not wait on DRAM
+    const uint32_t ahead = g + ahead_slots;
+    if (ahead_slots && ahead < total) {
       const uint32_t ps = m.nseg > 1 ? seg_of(m, ahead) : 0u;
       const uint32_t pt = ahead - (m.nseg > 1 ? __ldg(m.start + ps) : 0u);
       const Ctl* pc = ctls + ps;
@@ -586,20 +606,25 @@ __global__ void __launch_bounds__(kSortThreads, 4)
   SortCtl& sc = which ? ctl->in_sort : ctl->out_sort;
   const bool full = cnt == (uint32_t)kSortTile;
   if (!HI && !t.in) {
-    if (full) sweep_body<BYTE, HI, true, true>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
-    else sweep_body<BYTE, HI, true, false>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
+    if (full) sweep_body<BYTE, HI, RANK, true, true>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
+    else sweep_body<BYTE, HI, RANK, true, false>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
   } else {
-    if (full) sweep_body<BYTE, HI, false, true>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
-    else sweep_body<BYTE, HI, false, false>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
+    if (full) sweep_body<BYTE, HI, RANK, false, true>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
+    else sweep_body<BYTE, HI, RANK, false, false>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
   }
 }
 
-using SweepFn = void (*)(Ctl*, SegMap, uint32_t*, int, int, int);
-// [hi][byte]: the digit of out-sort pass p is byte p % 4 of the low word
-// (p < 4) or of the high word; in-sort pass p is byte p of the high word
-static const SweepFn kSweep[2][4] = {
-    {k_onesweep<0, false>, k_onesweep<1, false>, k_onesweep<2, false>, k_onesweep<3, false>},
-    {k_onesweep<0, true>, k_onesweep<1, true>, k_onesweep<2, true>, k_onesweep<3, true>}};
+using SweepFn = void (*)(Ctl*, SegMap, uint32_t*, int, int, int, uint32_t);
+// [rank method][hi][byte]: the digit of out-sort pass p is byte p % 4 of the
+// low word (p < 4) or of the high word; in-sort pass p is byte p of the high
+// word
+#define RINGO_SWEEPS(R)                                                                      \
+  {{k_onesweep<0, false, R>, k_onesweep<1, false, R>, k_onesweep<2, false, R>,              \
+    k_onesweep<3, false, R>},                                                                \
+   {k_onesweep<0, true, R>, k_onesweep<1, true, R>, k_onesweep<2, true, R>,                 \
+    k_onesweep<3, true, R>}}
+static const SweepFn kSweep[2][2][4] = {RINGO_SWEEPS(0), RINGO_SWEEPS(1)};
+#undef RINGO_SWEEPS
 
 static std::mutex g_sweep_attr_mu;
 static uint64_t g_sweep_attr_devs = 0;  // bit d: set on device d
@@ -611,10 +636,11 @@ void prepare_launches() {
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_sweep_attr_mu);
   if (dev < 64 && !((g_sweep_attr_devs >> dev) & 1)) {
-    for (int h = 0; h < 2; ++h)
-      for (int b = 0; b < 4; ++b)
-        cudaFuncSetAttribute(kSweep[h][b], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(SweepSmem));
+    for (int r = 0; r < 2; ++r)
+      for (int h = 0; h < 2; ++h)
+        for (int b = 0; b < 4; ++b)
+          cudaFuncSetAttribute(kSweep[r][h][b], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sizeof(SweepSmem));
     g_sweep_attr_devs |= 1ull << dev;
   }
 }
@@ -625,9 +651,15 @@ void launch_onesweep(const Launch& L, int which, int pass, int gpass, uint32_t* 
   prepare_launches();
   // shift = (which ? 32 : 0) + 8 * pass; see k_plan
   const int shift = (which ? 32 : 0) + kRadixBits * pass;
-  const SweepFn fn = kSweep[shift >= 32][(shift & 31) >> 3];
+  const int rank = L.opts.rank_method == 1 ? 1 : 0;
+  const SweepFn fn = kSweep[rank][shift >= 32][(shift & 31) >> 3];
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t waves = (uint32_t)max(0, min(2, L.opts.prefetch_waves));
+  const uint32_t ahead = waves * kSweepBlocksPerSm * (uint32_t)sms;
   fn<<<L.row_slots, kSortThreads, sizeof(SweepSmem), s>>>(L.ctls, L.rows, counter, which, pass,
-                                                          gpass);
+                                                          gpass, ahead);
 }
 
 }  // namespace ringo

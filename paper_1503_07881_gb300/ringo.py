@@ -105,6 +105,10 @@ SIGNATURES = {
     "ringo_table_select": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int, ctypes.c_int, _I32, _P, _P]),
     "ringo_table_join": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I64, _P, _P, _I64, _P,
                                         _P]),
+    "ringo_tune_table": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P]),
+    "ringo_tune_lookup": (ctypes.c_int, [_I32, _I64, _P, _P]),
+    "ringo_tune_set_cache": (ctypes.c_int, [ctypes.c_char_p]),
+    "ringo_sort_opts_force": (ctypes.c_int, [_P]),
     "ringo_test_inject_alloc_failure": (ctypes.c_int, [_I32]),
     "ringo_test_inject_lookback_timeout": (ctypes.c_int, [ctypes.c_uint32]),
     "ringo_test_pool_used": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64)]),
@@ -434,6 +438,50 @@ def ringo_profile_stop() -> list[dict]:
     _check(load().ringo_profile_stop(arr, cap, ctypes.byref(n)), "ringo_profile_stop")
     return [{"name": arr[i].name.decode(), "launches": arr[i].launches,
              "total_ms": arr[i].total_ms} for i in range(min(n.value, cap))]
+
+
+class SortOpts(ctypes.Structure):
+    _fields_ = [("rank_method", ctypes.c_int32), ("prefetch_waves", ctypes.c_int32),
+                ("wave_rows", ctypes.c_int64)]
+
+
+def _opts_dict(o: SortOpts) -> dict:
+    return {"rank_method": o.rank_method, "prefetch_waves": o.prefetch_waves,
+            "wave_rows": o.wave_rows}
+
+
+def ringo_tune_table(src: torch.Tensor, dst: torch.Tensor, stream=None) -> tuple[dict, float]:
+    """Times every radix pass variant on this table and records the fastest
+    for its size class; returns (options, ms)."""
+    o, ms = SortOpts(), ctypes.c_double()
+    _check(load().ringo_tune_table(_col_ptr(src, "src"), _col_ptr(dst, "dst"), src.numel(),
+                                   _stream_ptr(stream), ctypes.byref(o), ctypes.byref(ms)),
+           "ringo_tune_table")
+    return _opts_dict(o), ms.value
+
+
+def ringo_tune_lookup(kind: int, rows: int) -> tuple[bool, dict]:
+    """The recorded choice for (this GPU, kind 0 table / 1 batch, class of rows)."""
+    o, found = SortOpts(), ctypes.c_int32()
+    _check(load().ringo_tune_lookup(int(kind), int(rows), ctypes.byref(o), ctypes.byref(found)),
+           "ringo_tune_lookup")
+    return bool(found.value), _opts_dict(o)
+
+
+def ringo_tune_set_cache(path: str | None) -> None:
+    """Keep tuned choices in this JSON file (read now, rewritten on change)."""
+    _check(load().ringo_tune_set_cache(path.encode() if path else None), "ringo_tune_set_cache")
+
+
+def ringo_sort_opts_force(opts: dict | None) -> None:
+    """Force radix pass options for every conversion (None: back to the
+    recorded choices)."""
+    if opts is None:
+        _check(load().ringo_sort_opts_force(None), "ringo_sort_opts_force")
+        return
+    o = SortOpts(int(opts.get("rank_method", 0)), int(opts.get("prefetch_waves", 1)),
+                 int(opts.get("wave_rows", 0)))
+    _check(load().ringo_sort_opts_force(ctypes.byref(o)), "ringo_sort_opts_force")
 
 
 def ringo_test_inject_alloc_failure(skip: int) -> None:

@@ -74,3 +74,25 @@ def test_failure_injection_hooks_argument_handling():
     # arming and disarming the allocation failure touches no device
     assert lib.ringo_test_inject_alloc_failure(3) == ringo.RINGO_OK
     assert lib.ringo_test_inject_alloc_failure(-1) == ringo.RINGO_OK
+
+
+def test_sort_opts_force_argument_checks():
+    """Forcing pass options checks their ranges before anything else; a
+    valid force and its release touch no device."""
+    lib = ringo.load()
+    for bad in ((2, 1, 0), (-1, 1, 0), (0, 3, 0), (0, -1, 0), (0, 1, -5)):
+        o = ringo.SortOpts(*bad)
+        assert lib.ringo_sort_opts_force(ctypes.byref(o)) == ringo.RINGO_EINVAL, bad
+    o = ringo.SortOpts(1, 2, 0)
+    assert lib.ringo_sort_opts_force(ctypes.byref(o)) == ringo.RINGO_OK
+    assert lib.ringo_sort_opts_force(None) == ringo.RINGO_OK
+    assert lib.ringo_tune_lookup(3, 10, ctypes.byref(o), None) == ringo.RINGO_EINVAL
+    assert lib.ringo_tune_table(None, None, 10, None, ctypes.byref(o), None) == ringo.RINGO_EINVAL
+
+
+def test_tune_cache_rejects_a_file_that_is_not_a_cache(tmp_path):
+    lib = ringo.load()
+    bad = tmp_path / "not_a_cache.json"
+    bad.write_text('{"something": 1}')
+    assert lib.ringo_tune_set_cache(str(bad).encode()) == ringo.RINGO_EINVAL
+    assert lib.ringo_tune_set_cache(None) == ringo.RINGO_OK
