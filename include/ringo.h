@@ -452,6 +452,10 @@ typedef struct {
   int32_t max_batch;       /* requests per batch; 0: 1024 */
   int64_t max_batch_rows;  /* selected rows per batch (a larger single request
                               runs alone); 0: 2^28 */
+  int64_t small_rows;      /* requests of at most this many selected rows may
+                              also be served by one more worker whose stream
+                              has the device's highest priority, so they do
+                              not wait out a large wave; 0: 2^21, < 0: none */
 } ringo_server_config;
 
 /* submit flag: keep the converted graph with the result (its bytes stay
@@ -491,8 +495,8 @@ RINGO_API int64_t ringo_clock_ns(void);
  * (defaults).  The budget is taken into the library's device memory pool
  * once here (when the device has that much free), so requests do not wait
  * on device memory being mapped; the pool keeps it for later calls.
- * Errors: EINVAL (NULL b or out, budget <= 0, negative config field),
- * ERANGE (more than 16 workers).
+ * Errors: EINVAL (NULL b or out, budget <= 0, negative workers, max_batch
+ * or max_batch_rows), ERANGE (more than 16 workers).
  */
 RINGO_API int ringo_server_create(const ringo_base* b, int64_t hbm_budget_bytes,
                                   const ringo_server_config* cfg, ringo_server** out);

@@ -9,7 +9,11 @@
 // device bytes of everything in flight stay within the budget, and the
 // admitted requests run as one captured wave of the multi-segment pipeline.
 // While one worker's wave runs on the device, the next worker already counts,
-// admits and launches the requests that arrived meanwhile.
+// admits and launches the requests that arrived meanwhile.  One more worker
+// (the small lane) serves only requests of at most cfg.small_rows rows, on a
+// stream of the device's highest priority: a small request that arrives
+// while a large wave runs starts at once, its kernels' blocks taking SMs as
+// the large wave's blocks finish, instead of waiting for the whole wave.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -252,19 +256,41 @@ bool has_uncounted(ringo_server* S) {
   return false;
 }
 
-void worker_main(ringo_server* S) {
+bool is_small(const ringo_server* S, const Req* r) {
+  return r->rows >= 0 && r->rows <= S->cfg.small_rows;
+}
+
+// A counted small request that fits in the budget now (the small lane's
+// admission; it skips requests of any other size).
+bool small_admissible(ringo_server* S) {
+  for (Req* r : S->pending)
+    if (is_small(S, r) && S->core->inflight + request_bytes(r) <= S->budget_bytes) return true;
+  return false;
+}
+
+// lane 0: the regular workers; lane 1: the small lane (see the top).
+void worker_main(ringo_server* S, int lane) {
   cudaSetDevice(S->device);
   cudaStream_t st = nullptr;
-  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (lane == 1) {
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, greatest);
+  } else {
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  }
   Core& C = *S->core;
   std::unique_lock<std::mutex> lk(C.mu);
   while (true) {
     C.cv_sched.wait(lk, [&] {
       if (S->stop && S->pending.empty()) return true;
-      if (has_uncounted(S) || front_admissible(S)) return true;
+      if (has_uncounted(S)) return true;
+      if (lane == 1) return small_admissible(S) || S->stop;
+      if (front_admissible(S)) return true;
       return S->stop && S->active == 0 && S->pending.front()->rows >= 0;
     });
     if (S->stop && S->pending.empty()) break;
+    if (lane == 1 && S->stop && !has_uncounted(S) && !small_admissible(S)) break;
     // 1. count what has arrived
     std::vector<Req*> tocount;
     for (Req* r : S->pending)
@@ -291,7 +317,26 @@ void worker_main(ringo_server* S) {
     // 2. admit in arrival order within the budget
     std::vector<Req*> batch;
     int64_t rows = 0, bytes = 0;
-    {
+    if (lane == 1) {
+      for (auto it = S->pending.begin(); it != S->pending.end();) {
+        Req* r = *it;
+        if (!is_small(S, r)) {
+          ++it;
+          continue;
+        }
+        const int64_t b = request_bytes(r);
+        if ((int64_t)batch.size() >= S->cfg.max_batch || rows + r->rows > S->cfg.max_batch_rows ||
+            C.inflight + bytes + b > S->budget_bytes)
+          break;
+        r->est = b;
+        r->result->info.t_admit_ns = now_ns();
+        batch.push_back(r);
+        rows += r->rows;
+        bytes += b;
+        it = S->pending.erase(it);
+      }
+      if (!batch.empty()) C.add(bytes);
+    } else {
       while (!S->pending.empty()) {
         Req* r = S->pending.front();
         if (r->rows < 0) break;
@@ -324,8 +369,8 @@ void worker_main(ringo_server* S) {
     if (batch.empty()) {
       // stopping, nothing in flight, and the head still does not fit: only
       // kept graphs the caller holds can be in the way, so give up on it
-      if (S->stop && S->active == 0 && !S->pending.empty() && S->pending.front()->rows >= 0 &&
-          !front_admissible(S)) {
+      if (lane == 0 && S->stop && S->active == 0 && !S->pending.empty() &&
+          S->pending.front()->rows >= 0 && !front_admissible(S)) {
         finish(S, S->pending.front(), RINGO_EBUSY);
         S->pending.pop_front();
         C.cv_done.notify_all();
@@ -375,6 +420,7 @@ int ringo_server_create(const ringo_base* b, int64_t hbm_budget_bytes,
   if (c.workers == 0) c.workers = 1;
   if (c.max_batch == 0) c.max_batch = 1024;
   if (c.max_batch_rows == 0) c.max_batch_rows = 256ll << 20;
+  if (c.small_rows == 0) c.small_rows = 1ll << 21;
   if (c.workers > 16) return RINGO_ERANGE;
   ringo_server* S = new ringo_server();
   S->base = b;
@@ -392,7 +438,8 @@ int ringo_server_create(const ringo_base* b, int64_t hbm_budget_bytes,
     }
     cudaGetLastError();
   }
-  for (int i = 0; i < c.workers; ++i) S->workers.emplace_back(worker_main, S);
+  for (int i = 0; i < c.workers; ++i) S->workers.emplace_back(worker_main, S, 0);
+  if (c.small_rows > 0) S->workers.emplace_back(worker_main, S, 1);
   *out = S;
   return RINGO_OK;
 }

@@ -693,7 +693,7 @@ RINGO_SERVE_KEEP_GRAPH = 1
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("max_batch_rows", ctypes.c_int64)]
+                ("max_batch_rows", ctypes.c_int64), ("small_rows", ctypes.c_int64)]
 
 
 class ResultInfo(ctypes.Structure):
@@ -720,8 +720,8 @@ class Server:
     """Request server over a resident BaseTable (select + convert + top-k)."""
 
     def __init__(self, base: BaseTable, budget_bytes: int, workers: int = 0, max_batch: int = 0,
-                 max_batch_rows: int = 0):
-        cfg = ServerConfig(workers, max_batch, max_batch_rows)
+                 max_batch_rows: int = 0, small_rows: int = 0):
+        cfg = ServerConfig(workers, max_batch, max_batch_rows, small_rows)
         h = ctypes.c_void_p()
         _check(load().ringo_server_create(base._h, int(budget_bytes), ctypes.byref(cfg),
                                           ctypes.byref(h)), "ringo_server_create")

@@ -204,3 +204,28 @@ def test_argument_errors(base_cols):
     with pytest.raises(ringo.RingoError) as e:
         ringo.Server(base, 0)
     assert e.value.status == ringo.RINGO_EINVAL
+
+
+@pytest.mark.parametrize("small_rows", [-1, 20_000])
+def test_small_lane_results_equal_alone(base_cols, small_rows):
+    """With the small lane (requests of at most small_rows rows may also go
+    to a worker on a high-priority stream) and without it, every result of a
+    mix of small and large requests equals the oracle's and the same request
+    served alone."""
+    base, cols = base_cols
+    preds = tg.make_predicates(SPEC, 30, 500, 400_000, seed=21)
+    srv = ringo.Server(base, 40 << 30, workers=1, small_rows=small_rows)
+    try:
+        tickets = [srv.submit(p, topk=50) for p in preds]
+        mixed = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    finally:
+        srv.close()
+    assert st["completed"] == len(preds) and st["failed"] == 0
+    alone = ringo.Server(base, 40 << 30, workers=1, small_rows=-1)
+    try:
+        for p, m in zip(preds, mixed):
+            check_result(m, cols, p, 50)
+            same_result(m, alone.wait(alone.submit(p, topk=50)))
+    finally:
+        alone.close()
