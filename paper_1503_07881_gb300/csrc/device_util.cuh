@@ -178,7 +178,19 @@ struct ScanChunks {
   uint64_t* inc;   // [chunks] kScanInc | inclusive prefix once known
   uint32_t* cnt;   // [chunks] tiles that have added their value
   uint32_t limit;  // bound of the waits (0: kSpinLimit)
+  // 1: every chunk's two sums stay below 2^24 (a chunk covers at most 2^17
+  // items), so agg holds (tiles added << 48) | (A << 24) | B in one word: a
+  // single relaxed load says whether the chunk is complete, no counter or
+  // fence is needed.  0: agg holds the packed sums and cnt counts the tiles.
+  uint32_t small;
 };
+
+__device__ __forceinline__ uint64_t chunk_word(uint64_t agg) {
+  return (1ull << 48) | ((uint64_t)unpackA(agg) << 24) | (uint64_t)unpackB(agg);
+}
+__device__ __forceinline__ uint64_t chunk_sums(uint64_t w) {
+  return pack2((uint32_t)(w >> 24) & 0xFFFFFFu, (uint32_t)w & 0xFFFFFFu);
+}
 
 // Two-level tile prefix for the compaction kernels: like warp_lookback, but a
 // tile walks back only within its kChunkTiles-tile chunk and then over chunk
@@ -193,9 +205,13 @@ __device__ __forceinline__ uint64_t warp_lookback2(uint64_t* status, ScanChunks 
   // publish this tile's value, and add it to the chunk aggregate
   if (lane == 0) {
     st_relaxed_u64(status + tile, (tile == 0 ? kScanInc : kScanAgg) | agg);
-    if (agg) atomicAdd((unsigned long long*)(ch.agg + c), (unsigned long long)agg);
-    __threadfence();
-    atomicAdd(ch.cnt + c, 1u);
+    if (ch.small) {
+      atomicAdd((unsigned long long*)(ch.agg + c), (unsigned long long)chunk_word(agg));
+    } else {
+      if (agg) atomicAdd((unsigned long long*)(ch.agg + c), (unsigned long long)agg);
+      __threadfence();
+      atomicAdd(ch.cnt + c, 1u);
+    }
   }
   uint64_t excl = 0;
   if (tile == 0) return 0;
@@ -229,12 +245,17 @@ __device__ __forceinline__ uint64_t warp_lookback2(uint64_t* status, ScanChunks 
   int64_t cc = (int64_t)c - 1;
   while (cc >= 0) {
     const int64_t k = cc - lane;
-    uint64_t inc = 0;
+    uint64_t inc = 0, word = 0;
     uint32_t done = 0;
     if (k >= 0) {
       inc = ld_relaxed_u64(ch.inc + k);
       const uint32_t need = min((uint32_t)kChunkTiles, ntiles - ((uint32_t)k << kChunkShift));
-      done = ld_acquire_u32(ch.cnt + k) >= need ? 1u : 0u;
+      if (ch.small) {
+        word = ld_relaxed_u64(ch.agg + k);
+        done = (uint32_t)(word >> 48) >= need ? 1u : 0u;
+      } else {
+        done = ld_acquire_u32(ch.cnt + k) >= need ? 1u : 0u;
+      }
     }
     const uint32_t incm = __ballot_sync(0xFFFFFFFFu, k >= 0 && (inc >> 62) == 2);
     const int stop = incm ? __ffs(incm) - 1 : 32;
@@ -247,7 +268,7 @@ __device__ __forceinline__ uint64_t warp_lookback2(uint64_t* status, ScanChunks 
       continue;
     }
     uint64_t v = 0;
-    if (k >= 0 && lane < stop) v = ld_relaxed_u64(ch.agg + k);
+    if (k >= 0 && lane < stop) v = ch.small ? chunk_sums(word) : ld_relaxed_u64(ch.agg + k);
     if (lane == stop) v = inc & kScanValMask;
     excl += warp_sum(v);
     if (incm) return excl;
@@ -308,8 +329,9 @@ __device__ __forceinline__ Claim claim_next(SegMap m, uint32_t* counter) {
     c.valid = 0;
     return c;
   }
-  c.seg = seg_of(m, g);
-  c.tile = g - __ldg(m.start + c.seg);
+  // one segment (a single table): its slots start at 0, nothing to search
+  c.seg = m.nseg > 1 ? seg_of(m, g) : 0u;
+  c.tile = m.nseg > 1 ? g - __ldg(m.start + c.seg) : g;
   c.valid = 1;
   return c;
 }
@@ -320,9 +342,10 @@ __device__ __forceinline__ void claim_slot(SegMap m, uint32_t* counter, Claim* o
     out->valid = 0;
     return;
   }
-  const uint32_t sidx = seg_of(m, g);
+  // one segment (a single table): its slots start at 0, nothing to search
+  const uint32_t sidx = m.nseg > 1 ? seg_of(m, g) : 0u;
   out->seg = sidx;
-  out->tile = g - __ldg(m.start + sidx);
+  out->tile = m.nseg > 1 ? g - __ldg(m.start + sidx) : g;
   out->valid = 1;
 }
 

@@ -21,8 +21,10 @@ constexpr int kWarps = kScanThreads / 32;
 
 __device__ __forceinline__ int32_t unbias(uint32_t b) { return (int32_t)(b ^ kBias); }
 __device__ __forceinline__ ScanChunks chunks_of(const Ctl* ctl, int i) {
+  // a chunk of these scans covers at most 32 tiles of 4096 items
+  static_assert(kChunkTiles * kScanTile <= (1 << 17), "chunk sums fit 24 bits");
   return ScanChunks{ctl->scan_chunk_agg[i], ctl->scan_chunk_inc[i], ctl->scan_chunk_cnt[i],
-                    ctl->spin_limit};
+                    ctl->spin_limit, 1u};
 }
 }  // namespace
 

@@ -260,8 +260,10 @@ bool is_small(const ringo_server* S, const Req* r) {
   return r->rows >= 0 && r->rows <= S->cfg.small_rows;
 }
 
-// A counted small request that fits in the budget now (the small lane's
-// admission; it skips requests of any other size).
+// A counted small request that fits in the budget now.  The small lane's
+// admission below admits the first such request whenever this is true (it
+// skips, never stops at, small requests that do not fit), so a woken small
+// lane always makes progress or sleeps again.
 bool small_admissible(ringo_server* S) {
   for (Req* r : S->pending)
     if (is_small(S, r) && S->core->inflight + request_bytes(r) <= S->budget_bytes) return true;
@@ -325,9 +327,12 @@ void worker_main(ringo_server* S, int lane) {
           continue;
         }
         const int64_t b = request_bytes(r);
-        if ((int64_t)batch.size() >= S->cfg.max_batch || rows + r->rows > S->cfg.max_batch_rows ||
-            C.inflight + bytes + b > S->budget_bytes)
-          break;
+        if ((int64_t)batch.size() >= S->cfg.max_batch) break;
+        if ((!batch.empty() && rows + r->rows > S->cfg.max_batch_rows) ||
+            C.inflight + bytes + b > S->budget_bytes) {
+          ++it;  // a later small request may still fit
+          continue;
+        }
         r->est = b;
         r->result->info.t_admit_ns = now_ns();
         batch.push_back(r);

@@ -229,3 +229,30 @@ def test_small_lane_results_equal_alone(base_cols, small_rows):
             same_result(m, alone.wait(alone.submit(p, topk=50)))
     finally:
         alone.close()
+
+
+def test_small_lane_with_a_tight_budget_and_mixed_sizes(base_cols):
+    """Small requests of different sizes under a budget that holds only one
+    or two of them, with a request larger than the whole budget in the
+    middle: the small lane skips the ones that do not fit and admits later
+    ones that do; everything finishes, the large one with ENOMEM."""
+    base, cols = base_cols
+    preds = tg.make_predicates(SPEC, 24, 20_000, 200_000, seed=31)
+    counts = base.select_count(preds)
+    budget = int(1.5 * 120 * int(counts.max())) + (8 << 20)
+    huge = ([int(t) for t in range(SPEC.tags)], 0, 1 << 40)
+    for rep in range(3):
+        srv = ringo.Server(base, budget, workers=2)
+        try:
+            tickets = [srv.submit(p, topk=5) for p in preds[:12]]
+            big = srv.submit(huge, topk=5)
+            tickets += [srv.submit(p, topk=5) for p in preds[12:]]
+            res = [srv.wait(t, timeout_us=120_000_000) for t in tickets]
+            rb = srv.wait(big, timeout_us=120_000_000)
+            st = srv.stats()
+        finally:
+            srv.close()
+        for p, r in zip(preds, res):
+            check_result(r, cols, p, 5)
+        assert rb["status"] == ringo.RINGO_ENOMEM
+        assert st["max_inflight_bytes"] <= budget and st["inflight_bytes"] == 0
