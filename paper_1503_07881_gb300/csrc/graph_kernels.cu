@@ -170,14 +170,27 @@ void launch_dedup(const Launch& L, uint32_t* counter, cudaStream_t s) {
 // trivial) and writes rank_step.out.  Single-pass compaction count with
 // decoupled look-back.
 __global__ void __launch_bounds__(kScanThreads, 6)
-    k_dst_rank(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
+    k_dst_rank(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter, uint32_t ahead_slots) {
   __shared__ uint64_t s_keys[kScanTile];  // the tile, read once, coalesced
   __shared__ uint64_t s_before;           // the key just before the tile
   __shared__ uint32_t s_w[kWarps];
   __shared__ uint64_t s_prefix;
   __shared__ Claim s_cl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) claim_slot(m, counter, &s_cl);
+  if (tid == 0) {
+    claim_slot(m, counter, &s_cl);
+    // a single table: the tile one wave of resident blocks ahead goes to L2
+    // already, so that block's loads do not wait on DRAM
+    const uint32_t ahead = s_cl.slot + ahead_slots;
+    if (m.nseg == 1 && ahead < __ldg(m.start + 1)) {
+      const uint32_t n0 = ctls->n_rows, b0 = ahead * (uint32_t)kScanTile;
+      const uint64_t* in0 = ctls->rank_step.in;
+      if (in0 && b0 < n0) {
+        const uint32_t k = min((uint32_t)kScanTile, n0 - b0) & ~1u;
+        if (k) bulk_prefetch_l2(in0 + b0, k * 8u);
+      }
+    }
+  }
   __syncthreads();
   if (!s_cl.valid) return;
   Ctl* __restrict__ ctl = ctls + s_cl.seg;
@@ -252,7 +265,12 @@ __global__ void __launch_bounds__(kScanThreads, 6)
 }
 
 void launch_dst_rank(const Launch& L, uint32_t* counter, cudaStream_t s) {
-  if (L.row_slots) k_dst_rank<<<L.row_slots, kScanThreads, 0, s>>>(L.ctls, L.rows, counter);
+  if (!L.row_slots) return;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t ahead = 6u * (uint32_t)sms;  // six blocks resident per SM
+  k_dst_rank<<<L.row_slots, kScanThreads, 0, s>>>(L.ctls, L.rows, counter, ahead);
 }
 
 // ------------------------------------------------------------------ K5 ----
@@ -564,6 +582,14 @@ void launch_merge(const Launch& L, uint32_t* counter, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------- block tables --
+__device__ __forceinline__ void add_step(Ctl* ctl, uint32_t j, uint32_t off) {
+  const uint32_t i = atomicAdd(&ctl->n_steps, 1u);
+  if (i < (uint32_t)kMaxSteps) {
+    ctl->step_j[i] = j;
+    ctl->step_off[i] = off;
+  }
+}
+
 // blk[k] = map[32k], with kBlkDense set when the 32 entries from 32k are
 // consecutive node indices (no node of the other kind lies between them);
 // then map[j] = (blk[j >> 5] & ~kBlkDense) + (j & 31) without reading map.
@@ -588,11 +614,59 @@ __global__ void __launch_bounds__(256)
     if (k < nd) {
       const uint32_t a = k << kBlkShift, e = min(a + 32, Vd) - 1;
       const int32_t r0 = ctl->dst_rank[a], r1 = ctl->dst_rank[e];
-      ctl->dst_blk[k] = (uint32_t)r0 | ((uint32_t)(r1 - r0) == e - a ? kBlkDense : 0u);
+      const bool dense = (uint32_t)(r1 - r0) == e - a;
+      ctl->dst_blk[k] = (uint32_t)r0 | (dense ? kBlkDense : 0u);
+      // steps of dst_rank[j] - j: at the block's start, and inside a block
+      // that is not dense (looked at only while the list can still be used)
+      const uint32_t off0 = (uint32_t)r0 - a;
+      const uint32_t prev = a ? (uint32_t)ctl->dst_rank[a - 1] - (a - 1) : 0u;
+      if (off0 != prev) add_step(ctl, a, off0);
+      if (!dense && *(volatile uint32_t*)&ctl->n_steps <= (uint32_t)kMaxSteps) {
+        uint32_t last = off0;
+        for (uint32_t j = a + 1; j <= e; ++j) {
+          const uint32_t off = (uint32_t)ctl->dst_rank[j] - j;
+          if (off != last) add_step(ctl, j, off);
+          last = off;
+        }
+      }
     }
   }
   __syncthreads();
   }
+}
+
+// Sorts each table's step list by position (one block per table; the list
+// holds at most kMaxSteps entries, so a bitonic sort in shared memory).
+__global__ void __launch_bounds__(kMaxSteps) k_sort_steps(Ctl* __restrict__ ctls) {
+  __shared__ uint64_t s[kMaxSteps];
+  Ctl* __restrict__ ctl = ctls + blockIdx.x;
+  const uint32_t n = ctl->n_steps;
+  if (n < 2 || n > (uint32_t)kMaxSteps) return;
+  const uint32_t t = threadIdx.x;
+  s[t] = t < n ? ((uint64_t)ctl->step_j[t] << 32 | ctl->step_off[t]) : ~0ull;
+  __syncthreads();
+  for (uint32_t size = 2; size <= (uint32_t)kMaxSteps; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      const uint32_t o = t ^ stride;
+      if (o > t) {
+        const bool up = (t & size) == 0;
+        const uint64_t x = s[t], y = s[o];
+        if (up ? x > y : x < y) {
+          s[t] = y;
+          s[o] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (t < n) {
+    ctl->step_j[t] = (uint32_t)(s[t] >> 32);
+    ctl->step_off[t] = (uint32_t)s[t];
+  }
+}
+
+void launch_sort_steps(const Launch& L, cudaStream_t s) {
+  if (L.nseg) k_sort_steps<<<L.nseg, kMaxSteps, 0, s>>>(L.ctls);
 }
 
 void launch_rank_blocks(const Launch& L, uint32_t* counter, cudaStream_t s) {
@@ -673,7 +747,62 @@ __global__ void __launch_bounds__(256)
   if (base >= E) return;
   const uint32_t end = min(E, base + (uint32_t)kScanTile);
   uint32_t* err = &ctl->err;
-  if (Vd != V) remap_range(ctl->out_nbr, base, end, ctl->dst_blk, ctl->dst_rank, Vd, err);
+  if (Vd == V) return;
+  const uint32_t ns = ctl->n_steps;
+  if (ns > (uint32_t)kMaxSteps || blockDim.x != 256) {
+    remap_range(ctl->out_nbr, base, end, ctl->dst_blk, ctl->dst_rank, Vd, err);
+    return;
+  }
+  // few steps: node = j + the difference of the last step at or before j,
+  // found by a binary search of the sorted list in shared memory
+  __shared__ uint32_t s_j[kMaxSteps], s_off[kMaxSteps];
+  for (uint32_t t = threadIdx.x; t < ns; t += blockDim.x) {
+    s_j[t] = ctl->step_j[t];
+    s_off[t] = ctl->step_off[t];
+  }
+  __syncthreads();
+  int32_t* __restrict__ a = ctl->out_nbr;
+  auto node_of = [&](uint32_t j) -> uint32_t {
+    uint32_t lo = 0, hi = ns;  // steps [0, lo) are at or before j
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (s_j[mid] <= j) lo = mid + 1;
+      else hi = mid;
+    }
+    return j + (lo ? s_off[lo - 1] : 0u);
+  };
+  if (end - base == (uint32_t)kScanTile) {
+    constexpr int kVec = kScanTile / (4 * 256);
+    int4 x[kVec];
+#pragma unroll
+    for (int k = 0; k < kVec; ++k)
+      x[k] = __ldcs(reinterpret_cast<const int4*>(a + base + k * 1024) + threadIdx.x);
+#pragma unroll
+    for (int k = 0; k < kVec; ++k) {
+      uint32_t v[4] = {(uint32_t)x[k].x, (uint32_t)x[k].y, (uint32_t)x[k].z, (uint32_t)x[k].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (v[q] >= Vd) {  // never for a correct run index: recorded, not mapped
+          atomicOr(err, kErrRemap);
+          v[q] = 0;
+        } else {
+          v[q] = node_of(v[q]);
+        }
+      }
+      __stcs(reinterpret_cast<int4*>(a + base + k * 1024) + threadIdx.x,
+             make_int4((int)v[0], (int)v[1], (int)v[2], (int)v[3]));
+    }
+    return;
+  }
+  for (uint32_t e = base + threadIdx.x; e < end; e += blockDim.x) {
+    const uint32_t j = (uint32_t)a[e];
+    if (j >= Vd) {
+      atomicOr(err, kErrRemap);
+      a[e] = 0;
+    } else {
+      a[e] = (int32_t)node_of(j);
+    }
+  }
 }
 
 void launch_fill_in_off(const Launch& L, uint32_t* counter, cudaStream_t s) {

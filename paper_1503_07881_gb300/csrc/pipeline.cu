@@ -63,6 +63,7 @@ int enqueue_phase2(const Launch& L, cudaStream_t s) {
   RINGO_ENQUEUE("merge_split", launch_merge_split(L, s));
   RINGO_ENQUEUE("merge", launch_merge(L, c + 0, s));
   RINGO_ENQUEUE("rank_blocks", launch_rank_blocks(L, c + 1, s));
+  RINGO_ENQUEUE("sort_steps", launch_sort_steps(L, s));
   RINGO_ENQUEUE("remap", launch_remap(L, c + 2, s));
   return RINGO_OK;
 }

@@ -41,6 +41,7 @@ constexpr int kMergeItems = 8;
 constexpr int kMergeTile = kScanThreads * kMergeItems;  // 2048 merged items
 
 constexpr uint32_t kBias = 0x80000000u;  // int32 -> uint32 preserving order
+constexpr int kMaxSteps = 256;           // see Ctl::step_j
 
 // Ctl::err bits
 constexpr uint32_t kErrLookback = 1u;   // a radix look-back wait gave up
@@ -130,6 +131,14 @@ struct alignas(16) Ctl {
   int32_t* dst_rank;          // [Vd]
   uint32_t* src_blk;          // [ceil(Vs / 32)]
   uint32_t* dst_blk;          // [ceil(Vd / 32)]
+  // The dst-run -> node map as steps: dst_rank[j] - j only grows, by one
+  // for every node that is not a destination; where it changes, j and the
+  // new difference.  Filled (unordered) by k_rank_blocks while there are at
+  // most kMaxSteps, then sorted by k_sort_steps; n_steps counts them all, so
+  // a larger count means the list is not used.
+  uint32_t n_steps;
+  uint32_t step_j[kMaxSteps];
+  uint32_t step_off[kMaxSteps];
   // outputs
   int32_t* out_nbr;           // [n_rows] capacity
   int32_t* in_nbr;            // [n_rows] capacity
@@ -270,6 +279,7 @@ void launch_merge(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_rank_blocks(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_remap(const Launch& L, uint32_t* counter, cudaStream_t s);
 void launch_fill_in_off(const Launch& L, uint32_t* counter, cudaStream_t s);
+void launch_sort_steps(const Launch& L, cudaStream_t s);
 void launch_degrees(const int32_t* node_ids, const int64_t* off, uint32_t V,
                     const int32_t* ids, uint32_t n, int64_t* deg, cudaStream_t s);
 int launch_topk(const int32_t* node_ids, const int64_t* off, uint32_t V, uint32_t k,

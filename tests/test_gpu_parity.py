@@ -205,3 +205,26 @@ def test_lj_full_size_sampled():
 def test_twitter_full_size_sampled():
     e, v = _full_size("twitter", 1, 100)
     assert 1.4e9 < e < 1.47e9 and 3.5e7 < v <= 4.17e7
+
+
+@pytest.mark.parametrize("src_only", [0, 1, 255, 256, 257, 2000])
+def test_out_remap_step_list_threshold(src_only):
+    """The out-direction remap uses a short list of the map's steps when at
+    most 256 nodes are not destinations, else block tables: both paths, and
+    the boundary, against the oracle."""
+    rng = np.random.default_rng(100 + src_only)
+    dst_ids = np.arange(0, 3 * 60_000, 3, dtype=np.int64)          # 60K destinations
+    extra = rng.choice(np.arange(1, 3 * 60_000, 3), src_only, replace=False)  # between them
+    n = 250_000
+    src = rng.choice(np.concatenate([dst_ids, extra]), n)
+    dst = rng.choice(dst_ids, n)
+    # every destination and every extra source occurs
+    src[:src_only] = extra
+    dst[:dst_ids.size] = dst_ids
+    s, d = src.astype(np.int32), dst.astype(np.int32)
+    want = oracle.table_to_graph(s, d)
+    g = ringo.ringo_table_to_graph(torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda())
+    inf = g.info()
+    assert inf["num_nodes"] - inf["num_dst_nodes"] == src_only
+    pins.assert_same_graph(g.copy_to_host(), want, f"{src_only} source-only nodes")
+    g.free()
