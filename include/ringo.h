@@ -562,12 +562,21 @@ RINGO_API int ringo_profile_stop(ringo_kernel_stat* out, int32_t cap, int32_t* n
  *   rank_method     0: a warp's lanes with the same digit find each other
  *                      through shared-memory lane masks (default);
  *                   1: through one warp ballot per digit bit (no shared
- *                      atomics: better when many keys share a digit)
+ *                      atomics: better when many keys share a digit);
+ *                   2: through one warp match instruction on the digit
  *   prefetch_waves  0..2: how far ahead, in waves of resident blocks, a
  *                   pass asks L2 for the input of a tile (default 1)
  *   wave_rows       batches only: rows per captured launch (0: automatic)
- * ringo_tune_table -- times every pass variant on this table (device
- *   columns; three conversions each, the first a warm-up) and records the
+ *   in_digit_bits   8 or 9: digit width of the in-direction sort passes
+ *                   (0 means 8, the default).  With 9-bit digits a table
+ *                   with at most 2^27 distinct destinations needs three
+ *                   in-direction passes instead of four, each with twice
+ *                   the digits.
+ *   reserved        0
+ * ringo_tune_table -- times the pass variants on this table (device
+ *   columns; three conversions each, the first a warm-up: every rank method
+ *   and prefetch distance with 8-bit in-direction digits, then every rank
+ *   method with 9-bit digits at the best prefetch distance) and records the
  *   fastest for its class; later conversions of that class use it.
  *   *best (and *best_ms, if not NULL) receive the choice.  EINVAL for a NULL
  *   pointer or nrows <= 0; otherwise the errors of ringo_table_to_graph.
@@ -585,6 +594,8 @@ typedef struct {
   int32_t rank_method;
   int32_t prefetch_waves;
   int64_t wave_rows;
+  int32_t in_digit_bits;
+  int32_t reserved;
 } ringo_sort_opts;
 
 RINGO_API int ringo_tune_table(const int32_t* src, const int32_t* dst, int64_t nrows,

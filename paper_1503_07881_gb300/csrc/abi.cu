@@ -89,8 +89,8 @@ WsLayout layout_for(uint32_t n) {
   L.ctl = o; o = align_up(o + sizeof(Ctl));
   L.keysA = o; o = align_up(o + sizeof(uint64_t) * ((size_t)n + 1));
   L.keysB = o; o = align_up(o + sizeof(uint64_t) * ((size_t)n + 1));
-  L.st0 = o; o = align_up(o + sizeof(uint32_t) * tiles * kRadix);
-  L.st1 = o; o = align_up(o + sizeof(uint32_t) * tiles * kRadix);
+  L.st0 = o; o = align_up(o + radix_status_bytes(tiles));
+  L.st1 = o; o = align_up(o + radix_status_bytes(tiles));
   L.chunks = (tiles + kChunkTiles - 1) / kChunkTiles;
   L.chunk_bytes = align_up(radix_chunk_bytes(L.chunks));
   L.ch0 = o; o = align_up(o + L.chunk_bytes);

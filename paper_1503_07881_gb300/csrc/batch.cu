@@ -64,7 +64,7 @@ __host__ __device__ inline SegLayout seg_layout(uint32_t n) {
   L.mtiles = (uint32_t)mtiles;
   L.chunks = (uint32_t)ch;
   uint64_t o = 0;
-  L.z_st0 = o; o = al(o + 4 * tiles * kRadix);
+  L.z_st0 = o; o = al(o + radix_status_bytes(tiles));
   L.z_ch0 = o; o = al(o + chunk_bytes);
   L.z_sc0 = o; o = al(o + scan_region(tiles));
   L.z_sc1 = o; o = al(o + scan_region(tiles));
@@ -73,7 +73,7 @@ __host__ __device__ inline SegLayout seg_layout(uint32_t n) {
   o = 0;
   L.keysA = o; o = al(o + 8 * (n + 1ull));
   L.keysB = o; o = al(o + 8 * (n + 1ull));
-  L.st1 = o; o = al(o + 4 * tiles * kRadix);
+  L.st1 = o; o = al(o + radix_status_bytes(tiles));
   L.ch1 = o; o = al(o + chunk_bytes);
   L.usrc = o; o = al(o + 4 * (n + 1ull));
   L.usrc_start = o; o = al(o + 4 * (n + 1ull));
@@ -1118,24 +1118,23 @@ int ringo_batch_autotune(const ringo_base* b, const ringo_select* preds, int32_t
   SweepOpts best_o = sort_opts_for(1, npred > 0 ? total / (uint64_t)npred : 0);
   {
     const ForcedOptsGuard keep;  // candidates are forced one after another
-    for (int r = 0; r <= 1; ++r) {
-      for (int pw = 0; pw <= 2; ++pw) {
-        const ringo_sort_opts o{r, pw, 0};
-        ringo_sort_opts_force(&o);
-        const auto t0 = std::chrono::steady_clock::now();
-        ringo_batch* bt = nullptr;
-        const int rc = ringo_convert_batch(b, preds, npred, best, stream, &bt);
-        const double ms =
-            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        ringo_batch_free(bt);
-        if (rc != RINGO_OK) return rc;
-        if (ms < best_t) {
-          best_t = ms;
-          best_o.rank_method = r;
-          best_o.prefetch_waves = pw;
-        }
+    int rc = RINGO_OK;
+    const auto measure = [&](const SweepOpts& so) {
+      const ringo_sort_opts o{so.rank_method, so.prefetch_waves, 0, so.in_digit_bits, 0};
+      ringo_sort_opts_force(&o);
+      const auto t0 = std::chrono::steady_clock::now();
+      ringo_batch* bt = nullptr;
+      rc = ringo_convert_batch(b, preds, npred, best, stream, &bt);
+      const double ms =
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      ringo_batch_free(bt);
+      if (rc == RINGO_OK && ms < best_t) {
+        best_t = ms;
+        best_o = so;
       }
-    }
+    };
+    for_each_candidate(measure, [&] { return best_o; }, [&] { return rc == RINGO_OK; });
+    if (rc != RINGO_OK) return rc;
   }
   record_tuned(1, npred > 0 ? total / (uint64_t)npred : 0, best_o, best, best_t, 0, 0);
   *best_wave_rows = best;

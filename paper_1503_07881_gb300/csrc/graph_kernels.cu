@@ -35,17 +35,21 @@ __device__ __forceinline__ ScanChunks chunks_of(const Ctl* ctl, int i) {
 //   in-sort keys  spare[e]   = dst-run index << 32 | s_index(src)
 //   out_nbr[e]               = dst-run index (turned into a node index later)
 //   usrc[s], usrc_start[s]   = src ID and its first edge; usrc_start[Vs] = E
-//   in_sort.hist             = digit histograms of the in-sort passes
+//   in_sort.hist             = digit histograms of the in-sort passes, RB-bit
+//                              digits of the dst-run index (pass p, digit d
+//                              at [(p << RB) + d])
+template <int RB>
 __global__ void __launch_bounds__(kScanThreads, 6)
     k_dedup(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
+  constexpr int R = 1 << RB;
   __shared__ uint64_t s_keys[kScanTile];  // the tile, read once, coalesced
-  __shared__ uint32_t s_hist[kInPasses][kRadix];
+  __shared__ uint32_t s_hist[kInPasses][R];
   __shared__ uint32_t s_we[kWarps], s_ws[kWarps];
   __shared__ uint64_t s_prefix, s_before;
   __shared__ Claim s_cl;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) claim_slot(m, counter, &s_cl);
-  for (int i = tid; i < kInPasses * kRadix; i += kScanThreads) (&s_hist[0][0])[i] = 0;
+  for (int i = tid; i < kInPasses * R; i += kScanThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
   if (!s_cl.valid) return;
   Ctl* __restrict__ ctl = ctls + s_cl.seg;
@@ -59,7 +63,7 @@ __global__ void __launch_bounds__(kScanThreads, 6)
   // in-sort digit positions that can vary: dst-run indices are below Vd
   const uint32_t Vd = ctl->Vd;
   int npos = 1;
-  while (npos < kInPasses && ((Vd - 1) >> (8 * npos)) != 0) ++npos;
+  while (npos < kInPasses && ((Vd - 1) >> (RB * npos)) != 0) ++npos;
   for (uint32_t j = tid; j < cnt; j += kScanThreads) s_keys[j] = __ldcs(keys + base + j);
   if (tid == 0) s_before = base > 0 ? keys[base - 1] : 0;
   __syncthreads();
@@ -108,7 +112,7 @@ __global__ void __launch_bounds__(kScanThreads, 6)
         ctl->Vs = Vs;
         ctl->usrc_start[Vs] = (int32_t)E;
         // positions that cannot vary hold every edge in digit 0
-        for (int p = npos; p < kInPasses; ++p) ctl->in_sort.hist[p][0] = E;
+        for (int p = npos; p < kInPasses; ++p) ctl->in_sort.hist[p << RB] = E;
       }
     }
   }
@@ -136,7 +140,7 @@ __global__ void __launch_bounds__(kScanThreads, 6)
     const uint32_t db = (uint32_t)k;
     // the highest varying position takes few values: one add per value per
     // warp instead of up to 32 colliding adds on one counter
-    const uint32_t td = (db >> (8 * top)) & 0xFFu;
+    const uint32_t td = (db >> (RB * top)) & (R - 1u);
     const uint32_t peers = __match_any_sync(emask, td);
     if (lane == 31 - __clz(peers)) atomicAdd(&s_hist[top][td], (uint32_t)__popc(peers));
     const uint32_t sidx = head_s ? s : s - 1;
@@ -144,21 +148,25 @@ __global__ void __launch_bounds__(kScanThreads, 6)
     out_nbr[e] = (int32_t)db;
 #pragma unroll
     for (int p = 0; p < kInPasses - 1; ++p)  // fixed trip count: predicated, no loop branch
-      if (p < top) atomicAdd(&s_hist[p][(db >> (8 * p)) & 0xFFu], 1u);
+      if (p < top) atomicAdd(&s_hist[p][(db >> (RB * p)) & (R - 1u)], 1u);
     if (head_s) {
       usrc[s] = unbias((uint32_t)(k >> 32));
       usrc_start[s] = (int32_t)e;
     }
   }
   __syncthreads();
-  for (int i = tid; i < kInPasses * kRadix; i += kScanThreads) {
+  for (int i = tid; i < kInPasses * R; i += kScanThreads) {
     const uint32_t c = (&s_hist[0][0])[i];
-    if (c) atomicAdd(&ctl->in_sort.hist[0][0] + i, c);
+    if (c) atomicAdd(&ctl->in_sort.hist[0] + i, c);
   }
 }
 
 void launch_dedup(const Launch& L, uint32_t* counter, cudaStream_t s) {
-  if (L.row_slots) k_dedup<<<L.row_slots, kScanThreads, 0, s>>>(L.ctls, L.rows, counter);
+  if (!L.row_slots) return;
+  if (L.opts.in_digit_bits == 9)
+    k_dedup<9><<<L.row_slots, kScanThreads, 0, s>>>(L.ctls, L.rows, counter);
+  else
+    k_dedup<8><<<L.row_slots, kScanThreads, 0, s>>>(L.ctls, L.rows, counter);
 }
 
 // ------------------------------------------------------------- dst rank ---

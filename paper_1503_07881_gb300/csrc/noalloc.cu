@@ -52,10 +52,10 @@ constexpr size_t kOffCtl = 0;
 constexpr size_t kOffKeysA = up(kOffCtl + sizeof(Ctl));
 constexpr size_t kOffKeysB = up(kOffKeysA + 8 * ((size_t)kMaxRows + 1));
 constexpr size_t kOffSt0 = up(kOffKeysB + 8 * ((size_t)kMaxRows + 1));
-constexpr size_t kOffSt1 = up(kOffSt0 + 4 * kTiles * kRadix);
+constexpr size_t kOffSt1 = up(kOffSt0 + radix_status_bytes(kTiles));
 constexpr size_t kChunks = (kTiles + kChunkTiles - 1) / kChunkTiles;
 constexpr size_t kChunkBytes = up(radix_chunk_bytes(kChunks));
-constexpr size_t kOffCh0 = up(kOffSt1 + 4 * kTiles * kRadix);
+constexpr size_t kOffCh0 = up(kOffSt1 + radix_status_bytes(kTiles));
 constexpr size_t kOffCh1 = up(kOffCh0 + kChunkBytes);
 constexpr size_t kOffSc0 = up(kOffCh1 + kChunkBytes);
 constexpr size_t chunks_for(size_t tiles) { return (tiles + kChunkTiles - 1) / kChunkTiles; }
@@ -189,7 +189,7 @@ extern "C" int ringo_table_to_graph_noalloc(const int32_t* src, const int32_t* d
   Launch run = solo_launch(dctl, &h, n);
   run.opts = sort_opts_for(0, n);
   NA_TRY(cudaMemcpyAsync(dctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-  NA_TRY(cudaMemsetAsync(ws + kOffSt0, 0, 4 * (size_t)tiles * kRadix, s));
+  NA_TRY(cudaMemsetAsync(ws + kOffSt0, 0, radix_status_bytes(tiles), s));
   NA_TRY(cudaMemsetAsync(ws + kOffCh0, 0, radix_chunk_bytes(chunks), s));
   NA_TRY(cudaMemsetAsync(ws + kOffSc0, 0, kOffUsrc - kOffSc0, s));
   if ((rc = enqueue_phase1(run, s)) != RINGO_OK) return rc;

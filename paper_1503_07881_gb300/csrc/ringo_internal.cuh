@@ -23,10 +23,21 @@
 namespace ringo {
 
 // ------------------------------------------------------------- constants --
-constexpr int kRadixBits = 8;
+constexpr int kRadixBits = 8;   // digit width of the out-sort passes
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kOutPasses = 8;   // 64-bit (src,dst) keys
 constexpr int kInPasses = 4;    // dst half of the (dst, src-run) keys
+// The in-sort may use 9-bit digits instead (SweepOpts::in_digit_bits): four
+// positions cover 36 bits, and three already cover the dst-run index of any
+// table with at most 2^27 distinct destinations.
+constexpr int kMaxRadixBits = 9;
+constexpr int kMaxRadix = 1 << kMaxRadixBits;
+// Words per tile (and per chunk) row of the radix look-back, whatever the
+// digit width of the pass: a pass of 2^b digits uses the first 2^b words.
+constexpr int kStRow = kMaxRadix;
+// Histogram words of one sort: 8 passes x 256 digits or 4 passes x 512.
+constexpr int kHistWords = kOutPasses * kRadix;
+static_assert(kInPasses * kMaxRadix <= kHistWords, "in-sort histograms fit");
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys
@@ -87,10 +98,12 @@ struct SortCtl {
   PassDesc pass[kOutPasses];
   uint32_t n;                 // keys to sort
   uint32_t active_passes;
+  uint32_t bits;              // digit width of the passes (8 or 9)
   uint64_t* result;           // buffer holding the sorted keys
   uint64_t* spare;            // the other ping-pong buffer
-  uint32_t hist[kOutPasses][kRadix];
-  uint32_t base[kOutPasses][kRadix];
+  // digit counts and exclusive starts: pass p, digit d at [(p << bits) + d]
+  uint32_t hist[kHistWords];
+  uint32_t base[kHistWords];
 };
 
 struct alignas(16) Ctl {
@@ -105,7 +118,7 @@ struct alignas(16) Ctl {
   // workspace
   uint64_t* keysA;            // [n_rows + 1]
   uint64_t* keysB;            // [n_rows + 1]
-  uint32_t* status[2];        // [status_rows][kRadix] each, alternating passes
+  uint32_t* status[2];        // [status_rows][kStRow] each, alternating passes
   uint32_t status_rows;
   // chunk level of the radix look-back (kChunkTiles tiles per chunk), two
   // regions alternating with the passes like `status`:
@@ -113,8 +126,8 @@ struct alignas(16) Ctl {
   //                     count they added; one 64-bit word, so a single load
   //                     tells whether the sum is complete
   //   chunk_inc[c][d] = kStInc | inclusive prefix of digit d through chunk c
-  uint64_t* chunk_agg[2];     // [chunks][kRadix]
-  uint32_t* chunk_inc[2];     // [chunks][kRadix]
+  uint64_t* chunk_agg[2];     // [chunks][kStRow]
+  uint32_t* chunk_inc[2];     // [chunks][kStRow]
   uint32_t chunk_rows;
   uint64_t* scan_status[3];   // [tiles] each: dedup, dst_rank, merge
   uint64_t* scan_chunk_agg[3];  // [chunks of those tiles] packed sums
@@ -158,11 +171,15 @@ struct alignas(16) Ctl {
 // Bytes of one region of the radix chunk look-back (aggregates, then
 // prefixes), and its placement.
 __host__ __device__ constexpr uint64_t radix_chunk_bytes(uint64_t chunks) {
-  return 12ull * chunks * kRadix;
+  return 12ull * chunks * kStRow;
 }
 __host__ __device__ inline void place_radix_chunks(Ctl* c, int r, void* p, uint64_t chunks) {
   c->chunk_agg[r] = static_cast<uint64_t*>(p);
-  c->chunk_inc[r] = reinterpret_cast<uint32_t*>(static_cast<char*>(p) + 8ull * chunks * kRadix);
+  c->chunk_inc[r] = reinterpret_cast<uint32_t*>(static_cast<char*>(p) + 8ull * chunks * kStRow);
+}
+// Bytes of one region of the radix tile look-back for `tiles` tiles.
+__host__ __device__ constexpr uint64_t radix_status_bytes(uint64_t tiles) {
+  return 4ull * tiles * kStRow;
 }
 
 // Merge-path splits of the merge tiles (phase 2).  They live in the in-CSR
@@ -192,13 +209,21 @@ struct SegMap {
 //   rank_method     0: peers by shared-memory lane masks (one atomic OR and
 //                      one read per key), 1: peers by one warp ballot per
 //                      digit bit (no shared memory, 32 ALU operations per
-//                      key; no atomic conflicts when many keys share a digit)
+//                      key; no atomic conflicts when many keys share a digit),
+//                   2: peers by one warp match instruction on the digit
 //   prefetch_waves  how far ahead (in waves of resident blocks) each block
 //                   asks L2 for a tile's input; 0: no prefetch
+//   in_digit_bits   digit width of the in-sort passes, 8 or 9
 struct SweepOpts {
   int32_t rank_method = 0;
   int32_t prefetch_waves = 1;
+  int32_t in_digit_bits = 8;
 };
+// The radix pass resident blocks per SM of a variant (its launch bounds):
+// 512-digit passes with lane masks need more shared memory than four fit.
+__host__ __device__ constexpr uint32_t sweep_blocks_per_sm(int bits, int rank_method) {
+  return (bits > 8 && rank_method == 0) ? 3u : 4u;
+}
 
 // The segment table and slot maps of one run, and its claim counters.
 struct Launch {
@@ -247,6 +272,32 @@ struct ForcedOptsGuard {
   bool was;
   SweepOpts saved;
 };
+// The pass variants the tuners measure, in this order: every rank method and
+// prefetch distance with 8-bit in-sort digits, then every rank method with
+// 9-bit in-sort digits at the best prefetch distance so far.  `best()` gives
+// the best options measured so far; the walk stops once `ok()` is false.
+template <class Measure, class Best, class Ok>
+void for_each_candidate(Measure&& measure, Best&& best, Ok&& ok) {
+  for (int r = 0; r <= 2; ++r) {
+    for (int w = 0; w <= 2; ++w) {
+      if (!ok()) return;
+      SweepOpts o;
+      o.rank_method = r;
+      o.prefetch_waves = w;
+      o.in_digit_bits = 8;
+      measure(o);
+    }
+  }
+  const int w = best().prefetch_waves;
+  for (int r = 0; r <= 2; ++r) {
+    if (!ok()) return;
+    SweepOpts o;
+    o.rank_method = r;
+    o.prefetch_waves = w;
+    o.in_digit_bits = 9;
+    measure(o);
+  }
+}
 // Records a tuned choice (in memory and, when a cache file is set, on disk).
 void record_tuned(int kind, uint64_t rows, const SweepOpts& o, int64_t wave_rows, double ms,
                   int out_passes, int in_passes);

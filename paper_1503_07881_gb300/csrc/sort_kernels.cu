@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kHistThreads)
   for (int i = threadIdx.x; i < kOutPasses * kRadix; i += kHistThreads) (&h[0][0])[i] = 0;
   if (threadIdx.x == 0) cur_seg = 0xFFFFFFFFu;
   auto flush = [&](uint32_t sidx) {
-    uint32_t* dst = &ctls[sidx].out_sort.hist[0][0];
+    uint32_t* dst = &ctls[sidx].out_sort.hist[0];  // pass p, digit d at [p * 256 + d]
     for (int i = threadIdx.x; i < kOutPasses * kRadix; i += kHistThreads) {
       const uint32_t c = (&h[0][0])[i];
       if (c) {
@@ -108,31 +108,37 @@ void launch_histogram(const Launch& L, uint32_t* counter, cudaStream_t s) {
 // Turns the pass histograms into global digit offsets and decides, on the
 // device, which passes move keys: a pass whose digit is the same for every
 // key is the identity and is skipped.  Also fixes the ping-pong buffers.
-//   which = 0: out-sort of n_rows keys packed from the columns, digits at
-//              bits 0..63 (passes 0-3: dst, 4-7: src); between pass 3 and
+//   which = 0: out-sort of n_rows keys packed from the columns, 8-bit digits
+//              at bits 0..63 (passes 0-3: dst, 4-7: src); between pass 3 and
 //              pass 4 the dst-rank step always runs (it also packs from the
 //              columns when every dst pass was skipped); buffers keysA/keysB.
-//   which = 1: in-sort of E keys held in the out-sort's spare buffer,
-//              digits at bits 32..63 (the dst-run half).
-__global__ void __launch_bounds__(kRadix) k_plan(Ctl* __restrict__ ctls, int which) {
+//   which = 1: in-sort of E keys held in the out-sort's spare buffer, digits
+//              of in_bits (8 or 9) bits from bit 32 up (the dst-run half).
+__global__ void __launch_bounds__(kMaxRadix) k_plan(Ctl* __restrict__ ctls, int which, int in_bits) {
   Ctl* __restrict__ ctl = ctls + blockIdx.x;
-  __shared__ uint32_t sw[kRadix / 32 + 1];
+  __shared__ uint32_t sw[kMaxRadix / 32 + 1];
   __shared__ uint32_t trivial[kOutPasses];
   SortCtl& sc = which ? ctl->in_sort : ctl->out_sort;
   const int npass = which ? kInPasses : kOutPasses;
   const uint32_t n = which ? ctl->E : ctl->n_rows;
-  if (threadIdx.x < kOutPasses) trivial[threadIdx.x] = 0;
+  const int rb = which ? in_bits : kRadixBits;
+  const uint32_t R = 1u << rb;
+  const uint32_t d = threadIdx.x;
+  if (d < kOutPasses) trivial[d] = 0;
   __syncthreads();
   for (int p = 0; p < npass; ++p) {
-    const uint32_t c = sc.hist[p][threadIdx.x];
+    const uint32_t c = d < R ? sc.hist[(p << rb) + d] : 0u;
     uint32_t total;
-    const uint32_t excl = block_exclusive_sum<kRadix>(c, sw, total);
-    sc.base[p][threadIdx.x] = excl;
-    if (c == n) trivial[p] = 1;
+    const uint32_t excl = block_exclusive_sum<kMaxRadix>(c, sw, total);
+    if (d < R) {
+      sc.base[(p << rb) + d] = excl;
+      if (c == n) trivial[p] = 1;
+    }
     __syncthreads();
   }
   if (threadIdx.x != 0) return;
   sc.n = n;
+  sc.bits = (uint32_t)rb;
   uint64_t* const b0 = which ? ctl->out_sort.spare : ctl->keysA;
   uint64_t* const b1 = which ? ctl->out_sort.result : ctl->keysB;
   const uint64_t* cur = which ? b0 : nullptr;
@@ -140,7 +146,7 @@ __global__ void __launch_bounds__(kRadix) k_plan(Ctl* __restrict__ ctls, int whi
   uint32_t active = 0;
   const uint32_t shift0 = which ? 32 : 0;
   for (int p = 0; p < kOutPasses; ++p) {
-    sc.pass[p].shift = shift0 + kRadixBits * p;
+    sc.pass[p].shift = p < npass ? shift0 + (uint32_t)rb * p : 0u;
     sc.pass[p].active = 0;
     sc.pass[p].in = nullptr;
     sc.pass[p].out = nullptr;
@@ -167,7 +173,7 @@ __global__ void __launch_bounds__(kRadix) k_plan(Ctl* __restrict__ ctls, int whi
 }
 
 void launch_plan(const Launch& L, int which, cudaStream_t s) {
-  if (L.nseg) k_plan<<<L.nseg, kRadix, 0, s>>>(L.ctls, which);
+  if (L.nseg) k_plan<<<L.nseg, kMaxRadix, 0, s>>>(L.ctls, which, L.opts.in_digit_bits == 9 ? 9 : 8);
 }
 
 // ---------------------------------------------------------------- K2/K4 ---
@@ -176,9 +182,11 @@ void launch_plan(const Launch& L, int which, cudaStream_t s) {
 // steps are described at k_onesweep below).  which: 0 out-sort, 1 in-sort.
 // pass: index within that sort.  gpass: global pass number; status region
 // gpass&1 is used, and every processed tile clears its row of region
-// (gpass+1)&1 for the next pass.  A tile waits only on smaller tiles, every
-// one of which was claimed by a block that is resident or done and never
-// waits on a larger tile, so the waits always end.
+// (gpass+1)&1 for the next pass (the first `clear_words` words of the row:
+// that pass's digit count).  A tile waits only on smaller tiles, every one
+// of which was claimed by a block that is resident or done and never waits
+// on a larger tile, so the waits always end.  Rows of both regions are
+// kStRow words apart whatever the digit width.
 
 // Two-level decoupled look-back for digit d of `tile`: first over the
 // earlier tiles of the tile's own chunk (their aggregates or an inclusive
@@ -207,7 +215,7 @@ __device__ __forceinline__ uint32_t digit_lookback2(const uint32_t* __restrict__
     uint32_t v[kLbTiles];
 #pragma unroll
     for (int k = 0; k < kLbTiles; ++k)
-      v[k] = (j - k >= (int64_t)first) ? ld_relaxed_u32(st + (size_t)(j - k) * kRadix + d) : 0u;
+      v[k] = (j - k >= (int64_t)first) ? ld_relaxed_u32(st + (size_t)(j - k) * kStRow + d) : 0u;
     int used = 0;
     bool done = false, stall = false;
 #pragma unroll
@@ -241,8 +249,8 @@ __device__ __forceinline__ uint32_t digit_lookback2(const uint32_t* __restrict__
 #pragma unroll
     for (int k = 0; k < kLbChunks; ++k) {
       const bool in = cc - k >= 0;
-      inc[k] = in ? ld_relaxed_u32(cinc + (size_t)(cc - k) * kRadix + d) : 0u;
-      agg[k] = in ? ld_relaxed_u64(cagg + (size_t)(cc - k) * kRadix + d) : 0ull;
+      inc[k] = in ? ld_relaxed_u32(cinc + (size_t)(cc - k) * kStRow + d) : 0u;
+      agg[k] = in ? ld_relaxed_u64(cagg + (size_t)(cc - k) * kStRow + d) : 0ull;
     }
     int used = 0;
     bool done = false, stall = false;
@@ -275,26 +283,27 @@ __device__ __forceinline__ uint32_t digit_lookback2(const uint32_t* __restrict__
   return excl;
 }
 
-// The pass.  One 4096-key tile per block, four blocks per SM.  Per tile:
+// The pass.  One 4096-key tile per block, three or four blocks per SM.  Per
+// tile:
 //   0. the tile arrives in shared memory by one bulk asynchronous copy
 //      (cp.async.bulk + mbarrier; the first pass copies the two columns and
 //      packs the keys as it reads them);
 //   1. digit counts per warp (shared-memory adds), published at once, also
 //      into the chunk aggregate of the two-level look-back;
-//   2. thread d owns digit d: per-warp starts within the tile;
+//   2. thread t owns digits [t * DPT, t * DPT + DPT), DPT = digits / 256:
+//      per-warp starts within the tile;
 //   3. stable ranks: the lanes of a warp holding the same digit find each
-//      other through a shared peer mask (atomicOr of lane bits); the highest
-//      of them advances the warp's running position of that digit for the
-//      whole group, so each key gets its final place in the staged tile;
+//      other (through a shared lane mask, one ballot per digit bit, or a
+//      warp match); the highest of them advances the warp's running position
+//      of that digit for the whole group, so each key gets its final place
+//      in the staged tile;
 //   4. the keys move to their places in the same buffer;
-//   5. two-level look-back (thread d, digit d) -> global digit offsets;
+//   5. two-level look-back (thread t, its digits) -> global digit offsets;
 //   6. coalesced scatter of the staged tile.
-// The digit position is a template parameter (byte BYTE of the key's high or
-// low word, taken with one byte permute), and full tiles take a path without
-// bounds checks, so the per-key work is a few shared-memory operations and
-// no branches.
-// Blocks of the pass resident at once per SM (the launch bounds' minimum).
-constexpr uint32_t kSweepBlocksPerSm = 4;
+// An 8-bit digit is byte BYTE of the key's high or low word (a template
+// parameter, taken with one byte permute); a 9-bit digit is taken with a
+// shift and a mask.  Full tiles take a path without bounds checks, so the
+// per-key work is a few shared-memory operations and no branches.
 
 // What thread 0 learns about the block's tile, for the whole block.
 struct SweepTile {
@@ -304,29 +313,41 @@ struct SweepTile {
   uint32_t n;      // keys of this sort in the tile's segment
   uint32_t cnt;    // keys in the tile
   uint32_t bulk;   // keys brought by the bulk copy; the rest by plain loads
+  uint32_t shift;  // position of the digit within its 32-bit word
   const uint64_t* in;  // NULL: pack from the columns
   uint64_t* out;
 };
 
+template <int R, int RANK>
 struct SweepSmem {
-  uint64_t keys[kSortTile];               // the tile: input, then staged in digit order
-  uint32_t whist[kSortWarps][kRadix];     // per-warp counts, then running positions
-  uint32_t mask[kSortWarps][kRadix + 1];  // peer masks; slot kRadix: lanes past the end
-  int32_t delta[kRadix];
+  uint64_t keys[kSortTile];       // the tile: input, then staged in digit order
+  uint32_t whist[kSortWarps][R];  // per-warp counts, then running positions
+  // peer masks (lane-mask ranking only); slot R: lanes past the end
+  uint32_t mask[RANK == 0 ? kSortWarps : 1][RANK == 0 ? R + 1 : 1];
+  uint32_t delta[R];              // global place of a staged key minus its index
   uint32_t sw[kSortWarps + 1];
   SweepTile t;
   uint64_t bar;
 };
 
-template <int BYTE>
-__device__ __forceinline__ uint32_t byte_of(uint32_t w) {
-  return __byte_perm(w, 0u, 0x4440u + BYTE);
+__host__ __device__ constexpr size_t sweep_smem_bytes(int bits, int rank) {
+  return bits > 8 ? (rank == 0 ? sizeof(SweepSmem<512, 0>) : sizeof(SweepSmem<512, 1>))
+                  : (rank == 0 ? sizeof(SweepSmem<256, 0>) : sizeof(SweepSmem<256, 1>));
+}
+
+template <int RB, int BYTE>
+__device__ __forceinline__ uint32_t digit_of(uint32_t w, uint32_t sh) {
+  if constexpr (BYTE >= 0) {
+    return __byte_perm(w, 0u, 0x4440u + BYTE);
+  } else {
+    return (w >> sh) & ((1u << RB) - 1u);
+  }
 }
 
 // The word of key j that holds this pass's digit.  Packed first pass: the
 // columns sit in the tile buffer as src[0..4096) then dst[0..4096).
-template <bool HI, bool PACK>
-__device__ __forceinline__ uint32_t key_word(const SweepSmem& S, uint32_t j) {
+template <bool HI, bool PACK, class SM>
+__device__ __forceinline__ uint32_t key_word(const SM& S, uint32_t j) {
   if (PACK) {
     const int32_t* cols = reinterpret_cast<const int32_t*>(S.keys);
     return (uint32_t)cols[HI ? j : kSortTile + j] ^ kBias;
@@ -334,8 +355,8 @@ __device__ __forceinline__ uint32_t key_word(const SweepSmem& S, uint32_t j) {
   const uint64_t k = S.keys[j];
   return HI ? (uint32_t)(k >> 32) : (uint32_t)k;
 }
-template <bool PACK>
-__device__ __forceinline__ uint64_t key_at(const SweepSmem& S, uint32_t j) {
+template <bool PACK, class SM>
+__device__ __forceinline__ uint64_t key_at(const SM& S, uint32_t j) {
   if (PACK) {
     const int32_t* cols = reinterpret_cast<const int32_t*>(S.keys);
     return ((uint64_t)((uint32_t)cols[j] ^ kBias) << 32) | ((uint32_t)cols[kSortTile + j] ^ kBias);
@@ -343,77 +364,114 @@ __device__ __forceinline__ uint64_t key_at(const SweepSmem& S, uint32_t j) {
   return S.keys[j];
 }
 
-// Steps 1-6 for one tile of `cnt` keys (FULL: cnt == kSortTile).
-template <int BYTE, bool HI, int RANK, bool PACK, bool FULL>
-__device__ __forceinline__ void sweep_body(SweepSmem& S, Ctl* __restrict__ ctl, SortCtl& sc,
-                                           uint64_t* __restrict__ out, uint32_t tile,
+// Steps 1-6 for one tile of `cnt` keys (FULL: cnt == kSortTile); `sh` is the
+// digit's position within its word (9-bit digits).
+template <int RB, int BYTE, bool HI, int RANK, bool PACK, bool FULL>
+__device__ __forceinline__ void sweep_body(SweepSmem<(1 << RB), RANK>& S, Ctl* __restrict__ ctl,
+                                           SortCtl& sc, uint64_t* __restrict__ out, uint32_t tile,
                                            uint32_t ntiles, uint32_t cnt, uint32_t n, int pass,
-                                           int reg) {
+                                           int reg, uint32_t sh) {
+  constexpr int R = 1 << RB;
+  constexpr int DPT = R / kSortThreads;
+  static_assert(DPT == 1 || DPT == 2, "one or two digits per thread");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t wslot = warp * (kSortItems * 32) + lane;
+  const uint32_t d0 = (uint32_t)tid * DPT;  // this thread's first digit
   // 1. counts
   uint32_t* whist = S.whist[warp];
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const uint32_t j = wslot + i * 32;
-    if (FULL || j < cnt) atomicAdd(whist + byte_of<BYTE>(key_word<HI, PACK>(S, j)), 1u);
+    if (FULL || j < cnt) atomicAdd(whist + digit_of<RB, BYTE>(key_word<HI, PACK>(S, j), sh), 1u);
   }
   __syncthreads();
-  // 2. thread tid owns digit tid
-  uint32_t c[kSortWarps];
-  uint32_t bin_total = 0;
+  // 2. thread tid owns digits d0 .. d0 + DPT - 1
+  uint32_t c[DPT][kSortWarps];
+  uint32_t bin_total[DPT];
+#pragma unroll
+  for (int k = 0; k < DPT; ++k) bin_total[k] = 0;
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w) {
-    c[w] = S.whist[w][tid];
-    bin_total += c[w];
+    if constexpr (DPT == 1) {
+      c[0][w] = S.whist[w][tid];
+    } else {
+      const uint2 v = reinterpret_cast<const uint2*>(S.whist[w])[tid];
+      c[0][w] = v.x;
+      c[DPT - 1][w] = v.y;
+    }
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) bin_total[k] += c[k][w];
   }
   uint32_t* __restrict__ st = ctl->status[reg];
-  uint32_t* my_st = st + (size_t)tile * kRadix + tid;
-  st_relaxed_u32(my_st, tile == 0 ? (kStInc | bin_total) : (1u + bin_total));
+  uint32_t* my_st = st + (size_t)tile * kStRow + d0;
   const uint32_t chunk = tile >> kChunkShift;
   uint64_t* cagg = ctl->chunk_agg[reg];
   uint32_t* cinc = ctl->chunk_inc[reg];
-  // one more tile of this chunk, and its count, in one atomic word
-  atomicAdd(reinterpret_cast<unsigned long long*>(cagg + (size_t)chunk * kRadix + tid),
-            (1ull << 32) | bin_total);
+  uint32_t my_total = 0;
+#pragma unroll
+  for (int k = 0; k < DPT; ++k) {
+    st_relaxed_u32(my_st + k, tile == 0 ? (kStInc | bin_total[k]) : (1u + bin_total[k]));
+    // one more tile of this chunk, and its count, in one atomic word
+    atomicAdd(reinterpret_cast<unsigned long long*>(cagg + (size_t)chunk * kStRow + d0 + k),
+              (1ull << 32) | bin_total[k]);
+    my_total += bin_total[k];
+  }
   uint32_t tile_total;
-  const uint32_t bin_start = block_exclusive_sum<kSortThreads>(bin_total, S.sw, tile_total);
+  const uint32_t start0 = block_exclusive_sum<kSortThreads>(my_total, S.sw, tile_total);
+  uint32_t bin_start[DPT];
   {
-    uint32_t run = bin_start;
+    uint32_t run = start0;
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+      bin_start[k] = run;
+      run += bin_total[k];
+    }
+  }
+  {
+    uint32_t run[DPT];
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) run[k] = bin_start[k];
 #pragma unroll
     for (int w = 0; w < kSortWarps; ++w) {
-      S.whist[w][tid] = run;
-      run += c[w];
+      if constexpr (DPT == 1) {
+        S.whist[w][tid] = run[0];
+      } else {
+        reinterpret_cast<uint2*>(S.whist[w])[tid] = make_uint2(run[0], run[DPT - 1]);
+      }
+#pragma unroll
+      for (int k = 0; k < DPT; ++k) run[k] += c[k][w];
     }
   }
   __syncthreads();
   // 3. ranks -> places in the staged tile
   const uint32_t lt = lanemask_lt();
   const uint32_t bit = 1u << lane;
-  const uint32_t wmask = smem_addr(S.mask[warp]);
+  const uint32_t wmask = RANK == 0 ? smem_addr(S.mask[warp]) : 0u;
   const uint32_t whaddr = smem_addr(whist);
   uint32_t lpos[kSortItems / 2];  // two 16-bit places per register
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const uint32_t j = wslot + i * 32;
     const bool ok = FULL || j < cnt;
-    const uint32_t d = ok ? byte_of<BYTE>(key_word<HI, PACK>(S, j)) : (uint32_t)kRadix;
+    const uint32_t d = ok ? digit_of<RB, BYTE>(key_word<HI, PACK>(S, j), sh) : (uint32_t)R;
     uint32_t peers, old = 0;
     if constexpr (RANK == 0) {
       asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(wmask + 4 * d), "r"(bit) : "memory");
       __syncwarp();
       asm volatile("ld.shared.u32 %0, [%1];" : "=r"(peers) : "r"(wmask + 4 * d) : "memory");
       __syncwarp();
-    } else {
+    } else if constexpr (RANK == 1) {
       // one ballot per digit bit (and one for "past the end" in a partial
       // tile): the lanes that agree on every bit
       peers = 0xFFFFFFFFu;
 #pragma unroll
-      for (int q = 0; q < (FULL ? kRadixBits : kRadixBits + 1); ++q) {
+      for (int q = 0; q < (FULL ? RB : RB + 1); ++q) {
         const bool b = (d >> q) & 1u;
         const uint32_t bb = __ballot_sync(0xFFFFFFFFu, b);
         peers &= b ? bb : ~bb;
       }
+    } else {
+      peers = __match_any_sync(0xFFFFFFFFu, d);
     }
     const uint32_t leader = 31u - __clz(peers);
     // the group's highest lane (clears the mask entry and) advances the
@@ -450,17 +508,26 @@ __device__ __forceinline__ void sweep_body(SweepSmem& S, Ctl* __restrict__ ctl, 
   for (int i = 0; i < kSortItems; ++i) {
     if (FULL || wslot + i * 32 < cnt) S.keys[(lpos[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu] = key[i];
   }
-  // 5. look-back
-  uint32_t excl = 0;
-  if (tile > 0) {
-    excl = digit_lookback2(st, cagg, cinc, tile, ntiles, tid, ctl);
-    st_relaxed_u32(my_st, kStInc | (excl + bin_total));
+  // 5. look-back, one walk per digit; each digit's inclusive prefix is
+  // published as soon as it is known
+  uint32_t excl[DPT];
+#pragma unroll
+  for (int k = 0; k < DPT; ++k) {
+    excl[k] = 0;
+    if (tile > 0) {
+      excl[k] = digit_lookback2(st, cagg, cinc, tile, ntiles, d0 + k, ctl);
+      st_relaxed_u32(my_st + k, kStInc | (excl[k] + bin_total[k]));
+    }
   }
-  if ((tile & (kChunkTiles - 1)) == 0 && chunk > 0)
-    st_relaxed_u32(cinc + (size_t)(chunk - 1) * kRadix + tid, kStInc | excl);
-  if ((tile & (kChunkTiles - 1)) == kChunkTiles - 1 || tile == ntiles - 1)
-    st_relaxed_u32(cinc + (size_t)chunk * kRadix + tid, kStInc | (excl + bin_total));
-  S.delta[tid] = (int32_t)(sc.base[pass][tid] + excl) - (int32_t)bin_start;
+#pragma unroll
+  for (int k = 0; k < DPT; ++k) {
+    if ((tile & (kChunkTiles - 1)) == 0 && chunk > 0)
+      st_relaxed_u32(cinc + (size_t)(chunk - 1) * kStRow + d0 + k, kStInc | excl[k]);
+    if ((tile & (kChunkTiles - 1)) == kChunkTiles - 1 || tile == ntiles - 1)
+      st_relaxed_u32(cinc + (size_t)chunk * kStRow + d0 + k, kStInc | (excl[k] + bin_total[k]));
+    // modulo 2^32: the sum below is the key's place, which is below n
+    S.delta[d0 + k] = sc.base[(pass << RB) + d0 + k] + excl[k] - bin_start[k];
+  }
   __syncthreads();
   // 6. scatter
 #pragma unroll
@@ -469,18 +536,20 @@ __device__ __forceinline__ void sweep_body(SweepSmem& S, Ctl* __restrict__ ctl, 
     if (FULL || j < cnt) {
       const uint64_t k = S.keys[j];
       const uint32_t w = HI ? (uint32_t)(k >> 32) : (uint32_t)k;
-      const uint32_t pos = (uint32_t)(S.delta[byte_of<BYTE>(w)] + (int32_t)j);
+      const uint32_t pos = S.delta[digit_of<RB, BYTE>(w, sh)] + j;
       if (pos < n) out[pos] = k;
     }
   }
 }
 
-template <int BYTE, bool HI, int RANK>
-__global__ void __launch_bounds__(kSortThreads, kSweepBlocksPerSm)
+template <int RB, int BYTE, bool HI, int RANK>
+__global__ void __launch_bounds__(kSortThreads, sweep_blocks_per_sm(RB, RANK))
     k_onesweep(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter, int which, int pass,
-               int gpass, uint32_t ahead_slots) {
+               int gpass, uint32_t ahead_slots, uint32_t clear_words) {
+  constexpr int R = 1 << RB;
+  using Smem = SweepSmem<R, RANK>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  SweepSmem& S = *reinterpret_cast<SweepSmem*>(smem_raw);
+  Smem& S = *reinterpret_cast<Smem*>(smem_raw);
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(&S.bar, 1);
@@ -509,6 +578,7 @@ __global__ void __launch_bounds__(kSortThreads, kSweepBlocksPerSm)
       t.seg = seg;
       t.tile = tile;
       t.n = n;
+      t.shift = pd.shift & 31u;
       if (pd.active && tile < (n + kSortTile - 1) / kSortTile) {
         const uint32_t base = tile * (uint32_t)kSortTile;
         t.work = 1;
@@ -557,12 +627,10 @@ __global__ void __launch_bounds__(kSortThreads, kSweepBlocksPerSm)
       }
     }
   }
-#pragma unroll
-  for (int w = 0; w < kSortWarps; ++w) {
-    S.whist[w][tid] = 0;
-    S.mask[w][tid] = 0;
+  for (int i = tid; i < kSortWarps * R; i += kSortThreads) (&S.whist[0][0])[i] = 0;
+  if constexpr (RANK == 0) {
+    for (int i = tid; i < kSortWarps * (R + 1); i += kSortThreads) (&S.mask[0][0])[i] = 0;
   }
-  if (tid < kSortWarps) S.mask[tid][kRadix] = 0;
   __syncthreads();
   const SweepTile t = S.t;
   if (!t.valid) return;
@@ -572,11 +640,14 @@ __global__ void __launch_bounds__(kSortThreads, kSweepBlocksPerSm)
   if (tile < ctl->status_rows) {
     // clear this tile's row (and, for a chunk's first tile, the chunk's row)
     // of the other region for the next pass
-    ctl->status[nreg][(size_t)tile * kRadix + tid] = 0;
+    uint32_t* row = ctl->status[nreg] + (size_t)tile * kStRow;
+    for (uint32_t i = tid; i < clear_words; i += kSortThreads) row[i] = 0;
     if ((tile & (kChunkTiles - 1)) == 0) {
-      const uint32_t cidx = tile >> kChunkShift;
-      ctl->chunk_agg[nreg][(size_t)cidx * kRadix + tid] = 0;
-      ctl->chunk_inc[nreg][(size_t)cidx * kRadix + tid] = 0;
+      const size_t cbase = (size_t)(tile >> kChunkShift) * kStRow;
+      for (uint32_t i = tid; i < clear_words; i += kSortThreads) {
+        ctl->chunk_agg[nreg][cbase + i] = 0;
+        ctl->chunk_inc[nreg][cbase + i] = 0;
+      }
     }
   }
   if (!t.work) return;
@@ -605,26 +676,32 @@ __global__ void __launch_bounds__(kSortThreads, kSweepBlocksPerSm)
   }
   SortCtl& sc = which ? ctl->in_sort : ctl->out_sort;
   const bool full = cnt == (uint32_t)kSortTile;
-  if (!HI && !t.in) {
-    if (full) sweep_body<BYTE, HI, RANK, true, true>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
-    else sweep_body<BYTE, HI, RANK, true, false>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
-  } else {
-    if (full) sweep_body<BYTE, HI, RANK, false, true>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
-    else sweep_body<BYTE, HI, RANK, false, false>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg);
+  const uint32_t sh = t.shift;
+  if constexpr (!HI) {
+    if (!t.in) {
+      if (full) sweep_body<RB, BYTE, HI, RANK, true, true>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg, sh);
+      else sweep_body<RB, BYTE, HI, RANK, true, false>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg, sh);
+      return;
+    }
   }
+  if (full) sweep_body<RB, BYTE, HI, RANK, false, true>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg, sh);
+  else sweep_body<RB, BYTE, HI, RANK, false, false>(S, ctl, sc, t.out, tile, ntiles, cnt, n, pass, reg, sh);
 }
 
-using SweepFn = void (*)(Ctl*, SegMap, uint32_t*, int, int, int, uint32_t);
-// [rank method][hi][byte]: the digit of out-sort pass p is byte p % 4 of the
-// low word (p < 4) or of the high word; in-sort pass p is byte p of the high
-// word
-#define RINGO_SWEEPS(R)                                                                      \
-  {{k_onesweep<0, false, R>, k_onesweep<1, false, R>, k_onesweep<2, false, R>,              \
-    k_onesweep<3, false, R>},                                                                \
-   {k_onesweep<0, true, R>, k_onesweep<1, true, R>, k_onesweep<2, true, R>,                 \
-    k_onesweep<3, true, R>}}
-static const SweepFn kSweep[2][2][4] = {RINGO_SWEEPS(0), RINGO_SWEEPS(1)};
-#undef RINGO_SWEEPS
+using SweepFn = void (*)(Ctl*, SegMap, uint32_t*, int, int, int, uint32_t, uint32_t);
+// 8-bit digits, [rank method][hi][byte]: the digit of out-sort pass p is
+// byte p % 4 of the low word (p < 4) or of the high word; in-sort pass p is
+// byte p of the high word.  9-bit digits (in-sort only), [rank method]: bits
+// 9p .. 9p+8 of the high word.
+#define RINGO_SWEEPS8(R)                                                                     \
+  {{k_onesweep<8, 0, false, R>, k_onesweep<8, 1, false, R>, k_onesweep<8, 2, false, R>,     \
+    k_onesweep<8, 3, false, R>},                                                             \
+   {k_onesweep<8, 0, true, R>, k_onesweep<8, 1, true, R>, k_onesweep<8, 2, true, R>,        \
+    k_onesweep<8, 3, true, R>}}
+static const SweepFn kSweep8[3][2][4] = {RINGO_SWEEPS8(0), RINGO_SWEEPS8(1), RINGO_SWEEPS8(2)};
+#undef RINGO_SWEEPS8
+static const SweepFn kSweep9[3] = {k_onesweep<9, -1, true, 0>, k_onesweep<9, -1, true, 1>,
+                                   k_onesweep<9, -1, true, 2>};
 
 static std::mutex g_sweep_attr_mu;
 static uint64_t g_sweep_attr_devs = 0;  // bit d: set on device d
@@ -636,11 +713,14 @@ void prepare_launches() {
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_sweep_attr_mu);
   if (dev < 64 && !((g_sweep_attr_devs >> dev) & 1)) {
-    for (int r = 0; r < 2; ++r)
+    for (int r = 0; r < 3; ++r) {
       for (int h = 0; h < 2; ++h)
         for (int b = 0; b < 4; ++b)
-          cudaFuncSetAttribute(kSweep[r][h][b], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)sizeof(SweepSmem));
+          cudaFuncSetAttribute(kSweep8[r][h][b], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sweep_smem_bytes(8, r));
+      cudaFuncSetAttribute(kSweep9[r], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sweep_smem_bytes(9, r));
+    }
     g_sweep_attr_devs |= 1ull << dev;
   }
 }
@@ -649,17 +729,26 @@ void launch_onesweep(const Launch& L, int which, int pass, int gpass, uint32_t* 
                      cudaStream_t s) {
   if (L.row_slots == 0) return;
   prepare_launches();
-  // shift = (which ? 32 : 0) + 8 * pass; see k_plan
-  const int shift = (which ? 32 : 0) + kRadixBits * pass;
-  const int rank = L.opts.rank_method == 1 ? 1 : 0;
-  const SweepFn fn = kSweep[rank][shift >= 32][(shift & 31) >> 3];
+  const int rank = L.opts.rank_method >= 0 && L.opts.rank_method <= 2 ? L.opts.rank_method : 0;
+  const int in_bits = L.opts.in_digit_bits == 9 ? 9 : 8;
+  const int bits = which ? in_bits : kRadixBits;
+  SweepFn fn;
+  if (bits == 9) {
+    fn = kSweep9[rank];
+  } else {
+    // shift = (which ? 32 : 0) + 8 * pass; see k_plan
+    const int shift = (which ? 32 : 0) + kRadixBits * pass;
+    fn = kSweep8[rank][shift >= 32][(shift & 31) >> 3];
+  }
+  // the digit count of the pass that uses the other status region next
+  const uint32_t clear = gpass + 1 < kOutPasses ? (uint32_t)kRadix : (1u << in_bits);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const uint32_t waves = (uint32_t)max(0, min(2, L.opts.prefetch_waves));
-  const uint32_t ahead = waves * kSweepBlocksPerSm * (uint32_t)sms;
-  fn<<<L.row_slots, kSortThreads, sizeof(SweepSmem), s>>>(L.ctls, L.rows, counter, which, pass,
-                                                          gpass, ahead);
+  const uint32_t ahead = waves * sweep_blocks_per_sm(bits, rank) * (uint32_t)sms;
+  fn<<<L.row_slots, kSortThreads, sweep_smem_bytes(bits, rank), s>>>(
+      L.ctls, L.rows, counter, which, pass, gpass, ahead, clear);
 }
 
 }  // namespace ringo

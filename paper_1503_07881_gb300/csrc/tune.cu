@@ -78,7 +78,8 @@ void save_locked() {
     o << (first ? "" : ",\n") << " {\"gpu\": \"" << json_escape(std::get<0>(kv.first))
       << "\", \"kind\": " << std::get<1>(kv.first) << ", \"size_class\": " << std::get<2>(kv.first)
       << ", \"rank_method\": " << e.opts.rank_method << ", \"prefetch_waves\": "
-      << e.opts.prefetch_waves << ", \"wave_rows\": " << e.wave_rows << ", \"ms\": " << e.ms
+      << e.opts.prefetch_waves << ", \"in_digit_bits\": " << e.opts.in_digit_bits
+      << ", \"wave_rows\": " << e.wave_rows << ", \"ms\": " << e.ms
       << ", \"out_passes\": " << e.out_passes << ", \"in_passes\": " << e.in_passes << "}";
     first = false;
   }
@@ -124,8 +125,10 @@ bool load_locked(const std::string& path) {
     TuneEntry e;
     e.opts.rank_method = v.count("rank_method") ? (int)v["rank_method"] : 0;
     e.opts.prefetch_waves = v.count("prefetch_waves") ? (int)v["prefetch_waves"] : 1;
-    if (e.opts.rank_method < 0 || e.opts.rank_method > 1) e.opts.rank_method = 0;
+    e.opts.in_digit_bits = v.count("in_digit_bits") ? (int)v["in_digit_bits"] : 8;
+    if (e.opts.rank_method < 0 || e.opts.rank_method > 2) e.opts.rank_method = 0;
     if (e.opts.prefetch_waves < 0 || e.opts.prefetch_waves > 2) e.opts.prefetch_waves = 1;
+    if (e.opts.in_digit_bits != 9) e.opts.in_digit_bits = 8;
     e.wave_rows = v.count("wave_rows") ? (int64_t)v["wave_rows"] : 0;
     e.ms = v.count("ms") ? v["ms"] : 0;
     e.out_passes = v.count("out_passes") ? (int)v["out_passes"] : 0;
@@ -136,8 +139,9 @@ bool load_locked(const std::string& path) {
 }
 
 bool valid_opts(const ringo_sort_opts* o) {
-  return o && o->rank_method >= 0 && o->rank_method <= 1 && o->prefetch_waves >= 0 &&
-         o->prefetch_waves <= 2 && o->wave_rows >= 0;
+  return o && o->rank_method >= 0 && o->rank_method <= 2 && o->prefetch_waves >= 0 &&
+         o->prefetch_waves <= 2 && o->wave_rows >= 0 &&
+         (o->in_digit_bits == 0 || o->in_digit_bits == 8 || o->in_digit_bits == 9);
 }
 
 }  // namespace
@@ -195,11 +199,13 @@ int ringo_sort_opts_force(const ringo_sort_opts* opts) {
     return RINGO_OK;
   }
   if (!valid_opts(opts)) {
-    set_error("ringo_sort_opts_force: rank_method outside 0..1 or prefetch_waves outside 0..2");
+    set_error("ringo_sort_opts_force: rank_method outside 0..2, prefetch_waves outside 0..2, "
+              "in_digit_bits not 0, 8 or 9, or wave_rows < 0");
     return RINGO_EINVAL;
   }
   g_force.rank_method = opts->rank_method;
   g_force.prefetch_waves = opts->prefetch_waves;
+  g_force.in_digit_bits = opts->in_digit_bits == 9 ? 9 : 8;
   g_forced = true;
   return RINGO_OK;
 }
@@ -233,6 +239,7 @@ int ringo_tune_lookup(int32_t kind, int64_t rows, ringo_sort_opts* opts, int32_t
   opts->rank_method = e.opts.rank_method;
   opts->prefetch_waves = e.opts.prefetch_waves;
   opts->wave_rows = e.wave_rows;
+  opts->in_digit_bits = e.opts.in_digit_bits;
   return RINGO_OK;
 }
 
@@ -248,38 +255,37 @@ int ringo_tune_table(const int32_t* src, const int32_t* dst, int64_t nrows, void
   double best_t = 1e300;
   {
     const ForcedOptsGuard keep;  // candidates are forced one after another
-    for (int r = 0; r <= 1 && rc == RINGO_OK; ++r) {
-      for (int w = 0; w <= 2 && rc == RINGO_OK; ++w) {
-        const ringo_sort_opts o{r, w, 0};
-        ringo_sort_opts_force(&o);
-        double t = 1e300;
-        for (int rep = 0; rep < 3 && rc == RINGO_OK; ++rep) {  // the first run warms up
-          cudaStreamSynchronize((cudaStream_t)stream);
-          const auto t0 = std::chrono::steady_clock::now();
-          ringo_graph* g = nullptr;
-          rc = ringo_table_to_graph(src, dst, nrows, stream, &g);
-          const double ms =
-              std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
-                  .count();
-          if (g) {
-            ringo_graph_get_info(g, &info);
-            ringo_graph_free(g);
-          }
-          if (rep > 0 && ms < t) t = ms;
+    const auto measure = [&](const SweepOpts& so) {
+      const ringo_sort_opts o{so.rank_method, so.prefetch_waves, 0, so.in_digit_bits, 0};
+      ringo_sort_opts_force(&o);
+      double t = 1e300;
+      for (int rep = 0; rep < 3 && rc == RINGO_OK; ++rep) {  // the first run warms up
+        cudaStreamSynchronize((cudaStream_t)stream);
+        const auto t0 = std::chrono::steady_clock::now();
+        ringo_graph* g = nullptr;
+        rc = ringo_table_to_graph(src, dst, nrows, stream, &g);
+        const double ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                .count();
+        if (g) {
+          ringo_graph_get_info(g, &info);
+          ringo_graph_free(g);
         }
-        if (rc == RINGO_OK && t < best_t) {
-          best_t = t;
-          best_o.rank_method = r;
-          best_o.prefetch_waves = w;
-        }
+        if (rep > 0 && ms < t) t = ms;
       }
-    }
+      if (rc == RINGO_OK && t < best_t) {
+        best_t = t;
+        best_o = so;
+      }
+    };
+    for_each_candidate(measure, [&] { return best_o; }, [&] { return rc == RINGO_OK; });
   }
   if (rc != RINGO_OK) return rc;
   record_tuned(0, (uint64_t)nrows, best_o, 0, best_t, info.out_sort_passes, info.in_sort_passes);
   best->rank_method = best_o.rank_method;
   best->prefetch_waves = best_o.prefetch_waves;
   best->wave_rows = 0;
+  best->in_digit_bits = best_o.in_digit_bits;
   if (best_ms) *best_ms = best_t;
   return RINGO_OK;
 }

@@ -442,12 +442,13 @@ def ringo_profile_stop() -> list[dict]:
 
 class SortOpts(ctypes.Structure):
     _fields_ = [("rank_method", ctypes.c_int32), ("prefetch_waves", ctypes.c_int32),
-                ("wave_rows", ctypes.c_int64)]
+                ("wave_rows", ctypes.c_int64), ("in_digit_bits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 def _opts_dict(o: SortOpts) -> dict:
     return {"rank_method": o.rank_method, "prefetch_waves": o.prefetch_waves,
-            "wave_rows": o.wave_rows}
+            "wave_rows": o.wave_rows, "in_digit_bits": o.in_digit_bits}
 
 
 def ringo_tune_table(src: torch.Tensor, dst: torch.Tensor, stream=None) -> tuple[dict, float]:
@@ -480,7 +481,7 @@ def ringo_sort_opts_force(opts: dict | None) -> None:
         _check(load().ringo_sort_opts_force(None), "ringo_sort_opts_force")
         return
     o = SortOpts(int(opts.get("rank_method", 0)), int(opts.get("prefetch_waves", 1)),
-                 int(opts.get("wave_rows", 0)))
+                 int(opts.get("wave_rows", 0)), int(opts.get("in_digit_bits", 8)), 0)
     _check(load().ringo_sort_opts_force(ctypes.byref(o)), "ringo_sort_opts_force")
 
 

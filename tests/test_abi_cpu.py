@@ -80,9 +80,13 @@ def test_sort_opts_force_argument_checks():
     """Forcing pass options checks their ranges before anything else; a
     valid force and its release touch no device."""
     lib = ringo.load()
-    for bad in ((2, 1, 0), (-1, 1, 0), (0, 3, 0), (0, -1, 0), (0, 1, -5)):
+    for bad in ((3, 1, 0), (-1, 1, 0), (0, 3, 0), (0, -1, 0), (0, 1, -5), (0, 1, 0, 7),
+                (0, 1, 0, 10), (0, 1, 0, -1)):
         o = ringo.SortOpts(*bad)
         assert lib.ringo_sort_opts_force(ctypes.byref(o)) == ringo.RINGO_EINVAL, bad
+    for good in ((2, 2, 0, 9), (1, 0, 0, 8), (0, 1, 0, 0)):
+        o = ringo.SortOpts(*good)
+        assert lib.ringo_sort_opts_force(ctypes.byref(o)) == ringo.RINGO_OK, good
     o = ringo.SortOpts(1, 2, 0)
     assert lib.ringo_sort_opts_force(ctypes.byref(o)) == ringo.RINGO_OK
     assert lib.ringo_sort_opts_force(None) == ringo.RINGO_OK
