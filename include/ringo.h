@@ -263,9 +263,13 @@ RINGO_API int ringo_graph_pagerank(const ringo_graph* g, double damping, int32_t
  * list holds each neighbour once, sorted (node indices); a self-loop puts the
  * node once in its own list.  Both CSR directions hold the same symmetric
  * lists (num_edges counts each non-loop edge twice, once per endpoint).  The
- * table with each row also reversed goes through ringo_table_to_graph's
- * conversion, so nrows is at most 2^30 - 1 (ERANGE above).  Arguments and
- * other errors as ringo_table_to_graph.
+ * table goes through ringo_table_to_graph's conversion and each node's out-
+ * and in-list are then merged, so nrows is at most 2^31 - 1 (ERANGE above)
+ * and the device memory needed is that of the directed graph plus the
+ * undirected lists (twice, one per CSR direction).  The node list and
+ * num_src_nodes = num_dst_nodes = V describe the undirected graph; the sort
+ * pass counts are the directed conversion's.  Arguments and other errors as
+ * ringo_table_to_graph.
  */
 RINGO_API int ringo_table_to_undirected_graph(const int32_t* src, const int32_t* dst,
                                               int64_t nrows, void* stream, ringo_graph** out);

@@ -475,8 +475,8 @@ int ringo_table_to_undirected_graph(const int32_t* src, const int32_t* dst, int6
     set_error("nrows < 0 or NULL column");
     return RINGO_EINVAL;
   }
-  if (nrows > 0x3FFFFFFF) {
-    set_error("nrows exceeds 2^30 - 1 (the doubled table must fit 2^31 - 1 rows)");
+  if (nrows > 0x7FFFFFFF) {
+    set_error("nrows exceeds 2^31 - 1");
     return RINGO_ERANGE;
   }
   ringo_graph* g = new (std::nothrow) ringo_graph();
@@ -487,18 +487,48 @@ int ringo_table_to_undirected_graph(const int32_t* src, const int32_t* dst, int6
   if (nrows == 0) {
     rc = make_empty(g);
   } else {
-    const uint32_t n = (uint32_t)nrows;
-    const size_t bytes = sizeof(int32_t) * 2 * (size_t)n;
-    int32_t* s2 = (int32_t*)pool_alloc(bytes, g->stream);
-    int32_t* d2 = (int32_t*)pool_alloc(bytes, g->stream);
-    if (!s2 || !d2) {
+    // the directed graph, then each node's out- and in-list merged
+    ringo_graph* d = new (std::nothrow) ringo_graph();
+    if (!d) {
       rc = RINGO_ENOMEM;
     } else {
-      rc = launch_double_table(src, dst, n, s2, d2, g->stream);
-      if (rc == RINGO_OK) rc = convert(s2, d2, 2 * n, g);
+      d->stream = g->stream;
+      d->device = g->device;
+      rc = convert(src, dst, (uint32_t)nrows, d);
+      int64_t* uoff = nullptr;
+      int32_t* unbr = nullptr;
+      uint64_t M = 0;
+      if (rc == RINGO_OK)
+        rc = build_undirected(d->out_off, d->out_nbr, d->in_off, d->in_nbr,
+                              (uint32_t)d->info.num_nodes, (uint64_t)d->info.num_edges, g->stream,
+                              &uoff, &unbr, &M);
+      if (rc == RINGO_OK) {
+        const uint64_t V = (uint64_t)d->info.num_nodes;
+        g->info = d->info;
+        g->info.num_edges = (int64_t)M;
+        g->info.num_src_nodes = (int64_t)V;
+        g->info.num_dst_nodes = (int64_t)V;
+        g->node_ids = d->node_ids;  // the node list is the directed graph's
+        d->node_ids = nullptr;
+        g->out_off = uoff;
+        g->out_nbr = unbr;
+        // the in-CSR holds the same symmetric lists
+        g->in_off = (int64_t*)pool_alloc(8 * (V + 1), g->stream);
+        g->in_nbr = (int32_t*)pool_alloc(4 * M + 4, g->stream);
+        if (!g->in_off || !g->in_nbr) {
+          rc = RINGO_ENOMEM;
+        } else if (cudaMemcpyAsync(g->in_off, uoff, 8 * (V + 1), cudaMemcpyDeviceToDevice,
+                                   g->stream) != cudaSuccess ||
+                   cudaMemcpyAsync(g->in_nbr, unbr, 4 * M, cudaMemcpyDeviceToDevice,
+                                   g->stream) != cudaSuccess ||
+                   cudaStreamSynchronize(g->stream) != cudaSuccess) {
+          set_error(std::string("undirected copy: ") + cudaGetErrorString(cudaGetLastError()));
+          rc = RINGO_ECUDA;
+        }
+      }
+      free_graph_arrays(d);
+      delete d;
     }
-    pool_free(s2, g->stream);
-    pool_free(d2, g->stream);
   }
   if (rc != RINGO_OK) {
     free_graph_arrays(g);

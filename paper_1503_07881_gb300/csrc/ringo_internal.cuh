@@ -319,8 +319,13 @@ int launch_edge_table(const int32_t* node_ids, const int64_t* off, const int32_t
 int launch_node_table(const int32_t* node_ids, const int64_t* out_off, const int64_t* in_off,
                       uint32_t V, int32_t* ids, int64_t* outdeg, int64_t* indeg, cudaStream_t s);
 // undirected conversion and triangles (undirected.cu); ringo statuses
-int launch_double_table(const int32_t* src, const int32_t* dst, uint32_t n, int32_t* s2, int32_t* d2,
-                        cudaStream_t s);
+// The undirected lists of a directed graph (its V nodes, E edges, both
+// CSRs): each node's out- and in-list merged, a neighbour in both kept once.
+// Allocates *und_off[V + 1] and *und_nbr[*M] from the pool (on stream s) and
+// returns a ringo status; on failure nothing stays allocated.
+int build_undirected(const int64_t* out_off, const int32_t* out_nbr, const int64_t* in_off,
+                     const int32_t* in_nbr, uint32_t V, uint64_t E, cudaStream_t s,
+                     int64_t** und_off, int32_t** und_nbr, uint64_t* M);
 int run_triangles(const int64_t* off, const int32_t* nbr, uint32_t V, uint64_t E, cudaStream_t s,
                   uint64_t* count);
 // PageRank (pagerank.cu); returns a ringo status

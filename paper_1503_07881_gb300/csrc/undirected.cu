@@ -3,10 +3,17 @@
 // Table "paralg": triangle counting on the undirected LiveJournal and
 // Twitter2010 graphs).
 //
-// Undirected conversion: each row (s, d) is the edge {s, d}; the table with
-// every row also reversed goes through the same directed conversion, so each
-// node's list holds its neighbours once, sorted, and both CSR directions are
-// the same symmetric lists (a self-loop appears once).
+// Undirected conversion: each row (s, d) is the edge {s, d}, so a node's
+// undirected list is the union of its directed out- and in-lists.  The table
+// goes through the directed conversion once; then the two sorted lists of
+// every node are merged, an element present in both kept once.  In merged
+// position space node v starts at W(v) = out_off[v] + in_off[v]; each block
+// takes 2048 consecutive positions, found by a search for the node and a
+// merge-path split inside it, so a hub's lists are shared among many blocks
+// and many small nodes fill one block.  A counting pass, a scan of the block
+// counts and a writing pass give the lists (each block's output staged in
+// shared memory and stored contiguously) and the offsets (each node's first
+// element is never a duplicate).  Both CSR directions hold the same lists.
 //
 // Triangles: edges are oriented from the endpoint of smaller (degree, index)
 // to the larger, which keeps every oriented list below sqrt(2E) entries; a
@@ -29,17 +36,6 @@ namespace ringo {
 namespace {
 
 constexpr uint32_t kScanTileNodes = 2048;  // nodes per block of the offset scan
-
-__global__ void k_double_table(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                               uint32_t n, int32_t* __restrict__ s2, int32_t* __restrict__ d2) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int32_t a = src[i], b = dst[i];
-    s2[i] = a;
-    d2[i] = b;
-    s2[(size_t)n + i] = b;
-    d2[(size_t)n + i] = a;
-  }
-}
 
 __global__ void k_tc_degree(const int64_t* __restrict__ off, uint32_t V, int32_t* __restrict__ deg) {
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
@@ -89,16 +85,23 @@ __global__ void __launch_bounds__(256)
   if (threadIdx.x == 0) tsum[blockIdx.x] = s[0];
 }
 
-__global__ void k_tc_scan_tiles(uint64_t* __restrict__ tsum, uint32_t tiles) {
-  // one thread: tile counts are few (V / 2048)
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  uint64_t run = 0;
-  for (uint32_t t = 0; t < tiles; ++t) {
+// exclusive scan of tsum[0, tiles) in place, tsum[tiles] = the total; one
+// block of 1024 threads, each over a contiguous run of the tile sums
+__global__ void __launch_bounds__(1024) k_scan_tile_sums(uint64_t* __restrict__ tsum, uint32_t tiles) {
+  __shared__ uint64_t s_sw[1024 / 32 + 1];
+  const uint32_t per = (tiles + 1023) / 1024;
+  const uint32_t b = threadIdx.x * per;
+  const uint32_t e = min(b + per, tiles);
+  uint64_t local = 0;
+  for (uint32_t t = b; t < e; ++t) local += tsum[t];
+  uint64_t total;
+  uint64_t run = block_exclusive_sum<1024>(local, s_sw, total);
+  for (uint32_t t = b; t < e; ++t) {
     const uint64_t c = tsum[t];
     tsum[t] = run;
     run += c;
   }
-  tsum[tiles] = run;
+  if (threadIdx.x == 0) tsum[tiles] = total;
 }
 
 __global__ void __launch_bounds__(256)
@@ -200,6 +203,156 @@ __global__ void __launch_bounds__(256)
   if (lane == 0 && acc) atomicAdd(total, acc);
 }
 
+// ------------------------------------------------------- undirected merge --
+constexpr uint32_t kUmThreads = 256;
+constexpr uint32_t kUmItems = 8;                       // merged positions per thread
+constexpr uint32_t kUmTile = kUmThreads * kUmItems;    // merged positions per block
+
+// The directed graph whose lists are merged; W = 2E merged positions.
+struct UmGraph {
+  const int64_t* oo;
+  const int32_t* on;
+  const int64_t* io;
+  const int32_t* in;
+  uint32_t V;
+  uint64_t W;
+};
+
+// Where a block's positions start: the node holding the first one, and how
+// many of that node's out- (i) and in-elements (j) come before it.
+struct UmSplit {
+  uint32_t v, i, j, pad;
+};
+
+__device__ __forceinline__ uint64_t um_w(const UmGraph& g, uint32_t v) {
+  return (uint64_t)(__ldg(g.oo + v) + __ldg(g.io + v));
+}
+
+// The largest v in [lo, hi] with W(v) <= p (W(lo) <= p).
+__device__ __forceinline__ uint32_t um_node(const UmGraph& g, uint32_t lo, uint32_t hi, uint64_t p) {
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo + 1) / 2;
+    if (um_w(g, mid) <= p) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Merge path of sorted A[na], B[nb] with ties to A: how many of the first q
+// merged elements come from A.
+__device__ __forceinline__ uint32_t um_path(const int32_t* __restrict__ A, uint32_t na,
+                                            const int32_t* __restrict__ B, uint32_t nb, uint32_t q) {
+  uint32_t lo = q > nb ? q - nb : 0u, hi = q < na ? q : na;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(A + mid) <= __ldg(B + (q - 1 - mid))) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// part[c] for c in [0, nch]: the split at position min(c * kUmTile, W)
+__global__ void __launch_bounds__(256)
+    k_um_partition(UmGraph g, uint32_t nch, UmSplit* __restrict__ part) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c <= nch; c += gridDim.x * blockDim.x) {
+    const uint64_t p = (uint64_t)c * kUmTile < g.W ? (uint64_t)c * kUmTile : g.W;
+    UmSplit sp{um_node(g, 0, g.V, p), 0, 0, 0};
+    if (sp.v < g.V) {
+      const int64_t a0 = g.oo[sp.v], b0 = g.io[sp.v];
+      const uint32_t na = (uint32_t)(g.oo[sp.v + 1] - a0), nb = (uint32_t)(g.io[sp.v + 1] - b0);
+      const uint32_t q = (uint32_t)(p - (uint64_t)(a0 + b0));
+      sp.i = um_path(g.on + a0, na, g.in + b0, nb, q);
+      sp.j = q - sp.i;
+    }
+    part[c] = sp;
+  }
+}
+
+// Block c merges positions [c * kUmTile, min((c + 1) * kUmTile, W)), eight
+// consecutive ones per thread: the thread finds its node among the block's
+// nodes and its split inside that node, then merges on, into the next node
+// when one is used up.  An in-element equal to the last out-element taken in
+// the same node is a duplicate (ties go to the out-list first).
+//   WRITE = false: cnt[c] = the block's kept elements;
+//   WRITE = true: the kept elements to unbr from base[c] on, and uoff[v]
+//                 for every node whose first element the block holds.
+template <bool WRITE>
+__global__ void __launch_bounds__(kUmThreads)
+    k_um_merge(UmGraph g, const UmSplit* __restrict__ part, uint32_t* __restrict__ cnt,
+               const int64_t* __restrict__ base, int64_t* __restrict__ uoff,
+               int32_t* __restrict__ unbr) {
+  __shared__ int32_t s_out[WRITE ? kUmTile : 1];
+  __shared__ uint32_t s_sw[kUmThreads / 32 + 1];
+  const uint32_t c = blockIdx.x;
+  const uint64_t p0 = (uint64_t)c * kUmTile;
+  const uint64_t pend = p0 + kUmTile < g.W ? p0 + kUmTile : g.W;
+  const uint64_t pt = p0 + (uint64_t)threadIdx.x * kUmItems;
+  const uint32_t nitems =
+      pt >= pend ? 0u : (pend - pt < kUmItems ? (uint32_t)(pend - pt) : kUmItems);
+  int32_t x[kUmItems];
+  uint32_t vv[kUmItems];
+  uint32_t keep = 0, first = 0;
+  if (nitems) {
+    uint32_t v = um_node(g, part[c].v, part[c + 1].v, pt);
+    int64_t a0 = g.oo[v], b0 = g.io[v];
+    uint32_t na = (uint32_t)(g.oo[v + 1] - a0), nb = (uint32_t)(g.io[v + 1] - b0);
+    const uint32_t q = (uint32_t)(pt - (uint64_t)(a0 + b0));
+    uint32_t i = um_path(g.on + a0, na, g.in + b0, nb, q), j = q - i;
+    int32_t ca = i < na ? g.on[a0 + i] : INT32_MAX;    // next out-element
+    int32_t cb = j < nb ? g.in[b0 + j] : INT32_MAX;    // next in-element
+    int32_t la = i > 0 ? g.on[a0 + i - 1] : -1;        // last out-element taken
+#pragma unroll
+    for (uint32_t k = 0; k < kUmItems; ++k) {
+      if (k < nitems) {
+        while (i == na && j == nb) {  // this node is used up: on to the next with elements
+          ++v;
+          a0 = g.oo[v];
+          b0 = g.io[v];
+          na = (uint32_t)(g.oo[v + 1] - a0);
+          nb = (uint32_t)(g.io[v + 1] - b0);
+          i = j = 0;
+          ca = na ? g.on[a0] : INT32_MAX;
+          cb = nb ? g.in[b0] : INT32_MAX;
+          la = -1;
+        }
+        first |= (uint32_t)(i == 0 && j == 0) << k;
+        vv[k] = v;
+        if (i < na && (j == nb || ca <= cb)) {
+          x[k] = ca;
+          la = ca;
+          keep |= 1u << k;
+          ++i;
+          ca = i < na ? g.on[a0 + i] : INT32_MAX;
+        } else {
+          x[k] = cb;
+          if (cb != la) keep |= 1u << k;
+          ++j;
+          cb = j < nb ? g.in[b0 + j] : INT32_MAX;
+        }
+      }
+    }
+  }
+  uint32_t total;
+  const uint32_t off = block_exclusive_sum<kUmThreads>((uint32_t)__popc(keep), s_sw, total);
+  if constexpr (!WRITE) {
+    if (threadIdx.x == 0) cnt[c] = total;
+  } else {
+    const int64_t b = base[c];
+    uint32_t r = off;
+#pragma unroll
+    for (uint32_t k = 0; k < kUmItems; ++k) {
+      if ((keep >> k) & 1u) {
+        s_out[r] = x[k];
+        if ((first >> k) & 1u) uoff[vv[k]] = b + r;
+        ++r;
+      }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < total; t += kUmThreads) unbr[b + t] = s_out[t];
+    if (c == 0 && threadIdx.x == 0) uoff[g.V] = base[gridDim.x];
+  }
+}
+
 uint32_t grid_of(uint64_t work, uint32_t per_block, uint32_t cap) {
   uint64_t g = (work + per_block - 1) / per_block;
   if (g == 0) g = 1;
@@ -208,11 +361,74 @@ uint32_t grid_of(uint64_t work, uint32_t per_block, uint32_t cap) {
 
 }  // namespace
 
-int launch_double_table(const int32_t* src, const int32_t* dst, uint32_t n, int32_t* s2, int32_t* d2,
-                        cudaStream_t s) {
-  if (n == 0) return RINGO_OK;
-  k_double_table<<<grid_of(n, 256, 8192), 256, 0, s>>>(src, dst, n, s2, d2);
-  RINGO_LAUNCH_CHECK("k_double_table");
+int build_undirected(const int64_t* out_off, const int32_t* out_nbr, const int64_t* in_off,
+                     const int32_t* in_nbr, uint32_t V, uint64_t E, cudaStream_t s,
+                     int64_t** und_off, int32_t** und_nbr, uint64_t* M) {
+  *und_off = nullptr;
+  *und_nbr = nullptr;
+  *M = 0;
+  const UmGraph g{out_off, out_nbr, in_off, in_nbr, V, 2 * E};
+  const uint64_t nch64 = (g.W + kUmTile - 1) / kUmTile;
+  if (V == 0 || nch64 == 0) return RINGO_EINVAL;
+  if (nch64 >= 0x7FFFFFFFull) return RINGO_ERANGE;
+  const uint32_t nch = (uint32_t)nch64;
+  const uint32_t tiles = (nch + kScanTileNodes - 1) / kScanTileNodes;
+  // scratch: splits[nch + 1], block counts[nch], block starts[nch + 1], tile sums[tiles + 1]
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t bytes = al(sizeof(UmSplit) * ((size_t)nch + 1)) + al(4 * (size_t)nch) +
+                       al(8 * ((size_t)nch + 1)) + al(8 * ((size_t)tiles + 1));
+  char* buf = (char*)pool_alloc(bytes, s);
+  int64_t* uoff = (int64_t*)pool_alloc(8 * ((size_t)V + 1), s);
+  if (!buf || !uoff) {
+    pool_free(buf, s);
+    pool_free(uoff, s);
+    return RINGO_ENOMEM;
+  }
+  char* p = buf;
+  UmSplit* part = (UmSplit*)p;  p += al(sizeof(UmSplit) * ((size_t)nch + 1));
+  uint32_t* cnt = (uint32_t*)p; p += al(4 * (size_t)nch);
+  int64_t* base = (int64_t*)p;  p += al(8 * ((size_t)nch + 1));
+  uint64_t* tsum = (uint64_t*)p;
+  int rc = RINGO_OK;
+  uint64_t total = 0;
+  int32_t* unbr = nullptr;
+  cudaError_t e;
+  {
+    ProfScope ps("undirected_count", s);
+    k_um_partition<<<grid_of((uint64_t)nch + 1, 256, 152 * 32), 256, 0, s>>>(g, nch, part);
+    k_um_merge<false><<<nch, kUmThreads, 0, s>>>(g, part, cnt, nullptr, nullptr, nullptr);
+    k_tc_tile_sums<<<tiles, 256, 0, s>>>(cnt, nch, (uint64_t*)tsum);
+    k_scan_tile_sums<<<1, 1024, 0, s>>>(tsum, tiles);
+    k_tc_tile_scan<<<tiles, 256, 0, s>>>(cnt, nch, tsum, tiles, base);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&total, base + nch, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_error(std::string("undirected merge: ") + cudaGetErrorString(e));
+    rc = RINGO_ECUDA;
+  } else if (total > 0x7FFFFFFFFFull || !(unbr = (int32_t*)pool_alloc(4 * (size_t)total + 4, s))) {
+    rc = RINGO_ENOMEM;
+  } else {
+    {
+      ProfScope ps("undirected_write", s);
+      k_um_merge<true><<<nch, kUmThreads, 0, s>>>(g, part, nullptr, base, uoff, unbr);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_error(std::string("undirected merge: ") + cudaGetErrorString(e));
+      rc = RINGO_ECUDA;
+    }
+  }
+  pool_free(buf, s);
+  if (rc != RINGO_OK) {
+    pool_free(uoff, s);
+    pool_free(unbr, s);
+    return rc;
+  }
+  *und_off = uoff;
+  *und_nbr = unbr;
+  *M = total;
   return RINGO_OK;
 }
 
@@ -242,7 +458,7 @@ int run_triangles(const int64_t* off, const int32_t* nbr, uint32_t V, uint64_t E
     k_tc_degree<<<grid_of(V, 256, 8192), 256, 0, s>>>(off, V, deg);
     k_tc_count<<<warp_grid, 256, 0, s>>>(off, nbr, deg, V, cnt);
     k_tc_tile_sums<<<tiles, 256, 0, s>>>(cnt, V, tsum);
-    k_tc_scan_tiles<<<1, 32, 0, s>>>(tsum, tiles);
+    k_scan_tile_sums<<<1, 1024, 0, s>>>(tsum, tiles);
     k_tc_tile_scan<<<tiles, 256, 0, s>>>(cnt, V, tsum, tiles, offp);
     k_tc_fill<<<warp_grid, 256, 0, s>>>(off, nbr, deg, V, offp, nbrp);
   }

@@ -102,3 +102,49 @@ def pick_samples(src_h: np.ndarray, dst_h: np.ndarray, ids: np.ndarray, a: dict,
     absent = absent[~np.isin(absent, ids)].astype(np.int32)
     pick.append(absent)
     return np.unique(np.concatenate(pick).astype(np.int32))
+
+
+def check_undirected(u: dict, d: dict, chunk: int = 1 << 30) -> None:
+    """The undirected graph u of a table against the directed graph d of the
+    same table (whose own invariants check_properties establishes): the same
+    node list, both CSRs of u equal, and every node's list the sorted union of
+    its out- and in-lists in d.  Node ranges of at most `chunk` entries at a
+    time, so no torch operation sees more than 2^31 elements."""
+    V = d["num_nodes"]
+    assert u["num_nodes"] == V and torch.equal(u["node_ids"], d["node_ids"])
+    assert torch.equal(u["out_off"], u["in_off"]) and torch.equal(u["out_nbr"], u["in_nbr"])
+    uo, oo, io = u["out_off"], d["out_off"], d["in_off"]
+    assert uo.numel() == V + 1 and int(uo[0]) == 0 and int(uo[-1]) == u["num_edges"]
+    w = oo + io  # merged positions before each node
+    v0 = 0
+    while v0 < V:
+        v1 = int(torch.searchsorted(w, w[v0] + chunk, right=True)) - 1
+        v1 = min(max(v1, v0 + 1), V)
+        nodes = torch.arange(v1 - v0, device=uo.device)
+
+        def keys(off, nbr):
+            deg = off[v0 + 1:v1 + 1] - off[v0:v1]
+            own = torch.repeat_interleave(nodes, deg, output_size=int(deg.sum()))
+            return own * V + nbr[int(off[v0]):int(off[v1])].long()
+
+        want = torch.unique(torch.cat([keys(oo, d["out_nbr"]), keys(io, d["in_nbr"])]))
+        got = keys(uo, u["out_nbr"])
+        assert torch.equal(got, want), f"lists of nodes {v0}..{v1 - 1} differ"
+        del want, got
+        v0 = v1
+
+
+def check_undirected_samples(a: dict, src_h: np.ndarray, dst_h: np.ndarray,
+                             sample_ids: np.ndarray) -> None:
+    """The lists of sampled node IDs against the oracle's one-pass scan: the
+    neighbours of x are the union of its out- and in-neighbours."""
+    outs, ins, present = oracle.sample_lists(src_h, dst_h, sample_ids)
+    ids = a["node_ids"].cpu().numpy()
+    off, nbr = a["out_off"].cpu().numpy(), a["out_nbr"]
+    for k, x in enumerate(sample_ids):
+        r = int(np.searchsorted(ids, x))
+        found = r < ids.size and ids[r] == x
+        assert found == bool(present[k]), f"node {x}: presence differs"
+        if found:
+            got = ids[nbr[off[r]:off[r + 1]].cpu().numpy()]
+            assert np.array_equal(got, np.union1d(outs[k], ins[k])), f"list of node {x} differs"

@@ -59,8 +59,9 @@ def test_undirected_row_limit_checked_before_any_device_work():
     lib = ringo.load()
     fake = ctypes.c_void_p(4096)  # never dereferenced: the size check comes first
     h = ctypes.c_void_p()
-    rc = lib.ringo_table_to_undirected_graph(fake, fake, 1 << 30, None, ctypes.byref(h))
+    rc = lib.ringo_table_to_undirected_graph(fake, fake, 1 << 31, None, ctypes.byref(h))
     assert rc == ringo.RINGO_ERANGE and not h.value
+    assert b"nrows" in lib.ringo_last_error()
 
 
 def test_failure_injection_hooks_argument_handling():

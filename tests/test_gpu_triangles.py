@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 import torch
 
+import gpu_checks
 import oracle
 import pins
 from paper_1503_07881_gb300 import ringo, tablegen as tg
@@ -97,3 +98,48 @@ def test_lj_full_size_invariance():
     g2 = ringo.ringo_table_to_undirected_graph(s2, d2)
     assert g2.count_triangles() == t1
     g2.free()
+
+
+def test_reciprocal_edges_and_hub_splits():
+    """Mutual edges (the same pair in both directions, and repeated) are one
+    undirected edge; hubs whose lists span many merge blocks are split inside
+    the node, at ties between the two lists too."""
+    rng = np.random.default_rng(21)
+    a = rng.integers(-50_000, 50_000, 300_000).astype(np.int32)
+    b = rng.integers(-50_000, 50_000, 300_000).astype(np.int32)
+    half = rng.random(300_000) < 0.5
+    src = np.concatenate([a, b[half], a[:1000]])
+    dst = np.concatenate([b, a[half], b[:1000]])
+    check(src, dst, "reciprocal")
+    leaves = np.arange(0, 120_000, dtype=np.int32) * 3 + 1
+    hub_out = np.full(leaves.size, -5, np.int32)
+    evens = leaves[::2]
+    src = np.concatenate([hub_out, evens, np.full(7_000, 2, np.int32), evens[:7_000]])
+    dst = np.concatenate([leaves, np.full(evens.size, -5, np.int32), evens[:7_000],
+                          np.full(7_000, 2, np.int32)])
+    check(src, dst, "hubs")
+
+
+@pytest.mark.slow
+def test_twitter_full_size_undirected():
+    """The Twitter-shaped table (1.47B rows, above 2^30) in undirected form,
+    checked at full size: the directed graph's invariants, every undirected
+    list the union of the node's out- and in-lists, oracle lists of sampled
+    nodes, and a positive triangle count that a second run repeats."""
+    src, dst = tg.make_table("twitter", seed=1, device="cuda")
+    gd = ringo.ringo_table_to_graph(src, dst)
+    d = gpu_checks.graph_arrays(gd)
+    gpu_checks.check_properties(d, src, dst)
+    g = ringo.ringo_table_to_undirected_graph(src, dst)
+    u = gpu_checks.graph_arrays(g)
+    gpu_checks.check_undirected(u, d)
+    del d
+    gd.free()
+    src_h, dst_h = src.cpu().numpy(), dst.cpu().numpy()
+    ids = u["node_ids"].cpu().numpy()
+    sample = gpu_checks.pick_samples(src_h, dst_h, ids, u, n_random=60)
+    gpu_checks.check_undirected_samples(u, src_h, dst_h, sample)
+    del u, src_h, dst_h
+    tri = g.count_triangles()
+    assert tri > 0 and g.count_triangles() == tri
+    g.free()
