@@ -50,24 +50,6 @@ __device__ __forceinline__ bool oriented(const int32_t* __restrict__ deg, int32_
   return dv > du || (dv == du && v > u);
 }
 
-// cnt[u] = oriented out-degree; one warp per node
-__global__ void __launch_bounds__(256)
-    k_tc_count(const int64_t* __restrict__ off, const int32_t* __restrict__ nbr,
-               const int32_t* __restrict__ deg, uint32_t V, uint32_t* __restrict__ cnt) {
-  const int lane = threadIdx.x & 31;
-  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t u = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < V;
-       u += warps) {
-    const int64_t a = off[u], b = off[u + 1];
-    const int32_t du = deg[u];
-    uint32_t c = 0;
-    for (int64_t e = a + lane; e < b; e += 32) c += oriented(deg, du, (uint32_t)u, (uint32_t)nbr[e]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-    if (lane == 0) cnt[u] = c;
-  }
-}
-
 // exclusive scan of cnt into off+, in three steps: tile sums, one block over
 // the tile sums, each tile scanned from its offset
 __global__ void __launch_bounds__(256)
@@ -129,10 +111,11 @@ __global__ void __launch_bounds__(256)
   if (blockIdx.x == tiles - 1 && threadIdx.x == 0) offp[V] = (int64_t)tsum[tiles];
 }
 
-// oriented lists, in the order of the undirected lists (ascending index)
+// oriented lists, each in its node's own slot of the undirected lists (from
+// off[u]; ascending index) with its length in cnt[u]: one pass, no scan
 __global__ void __launch_bounds__(256)
     k_tc_fill(const int64_t* __restrict__ off, const int32_t* __restrict__ nbr,
-              const int32_t* __restrict__ deg, uint32_t V, const int64_t* __restrict__ offp,
+              const int32_t* __restrict__ deg, uint32_t V, uint32_t* __restrict__ cnt,
               int32_t* __restrict__ nbrp) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = lanemask_lt();
@@ -141,7 +124,7 @@ __global__ void __launch_bounds__(256)
        u += warps) {
     const int64_t a = off[u], b = off[u + 1];
     const int32_t du = deg[u];
-    int64_t w = offp[u];
+    int64_t w = a;
     for (int64_t e0 = a; e0 < b; e0 += 32) {
       const int64_t e = e0 + lane;
       const uint32_t v = e < b ? (uint32_t)nbr[e] : 0u;
@@ -150,6 +133,7 @@ __global__ void __launch_bounds__(256)
       if (keep) nbrp[w + __popc(m & lt)] = (int32_t)v;
       w += __popc(m);
     }
+    if (lane == 0) cnt[u] = (uint32_t)(w - a);
   }
 }
 
@@ -178,6 +162,23 @@ __device__ __forceinline__ uint32_t intersect(const int32_t* __restrict__ a, uin
     if (lo0 >= nb) break;
   }
   return c;
+}
+
+// the oriented lists packed in node order: N+(u) moves from its slot
+// nbrs[off[u], off[u] + cnt[u]) to nbrp[offp[u], offp[u + 1]) (offp: the
+// exclusive scan of cnt), so the lists the intersections read lie together
+__global__ void __launch_bounds__(256)
+    k_tc_pack(const int64_t* __restrict__ off, const uint32_t* __restrict__ cnt,
+              const int32_t* __restrict__ nbrs, const int64_t* __restrict__ offp, uint32_t V,
+              int32_t* __restrict__ nbrp) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t u = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < V;
+       u += warps) {
+    const int64_t a = off[u], w = offp[u];
+    const uint32_t n = cnt[u];
+    for (uint32_t k = lane; k < n; k += 32) nbrp[w + k] = nbrs[a + k];
+  }
 }
 
 // one warp per node u; lanes over v in N+(u)
@@ -437,10 +438,13 @@ int run_triangles(const int64_t* off, const int32_t* nbr, uint32_t V, uint64_t E
   *count = 0;
   if (V == 0 || E == 0) return RINGO_OK;
   const uint32_t tiles = (V + kScanTileNodes - 1) / kScanTileNodes;
-  // scratch: deg[V], cnt[V], off+[V+1], tile sums[tiles+1], total, nbr+[<= E]
+  // scratch: deg[V], cnt[V], off+[V+1], tile sums[tiles+1], total, the
+  // oriented lists in the undirected lists' slots (E entries), then packed
+  // (at most E / 2 + V entries: every non-loop edge is kept at one end)
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  const size_t bytes = al(4 * (size_t)V) * 2 + al(8 * ((size_t)V + 1)) + al(8 * ((size_t)tiles + 1)) +
-                       al(8) + al(4 * (size_t)E);
+  const size_t packed = E / 2 + V;
+  const size_t bytes = al(4 * (size_t)V) * 2 + al(8 * ((size_t)V + 1)) +
+                       al(8 * ((size_t)tiles + 1)) + al(8) + al(4 * (size_t)E) + al(4 * packed);
   char* buf = (char*)pool_alloc(bytes, s);
   if (!buf) return RINGO_ENOMEM;
   char* p = buf;
@@ -449,6 +453,7 @@ int run_triangles(const int64_t* off, const int32_t* nbr, uint32_t V, uint64_t E
   int64_t* offp = (int64_t*)p;      p += al(8 * ((size_t)V + 1));
   uint64_t* tsum = (uint64_t*)p;    p += al(8 * ((size_t)tiles + 1));
   unsigned long long* total = (unsigned long long*)p;  p += al(8);
+  int32_t* nbrs = (int32_t*)p;      p += al(4 * (size_t)E);
   int32_t* nbrp = (int32_t*)p;
   const uint32_t warp_grid = grid_of(V, 8, 152 * 64);
   int rc = RINGO_OK;
@@ -456,11 +461,11 @@ int run_triangles(const int64_t* off, const int32_t* nbr, uint32_t V, uint64_t E
   {
     ProfScope ps("triangles_orient", s);
     k_tc_degree<<<grid_of(V, 256, 8192), 256, 0, s>>>(off, V, deg);
-    k_tc_count<<<warp_grid, 256, 0, s>>>(off, nbr, deg, V, cnt);
+    k_tc_fill<<<warp_grid, 256, 0, s>>>(off, nbr, deg, V, cnt, nbrs);
     k_tc_tile_sums<<<tiles, 256, 0, s>>>(cnt, V, tsum);
     k_scan_tile_sums<<<1, 1024, 0, s>>>(tsum, tiles);
     k_tc_tile_scan<<<tiles, 256, 0, s>>>(cnt, V, tsum, tiles, offp);
-    k_tc_fill<<<warp_grid, 256, 0, s>>>(off, nbr, deg, V, offp, nbrp);
+    k_tc_pack<<<warp_grid, 256, 0, s>>>(off, cnt, nbrs, offp, V, nbrp);
   }
   {
     ProfScope ps("triangles_count", s);
