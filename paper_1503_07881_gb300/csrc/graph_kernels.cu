@@ -331,10 +331,36 @@ void launch_dst_runs(const Launch& L, uint32_t* counter, cudaStream_t s) {
   if (L.row_slots) k_dst_runs<<<L.row_slots, 256, 0, s>>>(L.ctls, L.rows, counter);
 }
 
-// in_off[r] holds, after the merge, the index j of node r's first
-// destination run (the merge cursor); the run starts are known once the
-// in-sort is done: in_off[r] = udst_start[j].  Persistent over the merge
-// tiles of every segment (each covers kMergeTile nodes).
+// in_off from the destination runs, after the in-sort: run j (first in-edge
+// udst_start[j], node dst_rank[j]) gives in_off = udst_start[j] to its node
+// and to every node between the previous run's node and it (nodes that are
+// not destinations have empty in-lists); after the last run in_off = E up to
+// node V.  Persistent over the merge tiles of every segment, kMergeTile runs
+// a tile (a segment's tiles cover Vs + Vd >= Vd items).  A node range of
+// kFillInline nodes or more is recorded (first node, last node, value) in
+// usrc_start, which phase 3 does not use, and filled by k_fill_ranges, so
+// that no thread writes a long range alone.
+constexpr uint32_t kFillInline = 32;
+
+__device__ __forceinline__ void fill_nodes(Ctl* __restrict__ ctl, int64_t* __restrict__ in_off,
+                                           uint32_t a, uint32_t b, uint32_t v) {
+  if (b - a < kFillInline) {
+    for (uint32_t r = a; r <= b; ++r) in_off[r] = (int64_t)v;
+    return;
+  }
+  // three words a range; a range holds at least kFillInline of the at most
+  // 2 * n_rows nodes, so n_rows + 1 words always suffice
+  const uint32_t i = atomicAdd(&ctl->n_fill, 1u);
+  uint32_t* rec = reinterpret_cast<uint32_t*>(ctl->usrc_start);
+  if (3ull * i + 2 < (uint64_t)ctl->n_rows + 1) {
+    rec[3 * i] = a;
+    rec[3 * i + 1] = b;
+    rec[3 * i + 2] = v;
+  } else {
+    atomicOr(&ctl->err, kErrRemap);
+  }
+}
+
 __global__ void __launch_bounds__(256)
     k_fill_in_off(Ctl* __restrict__ ctls, SegMap m, uint32_t* counter) {
   __shared__ Claim s_cl;
@@ -343,17 +369,39 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     if (!s_cl.valid) return;
     Ctl* __restrict__ ctl = ctls + s_cl.seg;
-    const uint32_t V = ctl->V, Vd = ctl->Vd;
-    const uint32_t r0 = s_cl.tile * (uint32_t)kMergeTile;
-    const uint32_t r1 = min(V, r0 + (uint32_t)kMergeTile);
+    const uint32_t V = ctl->V, Vd = ctl->Vd, E = ctl->E;
+    const uint32_t j0 = s_cl.tile * (uint32_t)kMergeTile;
+    const uint32_t j1 = min(Vd, j0 + (uint32_t)kMergeTile);
     int64_t* __restrict__ in_off = ctl->in_off;
     const int32_t* __restrict__ ustart = ctl->udst_start;
-    for (uint32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-      const uint32_t j = (uint32_t)in_off[r];
-      if (j <= Vd) in_off[r] = ustart[j];
-      else atomicOr(&ctl->err, kErrRemap);
+    const int32_t* __restrict__ drank = ctl->dst_rank;
+    for (uint32_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+      const uint32_t r1 = (uint32_t)drank[j];
+      const uint32_t r0 = j ? (uint32_t)drank[j - 1] + 1 : 0u;
+      if (r1 >= V || r0 > r1) {  // the run nodes ascend below V (never expected otherwise)
+        atomicOr(&ctl->err, kErrRemap);
+        continue;
+      }
+      fill_nodes(ctl, in_off, r0, r1, (uint32_t)ustart[j]);
+      if (j == Vd - 1 && r1 + 1 < V) fill_nodes(ctl, in_off, r1 + 1, V - 1, E);
     }
     __syncthreads();
+  }
+}
+
+// The node ranges k_fill_in_off recorded (long runs of nodes that are not
+// destinations; rare), one warp per range.  One block per segment.
+__global__ void __launch_bounds__(256) k_fill_ranges(Ctl* __restrict__ ctls) {
+  Ctl* __restrict__ ctl = ctls + blockIdx.x;
+  const uint32_t cap = (uint32_t)(((uint64_t)ctl->n_rows + 1) / 3);
+  const uint32_t n = min(ctl->n_fill, cap);
+  const uint32_t* __restrict__ rec = reinterpret_cast<const uint32_t*>(ctl->usrc_start);
+  int64_t* __restrict__ in_off = ctl->in_off;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+  for (uint32_t i = warp; i < n; i += warps) {
+    const uint32_t a = rec[3 * i], b = rec[3 * i + 1];
+    const int64_t v = (int64_t)rec[3 * i + 2];
+    for (uint64_t r = (uint64_t)a + lane; r <= b; r += 32) in_off[r] = v;
   }
 }
 
@@ -361,11 +409,9 @@ __global__ void __launch_bounds__(256)
 // node_ids = usrc U udst (both ascending).  Merge path over the two lists,
 // with a src item placed before an equal dst item; a dst item equal to the
 // src item before it is the same node and is dropped.  For every node the
-// merge cursor (i, j) (src items and dst items consumed before it) gives
-//   out_off[r] = usrc_start[i]   and   in_off[r] = udst_start[j],
-// which holds for nodes in both lists and for nodes in only one of them.
-// The merge runs before the in-sort, when udst_start is not known yet, so it
-// stores j in in_off[r] and k_fill_in_off replaces it afterwards.
+// merge cursor i (src items consumed before it) gives out_off[r] =
+// usrc_start[i], which holds for nodes in both lists and for nodes in only
+// one of them.  in_off is written after the in-sort, by k_dst_runs.
 // Also src_rank[i] and dst_rank[j]: the node index of each list entry.
 __device__ __forceinline__ uint32_t merge_path(const int32_t* a, uint32_t na, const int32_t* b,
                                                uint32_t nb, uint32_t diag) {
@@ -475,7 +521,6 @@ __device__ __forceinline__ void merge_tile(Ctl* __restrict__ ctl, uint32_t tile,
         const uint32_t V = unpackB(excl) + total;
         ctl->V = V;
         ctl->out_off[V] = (int64_t)ctl->E;
-        ctl->in_off[V] = (int64_t)Vd;  // destination-run index; E after the in-sort
       }
     }
   }
@@ -500,13 +545,11 @@ __device__ __forceinline__ void merge_tile(Ctl* __restrict__ ctl, uint32_t tile,
   const uint32_t r0 = unpackB(S.prefix);
   int32_t* __restrict__ node_ids = ctl->node_ids;
   int64_t* __restrict__ out_off = ctl->out_off;
-  int64_t* __restrict__ in_off = ctl->in_off;
   for (uint32_t t = tid; t < total; t += kScanThreads) {
     const uint32_t p = S.node[t];
     const uint32_t i = p & 0xFFFu, j = (p >> 12) & 0xFFFu;
     node_ids[r0 + t] = (p >> 24) ? sa[i] : sb[j];
     out_off[r0 + t] = S.start[i];
-    in_off[r0 + t] = (int64_t)(j0 + j);  // destination-run cursor, see k_fill_in_off
   }
   int32_t* __restrict__ src_rank = ctl->src_rank;
   int32_t* __restrict__ dst_rank = ctl->dst_rank;
@@ -815,6 +858,7 @@ __global__ void __launch_bounds__(256)
 
 void launch_fill_in_off(const Launch& L, uint32_t* counter, cudaStream_t s) {
   k_fill_in_off<<<persistent_grid(8), 256, 0, s>>>(L.ctls, L.merge, counter);
+  if (L.nseg) k_fill_ranges<<<L.nseg, 256, 0, s>>>(L.ctls);
 }
 
 void launch_remap(const Launch& L, uint32_t* counter, cudaStream_t s) {

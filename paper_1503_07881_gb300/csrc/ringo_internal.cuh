@@ -8,8 +8,8 @@
 // the order is kept) and emits the distinct destination IDs.  The four src
 // passes follow.  Adjacent duplicates are dropped while source runs are
 // counted; the surviving edges, re-keyed as (dst-run, source-run), are stably
-// sorted on the dst-run half; destination-run starts are recorded; the two
-// sorted ID lists are merged into the node list; finally both neighbour
+// sorted on the dst-run half; the two sorted ID lists are merged into the
+// node list; destination-run starts give the in-offsets; finally both neighbour
 // arrays go from run indices to node indices through monotone maps, almost
 // always answered by a small block table that stays in L2.  Sizes that only
 // the device knows (E, V, which radix passes are trivial) live in the device
@@ -134,7 +134,7 @@ struct alignas(16) Ctl {
   uint64_t* scan_chunk_inc[3];  // [chunks] inclusive prefix, flagged
   uint32_t* scan_chunk_cnt[3];  // [chunks] tiles that have added their sum
   int32_t* usrc;              // [n_rows + 1] distinct src IDs, ascending
-  int32_t* usrc_start;        // [n_rows + 1] first out-edge of each source run
+  int32_t* usrc_start;        // [n_rows + 1] first out-edge of each source run (phase 3: n_fill records)
   int32_t* udst;              // [n_rows + 1] distinct dst IDs, ascending
   int32_t* udst_start;        // [n_rows + 1] first in-edge of each destination run
   PassDesc rank_step;         // dst -> dst-run index, between out-sort passes 3 and 4
@@ -149,6 +149,7 @@ struct alignas(16) Ctl {
   // new difference.  Filled (unordered) by k_rank_blocks while there are at
   // most kMaxSteps, then sorted by k_sort_steps; n_steps counts them all, so
   // a larger count means the list is not used.
+  uint32_t n_fill;            // long node ranges of in_off recorded in usrc_start (phase 3)
   uint32_t n_steps;
   uint32_t step_j[kMaxSteps];
   uint32_t step_off[kMaxSteps];
@@ -348,7 +349,7 @@ size_t topk_scratch_bytes(uint32_t V, uint32_t k);
 //   phase 2: node merge, block tables, out-direction remap; needs node
 //            arrays and rank maps set in every control block (sized from Vs,
 //            Vd or from upper bounds).  Afterwards V, node_ids, out_off and
-//            out_nbr are final (in_off holds destination-run indices).
+//            out_nbr are final.
 //   phase 3: in-sort, destination runs with the in-direction remap, in_off.
 int enqueue_phase1(const Launch& L, cudaStream_t s);
 int enqueue_phase2(const Launch& L, cudaStream_t s);

@@ -228,3 +228,31 @@ def test_out_remap_step_list_threshold(src_only):
     assert inf["num_nodes"] - inf["num_dst_nodes"] == src_only
     pins.assert_same_graph(g.copy_to_host(), want, f"{src_only} source-only nodes")
     g.free()
+
+
+@pytest.mark.parametrize("gap", [0, 1, 30, 31, 32, 33, 5000])
+def test_in_offsets_across_nodes_without_in_edges(gap):
+    """Nodes that are only sources have empty in-lists, so their in-offset is
+    the next destination's: runs of `gap` such nodes before the first
+    destination, between destinations and after the last, across the length
+    where the destination-run kernel stops writing a run itself and records
+    it for the range fill, against the oracle."""
+    rng = np.random.default_rng(300 + gap)
+    ndst = 40
+    ids = (np.arange((ndst + 1) * (gap + 1), dtype=np.int64) * 7 - 900).astype(np.int32)
+    is_dst = np.zeros(ids.size, bool)
+    is_dst[gap::gap + 1][:ndst] = True
+    dsts, only_src = ids[is_dst], ids[~is_dst]
+    # every source-only node points at some destination; every destination
+    # has an in-edge (from the next destination, so that destinations are
+    # sources too for half of them)
+    src = [only_src, dsts]
+    dst = [rng.choice(dsts, only_src.size) if only_src.size else only_src, np.roll(dsts, 1)]
+    src = np.concatenate(src).astype(np.int32)
+    dst = np.concatenate(dst).astype(np.int32)
+    p = rng.permutation(src.size)
+    src, dst = src[p], dst[p]
+    g = ringo.ringo_table_to_graph(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda())
+    got = g.copy_to_host()
+    g.free()
+    pins.assert_same_graph(got, oracle.table_to_graph(src, dst), f"gap {gap}")
