@@ -18,9 +18,9 @@
 // Triangles: edges are oriented from the endpoint of smaller (degree, index)
 // to the larger, which keeps every oriented list below sqrt(2E) entries; a
 // triangle {a, b, c} with a < b < c in that order is counted exactly once, as
-// c in both N+(a) and N+(b).  For each oriented edge (u, v) the shorter of
-// N+(u), N+(v) is searched, element by element, in the longer (both sorted
-// by node index).
+// c in both N+(a) and N+(b).  For each oriented edge (u, v), N+(u) and N+(v)
+// (both sorted by node index) are merged when their lengths are close, else
+// the shorter is searched, element by element, in the longer.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -137,7 +137,12 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// |A ∩ B| for sorted lists: each element of the shorter searched in the longer
+// |A ∩ B| for sorted lists.  Lists of similar length (the longer at most
+// kTcMergeRatio times the shorter) are merged: one pass over both, in order,
+// consecutive loads that mostly hit L1.  A list much shorter than the other
+// has each of its elements searched in the longer one (a search per element,
+// resumed from the last position).
+constexpr uint64_t kTcMergeRatio = 4;
 __device__ __forceinline__ uint32_t intersect(const int32_t* __restrict__ a, uint32_t na,
                                               const int32_t* __restrict__ b, uint32_t nb) {
   if (na > nb) {
@@ -148,7 +153,28 @@ __device__ __forceinline__ uint32_t intersect(const int32_t* __restrict__ a, uin
     na = nb;
     nb = tn;
   }
-  uint32_t c = 0, lo0 = 0;
+  if (na == 0) return 0;
+  uint32_t c = 0;
+  if ((uint64_t)nb <= (uint64_t)na * kTcMergeRatio) {
+    uint32_t i = 0, j = 0;
+    int32_t x = a[0], y = b[0];
+    while (true) {
+      if (x < y) {
+        if (++i == na) break;
+        x = a[i];
+      } else if (x > y) {
+        if (++j == nb) break;
+        y = b[j];
+      } else {
+        ++c;
+        if (++i == na || ++j == nb) break;
+        x = a[i];
+        y = b[j];
+      }
+    }
+    return c;
+  }
+  uint32_t lo0 = 0;
   for (uint32_t i = 0; i < na; ++i) {
     const int32_t x = a[i];
     uint32_t lo = lo0, hi = nb;  // the elements of a ascend: search from the last position
