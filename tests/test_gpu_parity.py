@@ -207,7 +207,7 @@ def test_twitter_full_size_sampled():
     assert 1.4e9 < e < 1.47e9 and 3.5e7 < v <= 4.17e7
 
 
-@pytest.mark.parametrize("src_only", [0, 1, 255, 256, 257, 2000])
+@pytest.mark.parametrize("src_only", [0, 1, 31, 32, 33, 255, 256, 257, 2000])
 def test_out_remap_step_list_threshold(src_only):
     """The out-direction remap uses a short list of the map's steps when at
     most 256 nodes are not destinations, else block tables: both paths, and
