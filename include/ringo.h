@@ -277,7 +277,7 @@ RINGO_API int ringo_table_to_undirected_graph(const int32_t* src, const int32_t*
  * ringo_graph_count_triangles -- the number of triangles (three distinct
  * nodes, each pair joined) of the undirected graph held in g's out-CSR, which
  * must be symmetric (as built by ringo_table_to_undirected_graph); self-loops
- * are ignored.  Exact (64-bit integer).  Scratch of about 20 V + 6 E bytes
+ * are ignored.  Exact (64-bit integer).  Scratch of about 22 V + 6 E bytes
  * from the library's pool (E = num_edges, the adjacency entries); blocks
  * until *count is on the host.
  * Errors: EINVAL (NULL g or count), ENOMEM, ECUDA.

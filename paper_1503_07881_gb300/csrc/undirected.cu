@@ -37,15 +37,28 @@ namespace {
 
 constexpr uint32_t kScanTileNodes = 2048;  // nodes per block of the offset scan
 
-__global__ void k_tc_degree(const int64_t* __restrict__ off, uint32_t V, int32_t* __restrict__ deg) {
-  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
-    deg[v] = (int32_t)(off[v + 1] - off[v]);
+// deg[v], and deg16[v] = min(deg[v], 65535): the order of (degree, index)
+// is decided by the 16-bit copy (half the bytes, so the gathers of it stay in
+// L2) except between two nodes of degree 65535 or more
+constexpr uint32_t kDeg16Max = 0xFFFFu;
+
+__global__ void k_tc_degree(const int64_t* __restrict__ off, uint32_t V, int32_t* __restrict__ deg,
+                            uint16_t* __restrict__ deg16) {
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+    const int64_t d = off[v + 1] - off[v];
+    deg[v] = (int32_t)d;
+    deg16[v] = (uint16_t)(d < (int64_t)kDeg16Max ? d : (int64_t)kDeg16Max);
+  }
 }
 
 // u -> v when (deg u, u) < (deg v, v); self-loops dropped
-__device__ __forceinline__ bool oriented(const int32_t* __restrict__ deg, int32_t du, uint32_t u,
-                                         uint32_t v) {
+__device__ __forceinline__ bool oriented(const int32_t* __restrict__ deg,
+                                         const uint16_t* __restrict__ deg16, int32_t du,
+                                         uint32_t du16, uint32_t u, uint32_t v) {
   if (v == u) return false;
+  const uint32_t dv16 = __ldg(deg16 + v);
+  if (dv16 != du16) return dv16 > du16;
+  if (du16 < kDeg16Max) return v > u;  // the same degree
   const int32_t dv = __ldg(deg + v);
   return dv > du || (dv == du && v > u);
 }
@@ -115,8 +128,8 @@ __global__ void __launch_bounds__(256)
 // off[u]; ascending index) with its length in cnt[u]: one pass, no scan
 __global__ void __launch_bounds__(256)
     k_tc_fill(const int64_t* __restrict__ off, const int32_t* __restrict__ nbr,
-              const int32_t* __restrict__ deg, uint32_t V, uint32_t* __restrict__ cnt,
-              int32_t* __restrict__ nbrp) {
+              const int32_t* __restrict__ deg, const uint16_t* __restrict__ deg16, uint32_t V,
+              uint32_t* __restrict__ cnt, int32_t* __restrict__ nbrp) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = lanemask_lt();
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
@@ -124,11 +137,12 @@ __global__ void __launch_bounds__(256)
        u += warps) {
     const int64_t a = off[u], b = off[u + 1];
     const int32_t du = deg[u];
+    const uint32_t du16 = deg16[u];
     int64_t w = a;
     for (int64_t e0 = a; e0 < b; e0 += 32) {
       const int64_t e = e0 + lane;
       const uint32_t v = e < b ? (uint32_t)nbr[e] : 0u;
-      const bool keep = e < b && oriented(deg, du, (uint32_t)u, v);
+      const bool keep = e < b && oriented(deg, deg16, du, du16, (uint32_t)u, v);
       const uint32_t m = __ballot_sync(0xFFFFFFFFu, keep);
       if (keep) nbrp[w + __popc(m & lt)] = (int32_t)v;
       w += __popc(m);
@@ -464,18 +478,19 @@ int run_triangles(const int64_t* off, const int32_t* nbr, uint32_t V, uint64_t E
   *count = 0;
   if (V == 0 || E == 0) return RINGO_OK;
   const uint32_t tiles = (V + kScanTileNodes - 1) / kScanTileNodes;
-  // scratch: deg[V], cnt[V], off+[V+1], tile sums[tiles+1], total, the
-  // oriented lists in the undirected lists' slots (E entries), then packed
-  // (at most E / 2 + V entries: every non-loop edge is kept at one end)
+  // scratch: deg[V], cnt[V], deg16[V], off+[V+1], tile sums[tiles+1], total,
+  // the oriented lists in the undirected lists' slots (E entries), then
+  // packed (at most E / 2 + V entries: every non-loop edge is kept at one end)
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t packed = E / 2 + V;
-  const size_t bytes = al(4 * (size_t)V) * 2 + al(8 * ((size_t)V + 1)) +
+  const size_t bytes = al(4 * (size_t)V) * 2 + al(2 * (size_t)V) + al(8 * ((size_t)V + 1)) +
                        al(8 * ((size_t)tiles + 1)) + al(8) + al(4 * (size_t)E) + al(4 * packed);
   char* buf = (char*)pool_alloc(bytes, s);
   if (!buf) return RINGO_ENOMEM;
   char* p = buf;
   int32_t* deg = (int32_t*)p;       p += al(4 * (size_t)V);
   uint32_t* cnt = (uint32_t*)p;     p += al(4 * (size_t)V);
+  uint16_t* deg16 = (uint16_t*)p;   p += al(2 * (size_t)V);
   int64_t* offp = (int64_t*)p;      p += al(8 * ((size_t)V + 1));
   uint64_t* tsum = (uint64_t*)p;    p += al(8 * ((size_t)tiles + 1));
   unsigned long long* total = (unsigned long long*)p;  p += al(8);
@@ -486,8 +501,8 @@ int run_triangles(const int64_t* off, const int32_t* nbr, uint32_t V, uint64_t E
   cudaError_t e = cudaMemsetAsync(total, 0, 8, s);
   {
     ProfScope ps("triangles_orient", s);
-    k_tc_degree<<<grid_of(V, 256, 8192), 256, 0, s>>>(off, V, deg);
-    k_tc_fill<<<warp_grid, 256, 0, s>>>(off, nbr, deg, V, cnt, nbrs);
+    k_tc_degree<<<grid_of(V, 256, 8192), 256, 0, s>>>(off, V, deg, deg16);
+    k_tc_fill<<<warp_grid, 256, 0, s>>>(off, nbr, deg, deg16, V, cnt, nbrs);
     k_tc_tile_sums<<<tiles, 256, 0, s>>>(cnt, V, tsum);
     k_scan_tile_sums<<<1, 1024, 0, s>>>(tsum, tiles);
     k_tc_tile_scan<<<tiles, 256, 0, s>>>(cnt, V, tsum, tiles, offp);
