@@ -101,3 +101,29 @@ def test_tune_cache_rejects_a_file_that_is_not_a_cache(tmp_path):
     bad.write_text('{"something": 1}')
     assert lib.ringo_tune_set_cache(str(bad).encode()) == ringo.RINGO_EINVAL
     assert lib.ringo_tune_set_cache(None) == ringo.RINGO_OK
+
+
+def test_tune_cache_keeps_pass_options_and_repairs_bad_ones(tmp_path):
+    """A cache file's entries survive being read and written back: the rank
+    method, prefetch distance and in-direction digit width of each; values
+    out of range come back as the defaults.  No device is touched."""
+    import json
+    lib = ringo.load()
+    path = tmp_path / "tune.json"
+    path.write_text(json.dumps({"version": 1, "entries": [
+        {"gpu": 'GPU "A"', "kind": 0, "size_class": 30, "rank_method": 2, "prefetch_waves": 0,
+         "in_digit_bits": 9, "wave_rows": 0, "ms": 1.5, "out_passes": 8, "in_passes": 3},
+        {"gpu": "GPU B", "kind": 1, "size_class": 20, "rank_method": 7, "prefetch_waves": 5,
+         "in_digit_bits": 11, "wave_rows": 4096, "ms": 2.0, "out_passes": 8, "in_passes": 4}]}))
+    try:
+        assert lib.ringo_tune_set_cache(str(path).encode()) == ringo.RINGO_OK
+        entries = {(e["gpu"], e["kind"], e["size_class"]): e
+                   for e in json.loads(path.read_text())["entries"]}
+        a = entries[('GPU "A"', 0, 30)]
+        assert (a["rank_method"], a["prefetch_waves"], a["in_digit_bits"]) == (2, 0, 9)
+        assert a["in_passes"] == 3
+        b = entries[("GPU B", 1, 20)]
+        assert (b["rank_method"], b["prefetch_waves"], b["in_digit_bits"]) == (0, 1, 8)
+        assert b["wave_rows"] == 4096
+    finally:
+        assert lib.ringo_tune_set_cache(None) == ringo.RINGO_OK
