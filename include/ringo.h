@@ -181,7 +181,7 @@ RINGO_API void ringo_graph_free(ringo_graph* g);
  * reserved up front, a serving loop that must not enter the allocator).
  * The paper has no counterpart: this is a property of this library only.
  *   The call allocates no device or pinned host memory.  Scratch space is
- *   one fixed __device__ array inside the library (about 41 MB per GPU, held
+ *   one fixed __device__ array inside the library (43.4 MB = 41.4 MiB per GPU, held
  *   until the process exits), so:
  *   - nrows <= RINGO_NOALLOC_MAX_ROWS, else RINGO_ERANGE;
  *   - calls whose GPU work overlaps (other streams or threads) race on that
