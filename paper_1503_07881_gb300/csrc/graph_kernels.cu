@@ -444,7 +444,7 @@ struct MergeSmem {
 
 // The merge path splits of every merge tile of every table, before the
 // merge: one binary search per tile start, all of them in parallel.  The
-// splits go to the radix key buffer, which phase 2 no longer uses.
+// splits go to the in-CSR neighbour array, which only phase 3 writes.
 __global__ void __launch_bounds__(256)
     k_merge_split(Ctl* __restrict__ ctls, SegMap m) {
   const uint32_t total = __ldg(m.start + m.nseg);
