@@ -410,8 +410,14 @@ int build_undirected(const int64_t* out_off, const int32_t* out_nbr, const int64
   *M = 0;
   const UmGraph g{out_off, out_nbr, in_off, in_nbr, V, 2 * E};
   const uint64_t nch64 = (g.W + kUmTile - 1) / kUmTile;
-  if (V == 0 || nch64 == 0) return RINGO_EINVAL;
-  if (nch64 >= 0x7FFFFFFFull) return RINGO_ERANGE;
+  if (V == 0 || nch64 == 0) {
+    set_error("undirected merge: empty graph");
+    return RINGO_EINVAL;
+  }
+  if (nch64 >= 0x7FFFFFFFull) {
+    set_error("undirected merge: too many adjacency entries");
+    return RINGO_ERANGE;
+  }
   const uint32_t nch = (uint32_t)nch64;
   const uint32_t tiles = (nch + kScanTileNodes - 1) / kScanTileNodes;
   // scratch: splits[nch + 1], block counts[nch], block starts[nch + 1], tile sums[tiles + 1]
@@ -423,6 +429,7 @@ int build_undirected(const int64_t* out_off, const int32_t* out_nbr, const int64
   if (!buf || !uoff) {
     pool_free(buf, s);
     pool_free(uoff, s);
+    set_error("undirected merge: device memory");
     return RINGO_ENOMEM;
   }
   char* p = buf;
@@ -449,6 +456,7 @@ int build_undirected(const int64_t* out_off, const int32_t* out_nbr, const int64
     set_error(std::string("undirected merge: ") + cudaGetErrorString(e));
     rc = RINGO_ECUDA;
   } else if (total > 0x7FFFFFFFFFull || !(unbr = (int32_t*)pool_alloc(4 * (size_t)total + 4, s))) {
+    set_error("undirected merge: device memory for the lists");
     rc = RINGO_ENOMEM;
   } else {
     {
