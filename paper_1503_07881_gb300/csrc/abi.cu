@@ -516,6 +516,7 @@ int ringo_table_to_undirected_graph(const int32_t* src, const int32_t* dst, int6
         g->in_off = (int64_t*)pool_alloc(8 * (V + 1), g->stream);
         g->in_nbr = (int32_t*)pool_alloc(4 * M + 4, g->stream);
         if (!g->in_off || !g->in_nbr) {
+          set_error("undirected: device memory for the in-direction copy");
           rc = RINGO_ENOMEM;
         } else if (cudaMemcpyAsync(g->in_off, uoff, 8 * (V + 1), cudaMemcpyDeviceToDevice,
                                    g->stream) != cudaSuccess ||
